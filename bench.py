@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Recovered Mpixel/s of the block-CS video codec hot path on GB300.
+
+One step = the whole hot path over the CIF M-sweep clip: for each M in
+{26, 51, 77, 128}, encode all 8 GOPs (64 frames, 352x288, GOP 8, 16x16 blocks)
+then decode them with 300 FISTA iterations and score the result (PSNR).  The
+four plans (Phi, A, L) are built once before timing, like weights; their build
+time is reported as plan_ms.  value = recovered CS-frame pixels per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank decodes its own copy of
+the clip (replicas, weak scaling); value = pixels of all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = {
+    "workload": "CIF 352x288, 64 frames, GOP 8 (1 raw key + 7 CS), 16x16 blocks (N=256), "
+                "M in {26,51,77,128} (CR sweep), Gaussian Phi N(0,1/M) Philox seed 0, "
+                "FISTA 300 iters, lambda=0.01*||A^T y||_inf, synthetic surveillance scene",
+    "height": 288, "width": 352, "frames": 64, "gop": 8, "block": 16,
+    "ms": [26, 51, 77, 128], "iters": 300, "lambda_rel": 0.01, "seed": 0,
+}
+METRIC = "recovered Mpixel/s at fixed iters (CIF M-sweep, FISTA 300 iters)"
+L2_FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
+                                 else ".", ".bench_clocks_%d.csv" % os.getpid())
+
+    def __enter__(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.QUERY,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        loaded = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def decode_flops(blocks: int, m: int, n: int, iters: int) -> float:
+    """Algorithmic flops of the recovery: 4MN per block per iteration (A z and
+    A^T rho) plus 2MN once per block for lambda (A^T y)."""
+    return float(blocks) * (4.0 * m * n * iters + 2.0 * m * n)
+
+
+def oracle_sample(frames, wl, n_cs_frames: int):
+    """Time the FP64 oracle on the first n_cs_frames CS frames at every M.
+
+    Returns (seconds, recovered pixels, decoded frames per M)."""
+    from oracle import cs_oracle as O
+
+    gop, b = wl["gop"], wl["block"]
+    clip = frames[:gop]
+    t0 = time.perf_counter()
+    out = {}
+    for m in wl["ms"]:
+        plan = O.Plan(b * b, m, wl["seed"])
+        y = O.encode(plan, clip, gop)[:n_cs_frames]
+        dec = []
+        for i in range(n_cs_frames):
+            r_hat = O.decode_blocks(plan, y[i], wl["iters"], wl["lambda_rel"])
+            dec.append(clip[0].astype(np.float64) +
+                       O.unblockify(r_hat, wl["height"], wl["width"], b))
+        out[m] = np.stack(dec)
+    secs = time.perf_counter() - t0
+    pixels = len(wl["ms"]) * n_cs_frames * wl["height"] * wl["width"]
+    return secs, pixels, out
+
+
+def run_reference(args, wl, frames):
+    """The reference arm: the FP64 CPU oracle as it stands, bounded samples."""
+    n_cs = 1
+    for _ in range(args.warmup):
+        oracle_sample(frames, wl, n_cs)
+    secs = []
+    pixels = 0
+    for _ in range(args.steps):
+        s, pixels, _ = oracle_sample(frames, wl, n_cs)
+        secs.append(s)
+    total = sum(secs)
+    value = pixels * args.steps / total / 1e6
+    sample = ("first CS frame of the clip (396 blocks) at each M in %s, %d iters, per step"
+              % (wl["ms"], wl["iters"]))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {k: wl[k] for k in ("workload",)},
+        "cpu_baseline": {"value": value, "unit": "Mpixel/s", "cores": os.cpu_count(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--engine", choices=["auto", "plain", "tc"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps, always
+    rank, world, local = dist_env()
+    wl = dict(WORKLOAD)
+
+    from paper_1311_1419_gb300 import scenes
+
+    frames = scenes.surveillance_video(wl["frames"], wl["height"], wl["width"], seed=wl["seed"])
+
+    if args.impl == "reference":
+        if rank == 0:
+            run_reference(args, wl, frames)
+        return
+
+    import torch
+
+    import __graft_entry__
+    from paper_1311_1419_gb300 import binding as B
+
+    __graft_entry__.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    engine = {"auto": B.CS_ENGINE_AUTO, "plain": B.CS_ENGINE_PLAIN, "tc": B.CS_ENGINE_TC}[args.engine]
+    h, w, gop, b, iters = wl["height"], wl["width"], wl["gop"], wl["block"], wl["iters"]
+    n = b * b
+    n_gops = wl["frames"] // gop
+    n_cs = n_gops * (gop - 1)
+    nblk = (-(-h // b)) * (-(-w // b))
+    cs_idx = [t for t in range(wl["frames"]) if t % gop]
+
+    ctx = B.cs_ctx_create(local)
+    t0 = time.perf_counter()
+    plans = {m: B.cs_make_phi(ctx, n, m, wl["seed"]) for m in wl["ms"]}
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    params = {m: B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops,
+                               lambda_rel=wl["lambda_rel"], engine=engine) for m in wl["ms"]}
+
+    stream = torch.cuda.Stream(dev)
+    frames_dev = torch.from_numpy(frames).to(dev)
+    keys_host = np.ascontiguousarray(frames[::gop])
+    keys_dev = torch.from_numpy(keys_host).to(dev)
+    cs_dev = torch.from_numpy(np.ascontiguousarray(frames[cs_idx])).to(dev)
+    y_dev = {m: torch.empty((n_cs, nblk, m), dtype=torch.float32, device=dev) for m in wl["ms"]}
+    out_f = {m: torch.empty((n_cs, h, w), dtype=torch.float32, device=dev) for m in wl["ms"]}
+    out_u = {m: torch.empty((n_cs, h, w), dtype=torch.uint8, device=dev) for m in wl["ms"]}
+    psnr_dev = {m: torch.empty(n_cs, dtype=torch.float64, device=dev) for m in wl["ms"]}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    launches_per_step = 3 * len(wl["ms"])
+
+    dec_ev = {m: [] for m in wl["ms"]}
+
+    def step(record_decode: bool, fr, keys):
+        for m in wl["ms"]:
+            B.cs_encode_gop(plans[m], params[m], fr, y_dev[m], stream)
+            if record_decode:
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+            B.cs_decode_gop(plans[m], params[m], keys, y_dev[m], out_f[m], out_u[m], stream)
+            if record_decode:
+                e1.record(stream)
+                dec_ev[m].append((e0, e1))
+            B.cs_psnr(cs_dev, out_f[m], n_cs, h, w, psnr_dev[m], stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step(False, frames_dev, keys_dev)
+        torch.cuda.synchronize(dev)
+
+        # device-resident timed region, L2 flushed before every step
+        step_ms = []
+        with ClockSampler(local) as clocks:
+            for _ in range(args.steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                barrier()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step(True, frames_dev, keys_dev)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                barrier()
+                step_ms.append(e0.elapsed_time(e1))
+        clock_info = clocks.summary()
+
+        # end to end through the C ABI from pinned host memory
+        frames_pin = torch.from_numpy(frames).pin_memory()
+        keys_pin = torch.from_numpy(keys_host).pin_memory()
+        u8_pin = {m: torch.empty((n_cs, h, w), dtype=torch.uint8).pin_memory() for m in wl["ms"]}
+        ps_pin = {m: torch.empty(n_cs, dtype=torch.float64).pin_memory() for m in wl["ms"]}
+        fr_in = torch.empty_like(frames_dev)
+        key_in = torch.empty_like(keys_dev)
+        h2d = frames_pin.numel() + keys_pin.numel()
+        d2h = sum(u8_pin[m].numel() + 8 * ps_pin[m].numel() for m in wl["ms"])
+        e2e_ms = []
+        for it in range(args.warmup + args.steps):
+            flush.zero_()
+            torch.cuda.synchronize(dev)
+            barrier()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fr_in.copy_(frames_pin, non_blocking=True)
+            key_in.copy_(keys_pin, non_blocking=True)
+            step(False, fr_in, key_in)
+            for m in wl["ms"]:
+                u8_pin[m].copy_(out_u[m], non_blocking=True)
+                ps_pin[m].copy_(psnr_dev[m], non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            barrier()
+            if it >= args.warmup:
+                e2e_ms.append(e0.elapsed_time(e1))
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    total_ms = max_over_ranks(sum(step_ms))
+    e2e_total = max_over_ranks(sum(e2e_ms))
+    pixels_step = len(wl["ms"]) * n_cs * h * w
+    value = world * pixels_step * args.steps / (total_ms / 1e3) / 1e6
+    e2e_value = world * pixels_step * args.steps / (e2e_total / 1e3) / 1e6
+
+    # roofline of the dominant kernel (the decode), from its own launch events
+    dec_ms = {m: sum(a.elapsed_time(b_) for a, b_ in dec_ev[m]) / len(dec_ev[m]) for m in wl["ms"]}
+    blocks = n_cs * nblk
+    flops = {m: decode_flops(blocks, m, n, iters) for m in wl["ms"]}
+    peaks, peak_kind = read_peaks()
+    tc_used = engine == B.CS_ENGINE_TC
+    achieved = sum(flops.values()) / (sum(dec_ms.values()) / 1e3) / 1e12
+    if tc_used:
+        peak = peaks["bf16_tflops_sustained"]
+        bound = "tensor"
+    else:
+        clk = clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = n_sm * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
+        bound = "alu"
+    psnr = {m: float(np.mean(psnr_dev[m].cpu().numpy())) for m in wl["ms"]}
+
+    cpu = None
+    parity = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_sample = 5
+        secs, pix, ref = oracle_sample(frames, wl, n_sample)
+        cpu = {"value": pix / secs / 1e6, "unit": "Mpixel/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": "first %d CS frames (%d blocks) at each M in %s, %d iters; numpy "
+                         "FP64 (BLAS threads = cores)" % (n_sample, n_sample * nblk, wl["ms"],
+                                                          iters)}
+        from oracle import cs_oracle as O
+        parity = {}
+        for m in wl["ms"]:
+            got = out_f[m][:n_sample].cpu().numpy().astype(np.float64)
+            want = ref[m]
+            orig = frames[1:1 + n_sample]
+            parity[str(m)] = {
+                "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want)),
+            }
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": wl["workload"], "engine": args.engine,
+                       "l2": "flushed before every timed step (256 MB write)",
+                       "parallelism": "replicas x%d" % world},
+            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "decode", "peak_source": peak_kind if bound == "tensor" else
+                         "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clock_info,
+            "plan_ms": plan_ms,
+            "decode_ms_per_launch": {str(m): dec_ms[m] for m in wl["ms"]},
+            "psnr_db": {str(m): psnr[m] for m in wl["ms"]},
+            "parity_vs_oracle": parity,
+        }
+        print(json.dumps(line), flush=True)
+
+    for p in plans.values():
+        B.cs_plan_destroy(p)
+    B.cs_ctx_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

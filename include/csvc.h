@@ -1,0 +1,169 @@
+/*
+ * csvc.h -- C ABI of the GB300 (sm_103a) library for the hot path of the
+ * multiple-residual compressive-sensing (CS) surveillance video codec of
+ * Yu, Qiao, Luo and Yang, "Increasing compression ratio of low complexity
+ * compressive sensing video encoder with application-aware configurable
+ * mechanism" (arXiv 1311.1419).
+ *
+ * A video is split into GOPs of G frames: one key frame followed by G-1 CS
+ * frames (Sec. 3, Sec. 3.1).  Every CS frame subtracts the SAME key frame of
+ * its GOP (the multiple-residual scheme, Sec. 3.2), and each residual is
+ * measured block by block with one Gaussian random matrix Phi (M x N,
+ * N = B*B pixels per block): y_b = Phi r_b (Sec. 3.1, Sec. 4).  The decoder
+ * recovers every residual block by solving Eq. (1), read here as
+ * min_s 1/2 ||A s - y||^2 + lambda ||s||_1 with A = Phi Psi and Psi the
+ * orthonormal 2-D DCT of the block, by a fixed number of FISTA iterations,
+ * then adds it back to the key frame (Eq. 4).  Key frames are passed raw.
+ *
+ * Conventions for every call:
+ *  - Pointers named *_dev are device pointers on the context's GPU (for
+ *    example from torch.empty(..., device="cuda").data_ptr()); pointers named
+ *    *_host are host memory.  The caller owns all frame, measurement and
+ *    output buffers; the library owns contexts, plans and their device memory.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *    that take a stream only enqueue work on it and return; the caller
+ *    synchronises.  Calls without a stream return after their work is done.
+ *  - Frames are uint8 [F][H][W], row-major, no row padding.  Measurements are
+ *    float32 [n_cs][nblk][M]: CS frame, then block in raster order over the
+ *    zero-padded grid of ceil(H/B) x ceil(W/B) blocks, then measurement row.
+ *    Inside a block, pixel (p, q) is vector entry p*B + q.
+ *  - Every call returns a cs_status: 0 on success, a negative CS_E* code
+ *    otherwise; no exception or abort crosses the ABI.  On error nothing has
+ *    been enqueued unless the code is CS_ECUDA (see cs_last_error()).
+ */
+#ifndef CSVC_H
+#define CSVC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                     /* cudaStream_t == struct CUstream_st* */
+typedef struct CUstream_st* cs_stream_t;
+
+typedef struct cs_ctx cs_ctx;
+typedef struct cs_plan cs_plan;
+
+/* status codes */
+#define CS_OK 0
+#define CS_EINVAL (-1)     /* bad argument: shape, size, null pointer, plan mismatch */
+#define CS_ENOMEM (-2)     /* device allocation failed or HBM budget exceeded */
+#define CS_EAGAIN (-3)     /* serving admission refused for now: retry later */
+#define CS_ETIMEDOUT (-4)  /* a bounded device-side wait gave up */
+#define CS_ECUDA (-5)      /* a CUDA runtime call or kernel launch failed */
+#define CS_ENOTFOUND (-6)  /* unknown serving ticket */
+#define CS_ENODEV (-7)     /* no usable sm_103 device */
+
+/* arithmetic of the recovery (cs_params.precision) */
+#define CS_FP32 0          /* FP32-grade products: FP32 SIMT, or FP16 hi+lo split on tensor cores */
+#define CS_BF16 1          /* BF16 A and iterate, FP32 accumulate, FP32-grade tail iterations */
+#define CS_BF16X2 2        /* split-BF16 A (hi+lo), BF16 iterate, FP32-grade tail iterations */
+#define CS_FP16 3          /* FP16 A and iterate (scaled), FP32-grade tail iterations */
+
+/* decode kernel (cs_params.engine) */
+#define CS_ENGINE_AUTO 0   /* persistent tensor-core kernel when the shape allows it */
+#define CS_ENGINE_PLAIN 1  /* one CTA per block, FP32 SIMT: the plain baseline */
+#define CS_ENGINE_TC 2     /* persistent tcgen05 kernel; CS_EINVAL if the shape is unsupported */
+
+/* Codec parameters of one encode/decode call (Sec. 3.1: "GOP size and
+ * measurement matrix size" are the encoder's configuration). */
+typedef struct cs_params {
+    int32_t height, width;    /* frame size in pixels, >= 1 */
+    int32_t gop;              /* G: frames per GOP including the key frame, >= 2 */
+    int32_t n_gops;           /* consecutive GOPs handled by one call; 0 means 1 */
+    int32_t block;            /* B: block side; B*B must equal the plan's N */
+    int32_t m;                /* M: measurements per block; must equal the plan's M */
+    int32_t iters;            /* K: FISTA iterations (fixed count, no early stop), >= 0 */
+    int32_t fp32_tail_iters;  /* last iterations run FP32-grade when precision != CS_FP32 */
+    float lambda_rel;         /* lambda_b = lambda_rel * ||A^T y_b||_inf, >= 0 (0.01 default) */
+    int32_t precision;        /* CS_FP32, CS_BF16, CS_BF16X2 or CS_FP16 */
+    int32_t engine;           /* CS_ENGINE_* */
+} cs_params;
+
+/* ---- context ------------------------------------------------------------
+ * cs_ctx_create: bind a context to CUDA device `device` (must be sm_103).
+ * hbm_budget_bytes caps the device memory that serving admission may hand
+ * out (0 = no cap).  *out receives the context; destroy it with
+ * cs_ctx_destroy after every plan made from it has been destroyed. */
+int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes);
+int cs_ctx_destroy(cs_ctx* ctx);
+
+/* ---- plans: Phi, A = Phi Psi and the FISTA step --------------------------
+ * cs_make_phi: build the plan for blocks of N = B*B pixels and M measurements
+ * (1 <= M <= N <= 4096, N a perfect square) under `seed`, entirely on the
+ * device.  Phi (Sec. 3.1, Sec. 4: a Gaussian random matrix) has entries
+ * N(0, 1/M): pair q of row-major entries (2q, 2q+1) is Box-Muller of the
+ * Philox4x64-10 block with counter (q, (N << 16) | M, 0, 0) and key (seed, 0),
+ * u1 = ((x0 >> 11) + 1) 2^-53, u2 = (x1 >> 11) 2^-53, each entry divided by
+ * sqrt(M) in double and rounded to float; the result is bit-identical on
+ * every device.  The plan also holds A = Phi Psi (float32 [M][N], formed in
+ * FP64), the tensor-core operand copies of A, the DCT matrix and
+ * L = 1.0001 * lambda_max(Phi Phi^T) from 1000 FP64 power iterations.
+ * Returns after the plan is complete.  A plan is immutable: any number of
+ * streams may use it at once. */
+int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out);
+int cs_plan_destroy(cs_plan* plan);
+/* Borrowed device pointers (valid until cs_plan_destroy): Phi and A, float32
+ * [M][N] row-major.  *lipschitz receives L. */
+int cs_plan_phi(const cs_plan* plan, const float** phi_dev);
+int cs_plan_a(const cs_plan* plan, const float** a_dev);
+int cs_plan_lipschitz(const cs_plan* plan, double* lipschitz);
+
+/* ---- encode (Sec. 3.1) ----------------------------------------------------
+ * frames_dev: uint8 [n_gops*G][H][W]; frame t of the call is a key frame when
+ * t % G == 0.  y_dev: float32 [n_gops*(G-1)][nblk][M] with
+ * nblk = ceil(H/B) * ceil(W/B).  For CS frame t the residual is
+ * int(F_t) - int(F_key), key = floor(t/G)*G, zero outside the frame, and
+ * y_b = Phi r_b with FP32-grade products (exact residuals, FP32 accumulation). */
+int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_dev,
+                  float* y_dev, cs_stream_t stream);
+
+/* ---- decode (Sec. 3.2, Eqs. 1-4) ------------------------------------------
+ * key_dev: uint8 [n_gops][H][W] (the key frame of each GOP); y_dev as written
+ * by cs_encode_gop.  Per block: lambda_b = lambda_rel ||A^T y_b||_inf,
+ * s^0 = z^1 = 0, t_1 = 1, K iterations of
+ *   s^k = soft(z^k - A^T(A z^k - y_b)/L, lambda_b/L),
+ *   z^{k+1} = s^k + ((t_k - 1)/t_{k+1})(s^k - s^{k-1}),
+ * then F'_t = F_key + Psi s^K cropped to H x W.  frames_f32_dev: float32
+ * [n_gops*(G-1)][H][W] or NULL; frames_u8_dev: uint8, same shape, clamp of
+ * round-half-even, or NULL (at least one must be non-NULL). */
+int cs_decode_gop(cs_plan* plan, const cs_params* params, const uint8_t* key_dev,
+                  const float* y_dev, float* frames_f32_dev, uint8_t* frames_u8_dev,
+                  cs_stream_t stream);
+
+/* ---- quality and compression accounting (Sec. 4, Table I) ----------------
+ * cs_psnr: per-frame PSNR 10 log10(255^2 / MSE) of test_dev (float32
+ * [n][H][W]) against ref_dev (uint8 [n][H][W]), FP64 reductions on the device;
+ * psnr_dev: double [n]; +inf where the frames are identical. */
+int cs_psnr(const uint8_t* ref_dev, const float* test_dev, int32_t n_frames,
+            int32_t height, int32_t width, double* psnr_dev, cs_stream_t stream);
+/* Total CR of a GOP of 1 key + (G-1) CS frames, G / (1/cr_key + (G-1)/cr_cs):
+ * the closed form behind Table I.  Returns NaN for G < 1 or non-positive CRs. */
+double cs_total_cr(int32_t gop, double cr_key, double cr_cs);
+/* CR of one GOP with a raw key frame: G*H*W / (H*W + (G-1)*nblk*M). */
+double cs_raw_key_cr(int32_t gop, int32_t height, int32_t width, int32_t block, int32_t m);
+
+/* ---- serving --------------------------------------------------------------
+ * cs_submit: enqueue the decode of one request (cs_decode_gop semantics,
+ * frames_u8_dev output) on the context's serving streams.  Admission charges
+ * the request's device working set against the context's HBM budget and the
+ * number of free slots; when either is exhausted the call returns CS_EAGAIN
+ * and enqueues nothing.  *ticket identifies the request.
+ * cs_poll: non-blocking; *done = 1 once the request's output is complete,
+ * then *latency_ms is submit-to-completion time and the ticket is retired. */
+int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t* key_dev,
+              const float* y_dev, uint8_t* frames_u8_dev, uint64_t* ticket);
+int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms);
+
+/* ---- errors --------------------------------------------------------------- */
+const char* cs_strerror(int status);
+/* Detail of the last failure on the calling thread (empty if none). */
+const char* cs_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CSVC_H */

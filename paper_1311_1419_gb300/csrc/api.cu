@@ -1,0 +1,390 @@
+// The C ABI (include/csvc.h): contexts, plans, argument checking, dispatch of
+// the encode/decode/metrics kernels, compression-ratio accounting and the
+// serving tickets.  No torch type crosses this boundary; every call reports
+// failure through its return code.
+#include <math.h>
+#include <string.h>
+
+#include <atomic>
+#include <chrono>
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+namespace csvc {
+
+namespace {
+thread_local std::string g_last_error;
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int status, const std::string& msg) {
+    g_last_error = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t err, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorName(err) + " (" +
+                   cudaGetErrorString(err) + ")";
+    return err == cudaErrorMemoryAllocation ? CS_ENOMEM : CS_ECUDA;
+}
+
+struct Ticket {
+    uint64_t id = 0;
+    size_t bytes = 0;
+    double submit_ms = 0.0;
+    std::atomic<double> done_ms{-1.0};  // written by the host callback after the decode
+    cudaEvent_t done_event = nullptr;
+};
+
+namespace {
+
+void CUDART_CB mark_done(void* p) { static_cast<Ticket*>(p)->done_ms.store(now_ms()); }
+
+// Validate a call's parameters against the plan and derive the GOP shape.
+int make_shape(const cs_plan* plan, const cs_params* p, GopShape* gs) {
+    if (!plan || !p) return fail(CS_EINVAL, "null plan or params");
+    if (p->height < 1 || p->width < 1) return fail(CS_EINVAL, "frame size must be >= 1");
+    if (p->gop < 2) return fail(CS_EINVAL, "gop must be >= 2 (one key + at least one CS frame)");
+    if (p->n_gops < 0) return fail(CS_EINVAL, "n_gops must be >= 0");
+    if (p->block != plan->b) return fail(CS_EINVAL, "block*block does not match the plan's N");
+    if (p->m != plan->m) return fail(CS_EINVAL, "m does not match the plan's M");
+    gs->h = p->height;
+    gs->w = p->width;
+    gs->g = p->gop;
+    gs->n_gops = p->n_gops == 0 ? 1 : p->n_gops;
+    gs->b = plan->b;
+    gs->n = plan->n;
+    gs->m = plan->m;
+    gs->nbr = (p->height + plan->b - 1) / plan->b;
+    gs->nbc = (p->width + plan->b - 1) / plan->b;
+    gs->nblk = gs->nbr * gs->nbc;
+    const long long n_cs = (long long)gs->n_gops * (p->gop - 1);
+    if (n_cs * gs->nblk > (1ll << 31) - 1) return fail(CS_EINVAL, "too many blocks in one call");
+    gs->n_cs = (int)n_cs;
+    return CS_OK;
+}
+
+int check_decode_params(const cs_params* p) {
+    if (p->iters < 0 || p->iters > kMaxIters) return fail(CS_EINVAL, "iters out of range");
+    if (p->fp32_tail_iters < 0) return fail(CS_EINVAL, "fp32_tail_iters must be >= 0");
+    if (!(p->lambda_rel >= 0.f) || !isfinite(p->lambda_rel))
+        return fail(CS_EINVAL, "lambda_rel must be finite and >= 0");
+    if (p->precision < CS_FP32 || p->precision > CS_FP16) return fail(CS_EINVAL, "bad precision");
+    if (p->engine < CS_ENGINE_AUTO || p->engine > CS_ENGINE_TC) return fail(CS_EINVAL, "bad engine");
+    return CS_OK;
+}
+
+int decode_impl(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
+                float* out_f32, uint8_t* out_u8, cudaStream_t stream) {
+    GopShape gs;
+    int st = make_shape(plan, params, &gs);
+    if (st) return st;
+    st = check_decode_params(params);
+    if (st) return st;
+    if (!out_f32 && !out_u8) return fail(CS_EINVAL, "both outputs are NULL");
+    if (gs.n_cs > 0 && (!key || !y)) return fail(CS_EINVAL, "null input pointer");
+    DecodeArgs d;
+    d.plan = plan;
+    d.gs = gs;
+    d.key = key;
+    d.y = y;
+    d.out_f32 = out_f32;
+    d.out_u8 = out_u8;
+    d.iters = params->iters;
+    d.tail_iters = params->fp32_tail_iters;
+    d.lambda_rel = params->lambda_rel;
+    d.precision = params->precision;
+    d.beta = plan->ctx->beta_dev;
+    int engine = params->engine;
+    const bool tc_ok = tc_supported(plan, params->precision);
+    if (engine == CS_ENGINE_TC && !tc_ok)
+        return fail(CS_EINVAL, "tensor-core decode does not support this (N, M, precision)");
+    if (engine == CS_ENGINE_AUTO) engine = tc_ok ? CS_ENGINE_TC : CS_ENGINE_PLAIN;
+    if (engine == CS_ENGINE_PLAIN && params->precision != CS_FP32)
+        return fail(CS_EINVAL, "the plain engine computes in FP32 only");
+    cudaError_t e = engine == CS_ENGINE_TC ? launch_decode_tc(d, stream)
+                                           : launch_decode_plain(d, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "decode launch");
+    return CS_OK;
+}
+
+}  // namespace
+}  // namespace csvc
+
+using namespace csvc;
+
+extern "C" {
+
+int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
+    if (!out) return fail(CS_EINVAL, "out is NULL");
+    *out = nullptr;
+    int count = 0;
+    cudaError_t e = cudaGetDeviceCount(&count);
+    if (e != cudaSuccess || count == 0) return fail(CS_ENODEV, "no CUDA device");
+    if (device < 0 || device >= count) return fail(CS_EINVAL, "device index out of range");
+    CS_CUDA_TRY(cudaSetDevice(device));
+    cudaDeviceProp prop;
+    CS_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+    if (prop.major != 10 || prop.minor != 3)
+        return fail(CS_ENODEV, "this library is built for sm_103 (GB300) only");
+    cs_ctx* ctx = new (std::nothrow) cs_ctx();
+    if (!ctx) return fail(CS_ENOMEM, "host allocation failed");
+    ctx->device = device;
+    ctx->sm_count = prop.multiProcessorCount;
+    ctx->hbm_budget = hbm_budget_bytes;
+    // FISTA momentum schedule: t_1 = 1, t_{k+1} = (1 + sqrt(1 + 4 t_k^2))/2,
+    // beta_k = (t_k - 1)/t_{k+1}; a data-independent scalar sequence, in FP64.
+    std::vector<float> beta(kMaxIters);
+    double t = 1.0;
+    for (int k = 0; k < kMaxIters; ++k) {
+        const double tn = (1.0 + sqrt(1.0 + 4.0 * t * t)) / 2.0;
+        beta[k] = (float)((t - 1.0) / tn);
+        t = tn;
+    }
+    e = cudaMalloc(&ctx->beta_dev, sizeof(float) * kMaxIters);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(ctx->beta_dev, beta.data(), sizeof(float) * kMaxIters, cudaMemcpyHostToDevice);
+    for (int i = 0; e == cudaSuccess && i < 8; ++i) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) ctx->streams.push_back(s);
+    }
+    if (e != cudaSuccess) {
+        int st = cuda_fail(e, "context setup");
+        cs_ctx_destroy(ctx);
+        return st;
+    }
+    *out = ctx;
+    return CS_OK;
+}
+
+int cs_ctx_destroy(cs_ctx* ctx) {
+    if (!ctx) return CS_OK;
+    cudaSetDevice(ctx->device);
+    for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
+    for (Ticket* t : ctx->live) {
+        if (t->done_event) cudaEventDestroy(t->done_event);
+        delete t;
+    }
+    for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
+    if (ctx->beta_dev) cudaFree(ctx->beta_dev);
+    delete ctx;
+    return CS_OK;
+}
+
+int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out) {
+    if (!ctx || !out) return fail(CS_EINVAL, "null ctx or out");
+    *out = nullptr;
+    int b = (int)lround(sqrt((double)n));
+    if (n < 1 || n > kMaxN || b * b != n) return fail(CS_EINVAL, "N must be a perfect square <= 4096");
+    if (m < 1 || m > n || m > 1024) return fail(CS_EINVAL, "need 1 <= M <= min(N, 1024)");
+    CS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cs_plan* p = new (std::nothrow) cs_plan();
+    if (!p) return fail(CS_ENOMEM, "host allocation failed");
+    p->ctx = ctx;
+    p->n = n;
+    p->m = m;
+    p->b = b;
+    p->seed = seed;
+    double* gram = nullptr;
+    double* lam_dev = nullptr;
+    cudaStream_t s = nullptr;
+    double lam = 0.0;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    const size_t mn = (size_t)m * n;
+    if (e == cudaSuccess) e = cudaMalloc(&p->phi, mn * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&p->a, mn * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&p->dct, (size_t)b * b * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&gram, (size_t)m * m * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&lam_dev, sizeof(double));
+    if (e == cudaSuccess) e = launch_phi(p->phi, n, m, seed, s);
+    if (e == cudaSuccess) e = launch_form_a(p->phi, p->a, p->dct, n, m, b, s);
+    if (e == cudaSuccess) e = launch_lambda_max(p->phi, n, m, gram, lam_dev, s);
+    p->m_pad = tc_m_pad(m);
+    if (e == cudaSuccess && p->m_pad > 0) {
+        p->tc_bytes = tc_operand_bytes(n, p->m_pad);
+        e = cudaMalloc(&p->a_tc, p->tc_bytes);
+        if (e == cudaSuccess) e = launch_prepare_tc(p->a, p->a_tc, n, m, p->m_pad, s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lam, lam_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (gram) cudaFree(gram);
+    if (lam_dev) cudaFree(lam_dev);
+    if (s) cudaStreamDestroy(s);
+    if (e != cudaSuccess) {
+        int st = cuda_fail(e, "cs_make_phi");
+        cs_plan_destroy(p);
+        return st;
+    }
+    if (!(lam > 0.0) || !isfinite(lam)) {
+        cs_plan_destroy(p);
+        return fail(CS_ECUDA, "power iteration returned a non-positive lambda_max");
+    }
+    p->lipschitz = 1.0001 * lam;
+    *out = p;
+    return CS_OK;
+}
+
+int cs_plan_destroy(cs_plan* p) {
+    if (!p) return CS_OK;
+    cudaSetDevice(p->ctx->device);
+    if (p->phi) cudaFree(p->phi);
+    if (p->a) cudaFree(p->a);
+    if (p->dct) cudaFree(p->dct);
+    if (p->a_tc) cudaFree(p->a_tc);
+    delete p;
+    return CS_OK;
+}
+
+int cs_plan_phi(const cs_plan* p, const float** phi_dev) {
+    if (!p || !phi_dev) return fail(CS_EINVAL, "null argument");
+    *phi_dev = p->phi;
+    return CS_OK;
+}
+
+int cs_plan_a(const cs_plan* p, const float** a_dev) {
+    if (!p || !a_dev) return fail(CS_EINVAL, "null argument");
+    *a_dev = p->a;
+    return CS_OK;
+}
+
+int cs_plan_lipschitz(const cs_plan* p, double* lipschitz) {
+    if (!p || !lipschitz) return fail(CS_EINVAL, "null argument");
+    *lipschitz = p->lipschitz;
+    return CS_OK;
+}
+
+int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_dev, float* y_dev,
+                  cs_stream_t stream) {
+    GopShape gs;
+    int st = make_shape(plan, params, &gs);
+    if (st) return st;
+    if (gs.n_cs > 0 && (!frames_dev || !y_dev)) return fail(CS_EINVAL, "null buffer");
+    cudaError_t e = launch_encode(plan, gs, frames_dev, y_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "encode launch");
+    return CS_OK;
+}
+
+int cs_decode_gop(cs_plan* plan, const cs_params* params, const uint8_t* key_dev, const float* y_dev,
+                  float* frames_f32_dev, uint8_t* frames_u8_dev, cs_stream_t stream) {
+    return decode_impl(plan, params, key_dev, y_dev, frames_f32_dev, frames_u8_dev,
+                       (cudaStream_t)stream);
+}
+
+int cs_psnr(const uint8_t* ref_dev, const float* test_dev, int32_t n_frames, int32_t height,
+            int32_t width, double* psnr_dev, cs_stream_t stream) {
+    if (n_frames < 0 || height < 1 || width < 1) return fail(CS_EINVAL, "bad shape");
+    if (n_frames > 0 && (!ref_dev || !test_dev || !psnr_dev)) return fail(CS_EINVAL, "null buffer");
+    cudaError_t e = launch_psnr(ref_dev, test_dev, n_frames, height, width, psnr_dev,
+                                (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "psnr launch");
+    return CS_OK;
+}
+
+double cs_total_cr(int32_t gop, double cr_key, double cr_cs) {
+    if (gop < 1 || !(cr_key > 0.0) || !(cr_cs > 0.0)) return NAN;
+    return gop / (1.0 / cr_key + (gop - 1) / cr_cs);
+}
+
+double cs_raw_key_cr(int32_t gop, int32_t height, int32_t width, int32_t block, int32_t m) {
+    if (gop < 1 || height < 1 || width < 1 || block < 1 || m < 1) return NAN;
+    const double nblk = (double)((height + block - 1) / block) * ((width + block - 1) / block);
+    const double px = (double)height * width;
+    return gop * px / (px + (gop - 1) * nblk * m);
+}
+
+int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t* key_dev,
+              const float* y_dev, uint8_t* frames_u8_dev, uint64_t* ticket) {
+    if (!ctx || !plan || !params || !ticket) return fail(CS_EINVAL, "null argument");
+    if (plan->ctx != ctx) return fail(CS_EINVAL, "plan belongs to another context");
+    GopShape gs;
+    int st = make_shape(plan, params, &gs);
+    if (st) return st;
+    // working set charged to the budget: the request's inputs and outputs
+    const size_t bytes = (size_t)gs.n_gops * gs.h * gs.w +
+                         (size_t)gs.n_cs * gs.nblk * gs.m * sizeof(float) +
+                         (size_t)gs.n_cs * gs.h * gs.w;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    if ((int)ctx->live.size() >= ctx->max_slots) return fail(CS_EAGAIN, "no free serving slot");
+    if (ctx->hbm_budget && ctx->hbm_in_use + bytes > ctx->hbm_budget)
+        return fail(CS_EAGAIN, "HBM budget exhausted");
+    Ticket* t = new (std::nothrow) Ticket();
+    if (!t) return fail(CS_ENOMEM, "host allocation failed");
+    cudaStream_t s = ctx->streams[ctx->next_stream++ % ctx->streams.size()];
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->done_event, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete t;
+        return cuda_fail(e, "cs_submit");
+    }
+    t->id = ctx->next_ticket++;
+    t->bytes = bytes;
+    t->submit_ms = now_ms();
+    st = decode_impl(plan, params, key_dev, y_dev, nullptr, frames_u8_dev, s);
+    if (st == CS_OK) {
+        e = cudaLaunchHostFunc(s, mark_done, t);
+        if (e == cudaSuccess) e = cudaEventRecord(t->done_event, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "cs_submit completion hook");
+    }
+    if (st != CS_OK) {
+        // anything already enqueued still runs; keep the ticket alive until it does
+        cudaStreamSynchronize(s);
+        cudaEventDestroy(t->done_event);
+        delete t;
+        return st;
+    }
+    ctx->hbm_in_use += bytes;
+    ctx->live.push_back(t);
+    *ticket = t->id;
+    return CS_OK;
+}
+
+int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms) {
+    if (!ctx || !done) return fail(CS_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    for (size_t i = 0; i < ctx->live.size(); ++i) {
+        Ticket* t = ctx->live[i];
+        if (t->id != ticket) continue;
+        cudaError_t e = cudaEventQuery(t->done_event);
+        if (e == cudaErrorNotReady || t->done_ms.load() < 0.0) {
+            *done = 0;
+            return CS_OK;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cs_poll");
+        *done = 1;
+        if (latency_ms) *latency_ms = (float)(t->done_ms.load() - t->submit_ms);
+        ctx->hbm_in_use -= t->bytes;
+        cudaEventDestroy(t->done_event);
+        delete t;
+        ctx->live.erase(ctx->live.begin() + i);
+        return CS_OK;
+    }
+    return fail(CS_ENOTFOUND, "unknown or retired ticket");
+}
+
+const char* cs_strerror(int status) {
+    switch (status) {
+        case CS_OK: return "ok";
+        case CS_EINVAL: return "invalid argument";
+        case CS_ENOMEM: return "out of device memory or HBM budget";
+        case CS_EAGAIN: return "not admitted now, retry";
+        case CS_ETIMEDOUT: return "bounded device wait timed out";
+        case CS_ECUDA: return "CUDA error";
+        case CS_ENOTFOUND: return "unknown ticket";
+        case CS_ENODEV: return "no usable sm_103 device";
+        default: return "unknown status";
+    }
+}
+
+const char* cs_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/csvc.h"
+
+namespace csvc {
+
+// Maximum FISTA iteration count accepted by a call (size of the momentum table).
+constexpr int kMaxIters = 1 << 17;
+constexpr int kMaxN = 4096;
+
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t err, const char* what);
+
+#define CS_CUDA_TRY(expr)                                         \
+    do {                                                          \
+        cudaError_t _e = (expr);                                  \
+        if (_e != cudaSuccess) return ::csvc::cuda_fail(_e, #expr); \
+    } while (0)
+
+struct Ticket;
+
+}  // namespace csvc
+
+struct cs_ctx {
+    int device = 0;
+    int sm_count = 0;
+    size_t hbm_budget = 0;
+    float* beta_dev = nullptr;          // FISTA momentum (t_k - 1)/t_{k+1}, k = 1..kMaxIters
+    // serving state
+    std::mutex mu;
+    size_t hbm_in_use = 0;
+    int max_slots = 64;
+    std::vector<csvc::Ticket*> live;
+    uint64_t next_ticket = 1;
+    std::vector<cudaStream_t> streams;
+    int next_stream = 0;
+};
+
+struct cs_plan {
+    cs_ctx* ctx = nullptr;
+    int n = 0, m = 0, b = 0;
+    uint64_t seed = 0;
+    double lipschitz = 0.0;   // L = 1.0001 * lambda_max(Phi Phi^T)
+    float* phi = nullptr;     // [M][N] float32
+    float* a = nullptr;       // [M][N] float32, A = Phi Psi
+    float* dct = nullptr;     // [B][B] float32, C[k][j]
+    // tensor-core operands (fp16 hi/lo of A * 2^kAScaleLog2, padded, swizzled)
+    uint16_t* a_tc = nullptr;
+    int m_pad = 0;            // M rounded up to the tensor-core tile
+    size_t tc_bytes = 0;
+};
+
+namespace csvc {
+
+// plan construction kernels (phi.cu)
+cudaError_t launch_phi(float* phi, int n, int m, uint64_t seed, cudaStream_t s);
+cudaError_t launch_form_a(const float* phi, float* a, float* dct, int n, int m, int b,
+                          cudaStream_t s);
+cudaError_t launch_lambda_max(const float* phi, int n, int m, double* gram_scratch,
+                              double* result_dev, cudaStream_t s);
+
+// encode (encode.cu)
+struct GopShape {
+    int h, w, g, n_gops, b, n, m;
+    int nbr, nbc, nblk;   // block rows, block cols, blocks per frame
+    int n_cs;             // CS frames in the call = n_gops * (g - 1)
+};
+cudaError_t launch_encode(const cs_plan* plan, const GopShape& gs, const uint8_t* frames,
+                          float* y, cudaStream_t s);
+
+// decode (decode_plain.cu, decode_tc.cu)
+struct DecodeArgs {
+    const cs_plan* plan;
+    GopShape gs;
+    const uint8_t* key;
+    const float* y;
+    float* out_f32;
+    uint8_t* out_u8;
+    int iters;
+    int tail_iters;
+    float lambda_rel;
+    int precision;
+    const float* beta;
+};
+cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s);
+bool tc_supported(const cs_plan* plan, int precision);
+cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
+
+// metrics (metrics.cu)
+cudaError_t launch_psnr(const uint8_t* ref, const float* test, int n_frames, int h, int w,
+                        double* out, cudaStream_t s);
+
+// tensor-core operand preparation (decode_tc.cu)
+int tc_m_pad(int m);
+size_t tc_operand_bytes(int n, int m_pad);
+cudaError_t launch_prepare_tc(const float* a, uint16_t* a_tc, int n, int m, int m_pad,
+                              cudaStream_t s);
+
+}  // namespace csvc
