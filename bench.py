@@ -178,10 +178,17 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--engine", choices=["auto", "plain", "tc"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-m", type=int, default=0,
+                    help="run a single M of the sweep (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps, always
     rank, world, local = dist_env()
     wl = dict(WORKLOAD)
+    if args.only_m:
+        if args.only_m not in wl["ms"]:
+            ap.error("--only-m must be one of %s" % wl["ms"])
+        wl["ms"] = [args.only_m]
 
     from paper_1311_1419_gb300 import scenes
 
@@ -283,7 +290,7 @@ def main():
         h2d = frames_pin.numel() + keys_pin.numel()
         d2h = sum(u8_pin[m].numel() + 8 * ps_pin[m].numel() for m in wl["ms"])
         e2e_ms = []
-        for it in range(args.warmup + args.steps):
+        for it in range(0 if args.no_e2e else args.warmup + args.steps):
             flush.zero_()
             torch.cuda.synchronize(dev)
             barrier()
@@ -311,7 +318,7 @@ def main():
         return float(t.item())
 
     total_ms = max_over_ranks(sum(step_ms))
-    e2e_total = max_over_ranks(sum(e2e_ms))
+    e2e_total = max_over_ranks(sum(e2e_ms)) if e2e_ms else float("nan")
     pixels_step = len(wl["ms"]) * n_cs * h * w
     value = world * pixels_step * args.steps / (total_ms / 1e3) / 1e6
     e2e_value = world * pixels_step * args.steps / (e2e_total / 1e3) / 1e6
@@ -368,8 +375,9 @@ def main():
                          "kernel": "decode", "peak_source": peak_kind if bound == "tensor" else
                          "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"},
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
+            "e2e": None if not e2e_ms else {
+                "value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clock_info,
             "plan_ms": plan_ms,
