@@ -158,6 +158,27 @@ int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t
               const float* y_dev, uint8_t* frames_u8_dev, uint64_t* ticket);
 int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms);
 
+/* ---- allocation-free Lipschitz estimate -------------------------------------
+ * The paper has no counterpart to this call; it is a service for callers that
+ * must not allocate device memory: a serving process whose HBM was reserved
+ * in full at start-up, or a latency-critical loop that cannot take the
+ * device-wide synchronisation cudaMalloc/cudaFree may cause.
+ * cs_lambda_max_noalloc computes lambda_max(Phi Phi^T) of phi_dev (float32
+ * [M][N], for example cs_plan_phi's pointer) by the same FP64 Gram matrix and
+ * 1000 power iterations cs_make_phi uses, and writes it to lambda_max_dev (one
+ * device double; the plan's L is 1.0001 times this value).  It calls no
+ * cudaMalloc, cudaFree or allocating library routine: the M x M Gram matrix
+ * lives in a 512 KB array inside the library, which every GPU that loads the
+ * library holds until the process exits.  Limits: 1 <= M <= min(N, 256),
+ * N <= 4096; larger sizes return CS_EINVAL and enqueue nothing.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.
+ * Every call shares the one array, so calls whose work overlaps on the GPU
+ * race and must be serialised by the caller.  Enqueues on `stream` and
+ * returns. */
+int cs_lambda_max_noalloc(const float* phi_dev, int32_t n, int32_t m, double* lambda_max_dev,
+                          cs_stream_t stream);
+
 /* ---- errors --------------------------------------------------------------- */
 const char* cs_strerror(int status);
 /* Detail of the last failure on the calling thread (empty if none). */

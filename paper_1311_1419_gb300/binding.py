@@ -76,6 +76,7 @@ _SIGS = {
                                  ctypes.POINTER(ctypes.c_uint64)]),
     "cs_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32),
                                ctypes.POINTER(ctypes.c_float)]),
+    "cs_lambda_max_noalloc": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp]),
     "cs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "cs_last_error": (ctypes.c_char_p, []),
 }
@@ -209,6 +210,11 @@ def cs_poll(ctx: int, ticket: int):
     lat = ctypes.c_float()
     _check(load().cs_poll(ctx, int(ticket), ctypes.byref(done), ctypes.byref(lat)))
     return bool(done.value), float(lat.value)
+
+
+def cs_lambda_max_noalloc(phi_dev, n: int, m: int, lambda_max_dev, stream=None) -> None:
+    _check(load().cs_lambda_max_noalloc(_ptr(phi_dev), int(n), int(m), _ptr(lambda_max_dev),
+                                        _stream(stream)))
 
 
 def cs_strerror(status: int) -> str:
