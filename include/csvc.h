@@ -90,6 +90,11 @@ typedef struct cs_params {
  * cs_ctx_destroy after every plan made from it has been destroyed. */
 int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes);
 int cs_ctx_destroy(cs_ctx* ctx);
+/* cs_ctx_status: synchronise the context's device, then report CS_ETIMEDOUT
+ * (and clear the condition) if a kernel of this context gave up one of its
+ * bounded device-side waits since the last call: its outputs are incomplete.
+ * Otherwise CS_OK.  The context stays usable either way. */
+int cs_ctx_status(cs_ctx* ctx);
 
 /* ---- plans: Phi, A = Phi Psi and the FISTA step --------------------------
  * cs_make_phi: build the plan for blocks of N = B*B pixels and M measurements

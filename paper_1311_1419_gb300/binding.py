@@ -62,6 +62,7 @@ _i32 = ctypes.c_int32
 _SIGS = {
     "cs_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t]),
     "cs_ctx_destroy": (ctypes.c_int, [_vp]),
+    "cs_ctx_status": (ctypes.c_int, [_vp]),
     "cs_make_phi": (ctypes.c_int, [_vp, _i32, _i32, ctypes.c_uint64, ctypes.POINTER(_vp)]),
     "cs_plan_destroy": (ctypes.c_int, [_vp]),
     "cs_plan_phi": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
@@ -142,6 +143,10 @@ def cs_ctx_create(device: int = 0, hbm_budget_bytes: int = 0) -> int:
 
 def cs_ctx_destroy(ctx: int) -> None:
     _check(load().cs_ctx_destroy(ctx))
+
+
+def cs_ctx_status(ctx: int) -> None:
+    _check(load().cs_ctx_status(ctx))
 
 
 def cs_make_phi(ctx: int, n: int, m: int, seed: int) -> int:

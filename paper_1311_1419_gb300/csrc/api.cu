@@ -153,6 +153,8 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
     e = cudaMalloc(&ctx->beta_dev, sizeof(float) * kMaxIters);
     if (e == cudaSuccess)
         e = cudaMemcpy(ctx->beta_dev, beta.data(), sizeof(float) * kMaxIters, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->err_dev, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->err_dev, 0, sizeof(int));
     for (int i = 0; e == cudaSuccess && i < 8; ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -177,6 +179,7 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     }
     for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
     if (ctx->beta_dev) cudaFree(ctx->beta_dev);
+    if (ctx->err_dev) cudaFree(ctx->err_dev);
     delete ctx;
     return CS_OK;
 }
@@ -197,8 +200,11 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
     p->seed = seed;
     double* gram = nullptr;
     double* lam_dev = nullptr;
+    float* ranges_dev = nullptr;
+    float ranges[2] = {0.f, 0.f};
     cudaStream_t s = nullptr;
     double lam = 0.0;
+    const bool tc = tc_plan_supported(n, m);
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     const size_t mn = (size_t)m * n;
     if (e == cudaSuccess) e = cudaMalloc(&p->phi, mn * sizeof(float));
@@ -206,19 +212,28 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
     if (e == cudaSuccess) e = cudaMalloc(&p->dct, (size_t)b * b * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&gram, (size_t)m * m * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&lam_dev, sizeof(double));
+    if (e == cudaSuccess && tc) e = cudaMalloc(&ranges_dev, 2 * sizeof(float));
     if (e == cudaSuccess) e = launch_phi(p->phi, n, m, seed, s);
     if (e == cudaSuccess) e = launch_form_a(p->phi, p->a, p->dct, n, m, b, s);
     if (e == cudaSuccess) e = launch_lambda_max(p->phi, n, m, gram, lam_dev, s);
-    p->m_pad = tc_m_pad(m);
-    if (e == cudaSuccess && p->m_pad > 0) {
-        p->tc_bytes = tc_operand_bytes(n, p->m_pad);
-        e = cudaMalloc(&p->a_tc, p->tc_bytes);
-        if (e == cudaSuccess) e = launch_prepare_tc(p->a, p->a_tc, n, m, p->m_pad, s);
-    }
+    if (e == cudaSuccess && tc) e = launch_tc_ranges(p->a, p->phi, n, m, ranges_dev, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&lam, lam_dev, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && tc)
+        e = cudaMemcpyAsync(ranges, ranges_dev, sizeof(ranges), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && tc && ranges[0] > 0.f) {
+        // fp16 operands: A scaled so that max |A| lands near 2^14; the residual
+        // operand scaled down only if 4 * 255 * max_m ||Phi_m||_1 could pass 2^14
+        p->tc_ea = (int)floor(log2(16384.0 / (double)ranges[0]));
+        const double pbound = 4.0 * 255.0 * (double)ranges[1];
+        p->tc_ep = pbound > 16384.0 ? (int)floor(log2(16384.0 / pbound)) : 0;
+        e = cudaMalloc(&p->a_tc, tc_operand_bytes());
+        if (e == cudaSuccess) e = launch_tc_images(p->a, p->a_tc, n, m, p->tc_ea, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
     if (gram) cudaFree(gram);
     if (lam_dev) cudaFree(lam_dev);
+    if (ranges_dev) cudaFree(ranges_dev);
     if (s) cudaStreamDestroy(s);
     if (e != cudaSuccess) {
         int st = cuda_fail(e, "cs_make_phi");
@@ -369,6 +384,19 @@ int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms) {
         return CS_OK;
     }
     return fail(CS_ENOTFOUND, "unknown or retired ticket");
+}
+
+int cs_ctx_status(cs_ctx* ctx) {
+    if (!ctx) return fail(CS_EINVAL, "null ctx");
+    CS_CUDA_TRY(cudaSetDevice(ctx->device));
+    CS_CUDA_TRY(cudaDeviceSynchronize());
+    int flag = 0;
+    CS_CUDA_TRY(cudaMemcpy(&flag, ctx->err_dev, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        CS_CUDA_TRY(cudaMemset(ctx->err_dev, 0, sizeof(int)));
+        return fail(CS_ETIMEDOUT, "a decode kernel gave up a bounded device-side wait");
+    }
+    return CS_OK;
 }
 
 const char* cs_strerror(int status) {

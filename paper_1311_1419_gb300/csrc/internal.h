@@ -35,6 +35,7 @@ struct cs_ctx {
     int sm_count = 0;
     size_t hbm_budget = 0;
     float* beta_dev = nullptr;          // FISTA momentum (t_k - 1)/t_{k+1}, k = 1..kMaxIters
+    int* err_dev = nullptr;             // set to 1 by a kernel whose bounded wait gave up
     // serving state
     std::mutex mu;
     size_t hbm_in_use = 0;
@@ -53,10 +54,11 @@ struct cs_plan {
     float* phi = nullptr;     // [M][N] float32
     float* a = nullptr;       // [M][N] float32, A = Phi Psi
     float* dct = nullptr;     // [B][B] float32, C[k][j]
-    // tensor-core operands (fp16 hi/lo of A * 2^kAScaleLog2, padded, swizzled)
-    uint16_t* a_tc = nullptr;
-    int m_pad = 0;            // M rounded up to the tensor-core tile
-    size_t tc_bytes = 0;
+    // tensor-core operands: shared-memory images of A * 2^tc_ea (fp16 hi, fp16
+    // lo, bf16 hi, bf16 lo); NULL when the shape has no tensor-core kernel
+    uint8_t* a_tc = nullptr;
+    int tc_ea = 0;            // log2 scale of A in the 16-bit operands
+    int tc_ep = 0;            // log2 scale of the residual operand P
 };
 
 namespace csvc {
@@ -100,9 +102,10 @@ cudaError_t launch_psnr(const uint8_t* ref, const float* test, int n_frames, int
                         double* out, cudaStream_t s);
 
 // tensor-core operand preparation (decode_tc.cu)
-int tc_m_pad(int m);
-size_t tc_operand_bytes(int n, int m_pad);
-cudaError_t launch_prepare_tc(const float* a, uint16_t* a_tc, int n, int m, int m_pad,
-                              cudaStream_t s);
+bool tc_plan_supported(int n, int m);
+size_t tc_operand_bytes();
+cudaError_t launch_tc_ranges(const float* a, const float* phi, int n, int m, float* out,
+                             cudaStream_t s);
+cudaError_t launch_tc_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s);
 
 }  // namespace csvc
