@@ -227,7 +227,7 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
         p->tc_ea = (int)floor(log2(16384.0 / (double)ranges[0]));
         const double pbound = 4.0 * 255.0 * (double)ranges[1];
         p->tc_ep = pbound > 16384.0 ? (int)floor(log2(16384.0 / pbound)) : 0;
-        e = cudaMalloc(&p->a_tc, tc_operand_bytes());
+        e = cudaMalloc(&p->a_tc, tc_operand_bytes(m));
         if (e == cudaSuccess) e = launch_tc_images(p->a, p->a_tc, n, m, p->tc_ea, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     }

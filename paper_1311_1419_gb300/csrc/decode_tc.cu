@@ -4,24 +4,33 @@
 // 1/2 ||A s - y||^2 + lambda ||s||_1 (Eq. 1 with an l1 regulariser in the DCT
 // basis; Beck & Teboulle 2009), followed by r = Psi s and the key add-back of
 // Eq. (4).  Across blocks the two products of every iteration are dense
-// contractions, so a tile of 64 blocks runs them on the tensor cores:
+// contractions; a tile of 128 blocks runs them on the tensor cores with the
+// blocks on the 128 TMEM lanes:
 //
-//   GEMM1  U^T [M x 64] = A [M x N]   . Z^T [N x 64]     (u = A z per block)
-//   GEMM2  G^T [N x 64] = A^T [N x M] . P^T [M x 64]     (g = A^T (u - y))
+//   GEMM1  U [128 x M16] = Z [128 x 256]   . A^T [256 x M16]   (u = A z per block)
+//   GEMM2  G [128 x 256] = P [128 x M16]   . A   [M16 x 256]   (g = A^T (u - y))
 //
-// One CTA per SM holds A (hi and lo halves of a 2-term split, fp16 or bf16,
-// 128-byte swizzled) in shared memory for its whole life, loaded once by the
-// bulk-copy engine.  The iterates never leave the SM: Y, Z and S_prev live in
-// tensor memory next to the accumulators; the epilogue warps apply the soft
-// threshold and the momentum step and write the next MMA operand (Z, or the
-// residual P) back to shared memory as MN-major swizzled rows.  FP32-grade
-// products use three MMAs (hi.hi + hi.lo + lo.hi); the mixed-precision modes
-// run one MMA (hi.hi) until their FP32-grade tail.
+// A tcgen05.mma costs about the same number of cycles whatever its N when an
+// operand comes from shared memory, so GEMM2 is issued at the full N = 256 and
+// GEMM1 takes its A operand (Z) straight from tensor memory, where it runs at
+// the tensor cores' rate.  Per CTA (one per SM):
+//   shared memory : A (hi and lo 16-bit images, 128-byte swizzled, loaded by the
+//                   bulk-copy engine), the residual operand P (hi, lo), the DCT
+//   tensor memory : the accumulator (U, then G), Z hi and Z lo (GEMM1's A)
+//   registers     : s^{k-1} of the thread's 64 coefficients (the momentum state)
+// y is re-read from L2 each iteration, by coalesced asynchronous copies into the
+// P operand's slots while the tensor cores and the gradient step run.  The iterate z is kept as its hi + lo
+// halves (22 significant bits with fp16).  FP32-grade products use three MMAs
+// (hi.hi + lo.hi + hi.lo); mixed precision runs one (hi.hi) until its tail.
 //
-// Roles: warps 0-7 are the epilogue (TMEM lane quarter = warp % 4, column
-// half = warp / 4); warp 8 allocates TMEM, loads A and issues the MMAs.  Every
-// wait on an mbarrier is bounded; a wait that gives up sets the context's
-// error word and the CTA drains and exits without further work.
+// Roles: 16 warps; lane quarter (32 blocks) = warp % 4, column group = warp / 4
+// (64 coefficients of the gradient step in two slices of 32, a quarter of M16
+// in the residual step).  Thread 0 also loads A and issues the MMAs, between its own epilogue
+// phases (every phase waits on the previous one anyway); GEMM1 starts on the
+// first half of every column group as soon as all warps have written it.  One launch may carry several jobs (plans / GOP
+// calls of the same operand type); tiles are numbered across jobs and A is
+// reloaded when a CTA moves to another job.  Every mbarrier wait is bounded;
+// a wait that gives up sets the context's error word and the CTA drains.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <math.h>
@@ -34,59 +43,73 @@ namespace {
 
 using namespace tc;
 
-constexpr int kN = 256;              // coefficients per block (16 x 16 blocks)
-constexpr int kMPad = 128;           // rows of A kept on chip (M <= 128)
-constexpr int kTileBlocks = 64;      // blocks per tile = MMA N dimension
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = (kEpiWarps + 1) * 32;
-constexpr uint32_t kImgBytes = kMPad * kN * 2;          // one 16-bit image of A: 64 KB
-constexpr uint32_t kZBytes = kN * kTileBlocks * 2;      // 32 KB
-constexpr uint32_t kPBytes = kMPad * kTileBlocks * 2;   // 16 KB
-constexpr uint32_t kOffAHi = 0, kOffALo = kImgBytes;
-constexpr uint32_t kOffZHi = 2 * kImgBytes, kOffZLo = kOffZHi + kZBytes;
-constexpr uint32_t kOffPHi = kOffZLo + kZBytes, kOffPLo = kOffPHi + kPBytes;
-constexpr uint32_t kOffMisc = kOffPLo + kPBytes;        // 224 KB
+constexpr int kN = 256;               // coefficients per block (16 x 16 blocks)
+constexpr int kMaxM16 = 128;          // measurement rows kept on chip
+constexpr int kTile = 128;            // blocks per tile = TMEM lanes = MMA M
+constexpr int kEpiWarps = 16;
+constexpr int kThreads = kEpiWarps * 32;     // thread 0 also issues the MMAs
+constexpr int kPerThread = kN / 4;    // coefficients per epilogue thread
+constexpr uint32_t kAImgMax = kMaxM16 * kN * 2;         // 64 KB per 16-bit image
+constexpr uint32_t kPImg = kTile * kMaxM16 * 2;         // 32 KB per 16-bit image
+constexpr uint32_t kOffAHi = 0, kOffALo = kAImgMax;
+constexpr uint32_t kOffPHi = 2 * kAImgMax, kOffPLo = kOffPHi + kPImg;
+constexpr uint32_t kOffC = kOffPLo + kPImg;             // DCT matrix, 1 KB
+constexpr uint32_t kOffMisc = kOffC + 1024;
 constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024; // misc + alignment slack
-// TMEM columns
-constexpr uint32_t kColU = 0, kColY = 64, kColG = 128, kColZ = 256, kColS = 384;
+constexpr uint32_t kColAcc = 0, kColZHi = 256, kColZLo = 384;
 constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s per wait
 
-struct TcArgs {
-    const uint8_t* a_img;   // hi image then lo image, 2 x 64 KB
+struct Misc {
+    uint64_t bar_load, bar_u, bar_g, bar_p, bar_z0, bar_z1, bar_drain;
+    uint32_t tmem_base;
+    int abort;
+    uint32_t colmax[kTile];
+};
+
+}  // namespace
+
+// One job of a launch: the blocks of one cs_decode_gop call.
+struct TcJob {
+    const uint8_t* a_img;   // hi image then lo image, m16 x 512 bytes each
     const float* y;
     const uint8_t* keys;
     float* out_f32;
     uint8_t* out_u8;
     const float* dct;       // [16][16]
-    const float* beta;
-    int* err;
     GopShape gs;
-    long long rows;         // measured blocks in the call
-    int n_tiles;
+    long long rows;         // measured blocks
+    int tile_begin;         // first global tile of the job
+    int m16;                // M rounded up to 16
     int iters;
     int split_from;         // iterations k >= split_from use the 3-MMA split
-    float lambda_rel;
-    float inv_l;
-    float su;               // U = acc * su
-    float sg;               // G = acc * sg
-    float sp;               // P operand = P * sp
+    float lambda_rel, inv_l;
+    float su, sg, sp;       // U = acc su, G = acc sg, P operand = P sp
 };
 
-struct Misc {
-    uint64_t bar_load, bar_u, bar_g, bar_p, bar_z, bar_end;
-    uint32_t tmem_base;
-    int abort;
-    uint32_t colmax[kTileBlocks];
-    float tau[kTileBlocks];
+constexpr int kMaxJobs = 48;
+struct TcLaunch {
+    const float* beta;
+    int* err;
+    int n_jobs;
+    int n_tiles;
+    TcJob jobs[kMaxJobs];
 };
+
+namespace {
+
+__device__ __forceinline__ int job_of(const TcLaunch& L, int tile) {
+    int j = 0;
+    while (j + 1 < L.n_jobs && L.jobs[j + 1].tile_begin <= tile) ++j;
+    return j;
+}
 
 template <bool BF>
-__device__ __forceinline__ uint32_t pack2(float a, float b) {
+__device__ __forceinline__ uint32_t pack2(float2 v) {
     if constexpr (BF) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
         return *reinterpret_cast<uint32_t*>(&h);
     } else {
-        __half2 h = __floats2half2_rn(a, b);
+        __half2 h = __floats2half2_rn(v.x, v.y);
         return *reinterpret_cast<uint32_t*>(&h);
     }
 }
@@ -101,37 +124,6 @@ __device__ __forceinline__ float2 unpack2(uint32_t v) {
     }
 }
 
-// Write 32 values (blocks 32h .. 32h+31) of operand row `row` (8-row swizzle
-// atoms, one 128-byte row of 64 blocks) as hi and, if wanted, lo halves.
-template <bool BF>
-__device__ __forceinline__ void write_operand_row(uint8_t* hi_base, uint8_t* lo_base, int row,
-                                                  int half, const float (&v)[32], bool want_lo) {
-    const uint32_t r = row & 7;
-    uint8_t* hrow = hi_base + (row >> 3) * 1024 + r * 128;
-    uint8_t* lrow = lo_base + (row >> 3) * 1024 + r * 128;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const uint32_t chunk = (uint32_t)(4 * half + c);
-        uint32_t h[4], l[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const float a = v[8 * c + 2 * e], b = v[8 * c + 2 * e + 1];
-            h[e] = pack2<BF>(a, b);
-            if (want_lo) {
-                const float2 hf = unpack2<BF>(h[e]);
-                l[e] = pack2<BF>(a - hf.x, b - hf.y);
-            }
-        }
-        const uint32_t off = ((chunk ^ r) << 4);
-        *reinterpret_cast<uint4*>(hrow + off) = make_uint4(h[0], h[1], h[2], h[3]);
-        if (want_lo) *reinterpret_cast<uint4*>(lrow + off) = make_uint4(l[0], l[1], l[2], l[3]);
-    }
-}
-
-__device__ __forceinline__ void epi_barrier() {
-    asm volatile("bar.sync 1, %0;" ::"r"(kEpiWarps * 32) : "memory");
-}
-
 // Bounded wait; once any wait in the CTA has given up, later waits return at
 // once so that every role drains through the same control flow.
 __device__ __forceinline__ bool wait_bar(Misc* ms, uint64_t* bar, uint32_t parity, int* err) {
@@ -142,25 +134,107 @@ __device__ __forceinline__ bool wait_bar(Misc* ms, uint64_t* bar, uint32_t parit
     return false;
 }
 
+// Coefficients of an epilogue thread: two slices of 32, 32 c .. 32 c + 31 (half
+// 0) and 128 + 32 c .. (half 1), in chunks of 8.  Half 0 of all column groups
+// covers accumulator columns 0 .. 127, so once it is done GEMM1 may overwrite
+// them (U needs at most M16 <= 128 columns) while half 1 is still being read.
+__device__ __forceinline__ int coef_of(int cgrp, int half, int chunk) {
+    return 128 * half + 32 * cgrp + 8 * chunk;
+}
+
+__device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) {
+    return make_float2(__uint_as_float(a), __uint_as_float(b));
+}
+
+// Byte offset of the 8-byte granule holding elements k..k+3 (k % 4 == 0) of
+// row `row` in a K-major operand of `row_groups` 8-row groups, 128-byte swizzle.
+__device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t k, uint32_t row_groups) {
+    const uint32_t r = row & 7;
+    return ((k >> 6) * row_groups + (row >> 3)) * 1024u + r * 128u + ((((k & 63) >> 3) ^ r) << 4) +
+           ((k & 7) << 1);
+}
+
+// Stage the tile's y in the slots of the P operand, which are free between
+// GEMM2's completion and the next residual step.  y[b][m] goes to the slot the
+// residual step of block b later overwrites with P[b][m]: elements m, m+1 of
+// each 4-element granule to the P hi granule, m+2, m+3 to the P lo granule.
+// Warp wi of nw copies rows wi, wi + nw, ...; its lanes read consecutive m.
+__device__ __forceinline__ void stage_y(uint8_t* p_hi, uint8_t* p_lo, const float* y_tile,
+                                        long long rows_left, int m_rows, int wi, int lane, int nw) {
+    const int nrows = rows_left < kTile ? (int)rows_left : kTile;
+    for (int b = wi; b < nrows; b += nw) {
+        const float* src = y_tile + (long long)b * m_rows;
+        for (int m = lane; m < m_rows; m += 32) {
+            const uint32_t off = kmajor_off((uint32_t)b, (uint32_t)(m & ~3), kTile / 8);
+            cp_async4(((m & 2) ? p_lo : p_hi) + off + 4 * (m & 1), src + m, true);
+        }
+    }
+    cp_async_commit();
+}
+
+// GEMM1 for one half of K (h = 0: coefficients 0 .. 127, h = 1: 128 .. 255),
+// issued by the single MMA thread.
 template <bool BF>
-__global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const TcArgs args) {
+__device__ __forceinline__ void issue_gemm1_half(uint32_t tbase, uint32_t s_base, int m16, int h,
+                                                 bool split) {
+    const uint32_t rg = (uint32_t)(m16 / 8);
+    const uint64_t d_hi = desc_sw128(s_base + kOffAHi, 16, 1024);
+    const uint64_t d_lo = desc_sw128(s_base + kOffALo, 16, 1024);
+    const uint32_t id1 = idesc_f16(128, (uint32_t)m16, BF ? 1u : 0u, 0u, 0u);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint32_t ks = (uint32_t)(8 * h + j);
+        const uint32_t n0 = 16 * ks;
+        const uint32_t b16 = ((n0 >> 6) * rg * 1024 + ((n0 & 63) >> 4) * 32) >> 4;
+        const uint32_t zh = tbase + kColZHi + 8 * ks;
+        const uint32_t zl = tbase + kColZLo + 8 * ks;
+        mma_f16_tmem_a(tbase + kColAcc, zh, d_hi + b16, id1, (h | j) != 0);
+        if (split) {
+            mma_f16_tmem_a(tbase + kColAcc, zl, d_hi + b16, id1, 1);
+            mma_f16_tmem_a(tbase + kColAcc, zh, d_lo + b16, id1, 1);
+        }
+    }
+}
+
+// GEMM2: G = P A at N = 256, K = m16.
+template <bool BF>
+__device__ __forceinline__ void issue_gemm2(uint32_t tbase, uint32_t s_base, int m16, bool split) {
+    const uint64_t dp_hi = desc_sw128(s_base + kOffPHi, 16, 1024);
+    const uint64_t dp_lo = desc_sw128(s_base + kOffPLo, 16, 1024);
+    const uint64_t da_hi = desc_sw128(s_base + kOffAHi, (uint32_t)(m16 / 8) * 1024, 1024);
+    const uint64_t da_lo = desc_sw128(s_base + kOffALo, (uint32_t)(m16 / 8) * 1024, 1024);
+    const uint32_t id2 = idesc_f16(128, kN, BF ? 1u : 0u, 0u, 1u);
+    for (int ks = 0; ks < m16 / 16; ++ks) {
+        const uint32_t m0 = 16 * (uint32_t)ks;
+        const uint32_t a16 = ((m0 >> 6) * (kTile / 8) * 1024 + ((m0 & 63) >> 4) * 32) >> 4;
+        const uint32_t b16 = ((m0 >> 3) * 1024) >> 4;
+        mma_f16(tbase + kColAcc, dp_hi + a16, da_hi + b16, id2, ks > 0);
+        if (split) {
+            mma_f16(tbase + kColAcc, dp_lo + a16, da_hi + b16, id2, 1);
+            mma_f16(tbase + kColAcc, dp_hi + a16, da_lo + b16, id2, 1);
+        }
+    }
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant__ TcLaunch L) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
     Misc* ms = reinterpret_cast<Misc*>(sm + kOffMisc);
+    float* c_s = reinterpret_cast<float*>(sm + kOffC);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const GopShape& gs = args.gs;
-    const int m_rows = gs.m;
-    const int k_steps2 = (m_rows + 15) / 16;
+    const bool issuer = threadIdx.x == 0;   // the one thread that issues MMAs and copies
 
-    if (warp == kEpiWarps) {
+    if (warp == 0) {
         if (lane == 0) {
             mbar_init(&ms->bar_load, 1);
             mbar_init(&ms->bar_u, 1);
             mbar_init(&ms->bar_g, 1);
             mbar_init(&ms->bar_p, kEpiWarps);
-            mbar_init(&ms->bar_z, kEpiWarps);
-            mbar_init(&ms->bar_end, 1);
+            mbar_init(&ms->bar_z0, kEpiWarps);
+            mbar_init(&ms->bar_z1, kEpiWarps);
+            mbar_init(&ms->bar_drain, 1);
             ms->abort = 0;
             fence_mbar_init();
         }
@@ -168,253 +242,262 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const TcArgs args) {
         tmem_alloc(&ms->tmem_base, 512);
         tmem_relinquish();
     }
+    for (int i = threadIdx.x; i < 256; i += kThreads) c_s[i] = L.jobs[0].dct[i];
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     const uint32_t tbase = ms->tmem_base;
+    const uint32_t s_base = smem_u32(sm);
 
-    if (warp == kEpiWarps) {
-        // ------------------------------ MMA issuer ------------------------------
-        if (lane == 0) {
-            mbar_arrive_expect_tx(&ms->bar_load, 2 * kImgBytes);
-            for (uint32_t off = 0; off < 2 * kImgBytes; off += 32768)
-                bulk_g2s(sm + kOffAHi + off, args.a_img + off, 32768, &ms->bar_load);
-            bool ok = wait_bar(ms, &ms->bar_load, 0, args.err);
-            const uint32_t s_base = smem_u32(sm);
-            const uint32_t id1 = idesc_f16(128, kTileBlocks, BF ? 1u : 0u, 0u, 1u);
-            const uint32_t id2 = idesc_f16(128, kTileBlocks, BF ? 1u : 0u, 1u, 1u);
-            uint32_t phase_z = 0, phase_p = 0;
-            for (int tile = blockIdx.x; tile < args.n_tiles; tile += gridDim.x) {
-                for (int k = 0; k < args.iters; ++k) {
-                    const bool split = k >= args.split_from;
-                    ok = wait_bar(ms, &ms->bar_z, phase_z, args.err) && ok;
-                    phase_z ^= 1;
-                    fence_after_sync();
-                    if (ok) {
-                        for (int ks = 0; ks < kN / 16; ++ks) {
-                            const int n0 = 16 * ks;
-                            const uint32_t a_off = (n0 / 64) * (kMPad / 8) * 1024 + ((n0 % 64) / 16) * 32;
-                            const uint32_t z_off = (n0 / 8) * 1024;
-                            const uint64_t ahi = desc_sw128(s_base + kOffAHi + a_off, 16, 1024);
-                            const uint64_t zhi = desc_sw128(s_base + kOffZHi + z_off, 1024, 1024);
-                            mma_f16(tbase + kColU, ahi, zhi, id1, ks > 0);
-                            if (split) {
-                                const uint64_t alo = desc_sw128(s_base + kOffALo + a_off, 16, 1024);
-                                const uint64_t zlo = desc_sw128(s_base + kOffZLo + z_off, 1024, 1024);
-                                mma_f16(tbase + kColU, ahi, zlo, id1, 1);
-                                mma_f16(tbase + kColU, alo, zhi, id1, 1);
-                            }
-                        }
-                        mma_commit(&ms->bar_u);
-                    }
-                    ok = wait_bar(ms, &ms->bar_p, phase_p, args.err) && ok;
-                    phase_p ^= 1;
-                    fence_after_sync();
-                    if (ok) {
-                        for (int slab = 0; slab < kN / 128; ++slab) {
-                            for (int ks = 0; ks < k_steps2; ++ks) {
-                                const uint32_t a_off = (2 * slab) * (kMPad / 8) * 1024 + (2 * ks) * 1024;
-                                const uint32_t p_off = (2 * ks) * 1024;
-                                const uint64_t ahi =
-                                    desc_sw128(s_base + kOffAHi + a_off, (kMPad / 8) * 1024, 1024);
-                                const uint64_t phi = desc_sw128(s_base + kOffPHi + p_off, 1024, 1024);
-                                const uint32_t d = tbase + kColG + 64 * slab;
-                                mma_f16(d, ahi, phi, id2, ks > 0);
-                                if (split) {
-                                    const uint64_t alo =
-                                        desc_sw128(s_base + kOffALo + a_off, (kMPad / 8) * 1024, 1024);
-                                    const uint64_t plo = desc_sw128(s_base + kOffPLo + p_off, 1024, 1024);
-                                    mma_f16(d, ahi, plo, id2, 1);
-                                    mma_f16(d, alo, phi, id2, 1);
-                                }
-                            }
-                        }
-                        mma_commit(&ms->bar_g);
-                    }
-                }
-            }
-            // drain: every MMA issued so far has completed before TMEM is freed
-            mma_commit(&ms->bar_end);
-            mbar_wait(&ms->bar_end, 0, kWaitNs);
-            if (!ok) mbar_wait(&ms->bar_load, 0, kWaitNs);  // the A copy, if it never landed
+    const int q = warp & 3, cgrp = warp >> 2;
+    const int blk = 32 * q + lane;                          // TMEM lane = block of the tile
+    const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
+    uint8_t* p_hi = sm + kOffPHi;
+    uint8_t* p_lo = sm + kOffPLo;
+    uint32_t ph_u = 0, ph_g = 0;                            // every thread
+    uint32_t ph_z0 = 0, ph_z1 = 0, ph_p = 0, ph_load = 0;   // the issuer only
+    bool ok = true;
+    int cur = -1;
+    for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
+        const int jid = job_of(L, tile);
+        const TcJob& J = L.jobs[jid];
+        const GopShape& gs = J.gs;
+        const long long row = (long long)(tile - J.tile_begin) * kTile + blk;
+        const bool live = row < J.rows;
+        const int mq = J.m16 / 4;                           // residual rows of this thread
+        const int mbase = cgrp * mq;
+        const float2 ginv2 = make_float2(-J.sg * J.inv_l, -J.sg * J.inv_l);
+        float2 sp[kPerThread / 2];
+#pragma unroll
+        for (int i = 0; i < kPerThread / 2; ++i) sp[i] = make_float2(0.f, 0.f);
+        float tau = 0.f;
+        // --- tile init: Z = 0 in TMEM ---
+        {
+            uint32_t zr[32];
+#pragma unroll
+            for (int i = 0; i < 32; ++i) zr[i] = 0u;
+            tmem_st32(lane_addr + kColZHi + 32 * cgrp, zr);
+            tmem_st32(lane_addr + kColZLo + 32 * cgrp, zr);
+            if (cgrp == 0) ms->colmax[blk] = 0u;
+            tmem_wait_st();
         }
-        __syncwarp();
-    } else {
-        // ------------------------------ epilogue ------------------------------
-        const int q = warp & 3, half = warp >> 2;
-        const int lrow = 32 * q + lane;                     // TMEM lane of this thread
-        const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
-        uint8_t* z_hi = sm + kOffZHi;
-        uint8_t* z_lo = sm + kOffZLo;
-        uint8_t* p_hi = sm + kOffPHi;
-        uint8_t* p_lo = sm + kOffPLo;
-        const float ginv = args.sg * args.inv_l;
-        uint32_t phase_u = 0, phase_g = 0;
-        for (int tile = blockIdx.x; tile < args.n_tiles; tile += gridDim.x) {
-            const long long row0 = (long long)tile * kTileBlocks;
-            // --- tile init: Y, Z = S = 0 in TMEM, Z operand = 0 ---
-            {
-                uint32_t r[32];
+        // P slots start at zero (padding rows m >= M and absent blocks stay zero:
+        // their U and y are zero), then y is staged for the first residual step
+        const long long tile_row0 = (long long)(tile - J.tile_begin) * kTile;
+        const float* y_tile = J.y + tile_row0 * gs.m;
+        for (int i = threadIdx.x; i < (int)(2 * kPImg / 16); i += kThreads)
+            reinterpret_cast<uint4*>(p_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+        if (J.iters > 0) stage_y(p_hi, p_lo, y_tile, J.rows - tile_row0, gs.m, warp, lane, kEpiWarps);
+        fence_before_sync();
+        __syncthreads();   // also: every MMA of the previous tile has completed (its last G was waited)
+        fence_after_sync();
+        if (issuer) {
+            if (jid != cur) {
+                const uint32_t img = (uint32_t)J.m16 * kN * 2;
+                mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
+                bulk_g2s(sm + kOffAHi, J.a_img, img, &ms->bar_load);
+                bulk_g2s(sm + kOffALo, J.a_img + img, img, &ms->bar_load);
+                ok = wait_bar(ms, &ms->bar_load, ph_load, L.err) && ok;
+                ph_load ^= 1;
+                cur = jid;
+            }
+            if (J.iters > 0 && ok) {
+                issue_gemm1_half<BF>(tbase, s_base, J.m16, 0, 0 >= J.split_from);
+                issue_gemm1_half<BF>(tbase, s_base, J.m16, 1, 0 >= J.split_from);
+                mma_commit(&ms->bar_u);
+            }
+        }
+        for (int k = 0; k < J.iters; ++k) {
+            const float bk = L.beta[k];
+            // --- residual P = U - y (this thread: rows mbase .. mbase + mq) ---
+            const bool ok_u = wait_bar(ms, &ms->bar_u, ph_u, L.err);
+            ph_u ^= 1;
+            fence_after_sync();
+            cp_async_wait_all();   // this thread's share of y has landed ...
+            __syncthreads();       // ... and so has everyone else's
+            const float2 su2 = make_float2(J.su, J.su), sp2 = make_float2(J.sp, J.sp);
+            const bool p_split = k >= J.split_from;
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const long long row = row0 + 32 * half + j;
-                    float v = 0.f;
-                    if (lrow < m_rows && row < args.rows) v = args.y[row * m_rows + lrow];
-                    r[j] = __float_as_uint(v);
+            for (int g4 = 0; g4 < kMaxM16 / 16; ++g4) {
+                if (4 * g4 < mq) {
+                    uint32_t u[4];
+                    tmem_ld4(lane_addr + kColAcc + mbase + 4 * g4, u);
+                    const uint32_t off =
+                        kmajor_off((uint32_t)blk, (uint32_t)(mbase + 4 * g4), kTile / 8);
+                    const float2 y01 = *reinterpret_cast<const float2*>(p_hi + off);
+                    const float2 y23 = *reinterpret_cast<const float2*>(p_lo + off);
+                    tmem_wait_ld();
+                    const float2 p0 = mul2(sub2(mul2(u2f2(u[0], u[1]), su2), y01), sp2);
+                    const float2 p1 = mul2(sub2(mul2(u2f2(u[2], u[3]), su2), y23), sp2);
+                    const uint32_t h0 = pack2<BF>(p0), h1 = pack2<BF>(p1);
+                    if (ok_u) {
+                        *reinterpret_cast<uint2*>(p_hi + off) = make_uint2(h0, h1);
+                        if (p_split) {
+                            const uint32_t l0 = pack2<BF>(sub2(p0, unpack2<BF>(h0)));
+                            const uint32_t l1 = pack2<BF>(sub2(p1, unpack2<BF>(h1)));
+                            *reinterpret_cast<uint2*>(p_lo + off) = make_uint2(l0, l1);
+                        }
+                    }
                 }
-                tmem_st32(lane_addr + kColY + 32 * half, r);
-#pragma unroll
-                for (int j = 0; j < 32; ++j) r[j] = 0u;
-                for (int slab = 0; slab < 2; ++slab) {
-                    tmem_st32(lane_addr + kColZ + 64 * slab + 32 * half, r);
-                    tmem_st32(lane_addr + kColS + 64 * slab + 32 * half, r);
-                }
-                const float zero[32] = {};
-                for (int slab = 0; slab < 2; ++slab)
-                    write_operand_row<BF>(z_hi, z_lo, 128 * slab + lrow, half, zero, true);
-                if (threadIdx.x < kTileBlocks) ms->colmax[threadIdx.x] = 0u;
-                tmem_wait_st();
             }
             fence_proxy_async_smem();
             fence_before_sync();
-            epi_barrier();
-            if (args.iters > 0) {
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&ms->bar_z);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ms->bar_p);
+            if (issuer) {
+                ok = wait_bar(ms, &ms->bar_p, ph_p, L.err) && ok;
+                ph_p ^= 1;
+                fence_after_sync();
+                if (ok) {
+                    issue_gemm2<BF>(tbase, s_base, J.m16, p_split);
+                    mma_commit(&ms->bar_g);
+                }
             }
-            for (int k = 0; k < args.iters; ++k) {
-                // --- P = U - Y, as the MMA operand of GEMM2 ---
-                const bool ok_u = wait_bar(ms, &ms->bar_u, phase_u, args.err);
-                phase_u ^= 1;
-                fence_after_sync();
-                {
-                    uint32_t u[32], yv[32];
-                    tmem_ld32(lane_addr + kColU + 32 * half, u);
-                    tmem_ld32(lane_addr + kColY + 32 * half, yv);
-                    tmem_wait_ld();
-                    float p[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j)
-                        p[j] = (__uint_as_float(u[j]) * args.su - __uint_as_float(yv[j])) * args.sp;
-                    if (ok_u) write_operand_row<BF>(p_hi, p_lo, lrow, half, p, k >= args.split_from);
-                }
-                fence_proxy_async_smem();
-                fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&ms->bar_p);
 
-                // --- gradient step, soft threshold, momentum ---
-                const bool ok_g = wait_bar(ms, &ms->bar_g, phase_g, args.err);
-                phase_g ^= 1;
-                fence_after_sync();
-                if (k == 0) {
-                    // lambda_b = lambda_rel ||A^T y_b||_inf; here G = -A^T y
-                    for (int slab = 0; slab < 2; ++slab) {
-                        uint32_t g[32];
-                        tmem_ld32(lane_addr + kColG + 64 * slab + 32 * half, g);
-                        tmem_wait_ld();
+            // --- gradient step, soft threshold, momentum ---
+            const bool ok_g = wait_bar(ms, &ms->bar_g, ph_g, L.err);
+            ph_g ^= 1;
+            fence_after_sync();
+
+            if (k == 0) {
+                // lambda_b = lambda_rel ||A^T y_b||_inf; at k = 0, G = -A^T y
+                float mx = 0.f;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const float a = fabsf(__uint_as_float(g[j]) * args.sg);
-                            const uint32_t mx = __reduce_max_sync(0xffffffffu, __float_as_uint(a));
-                            if (lane == 0) atomicMax(&ms->colmax[32 * half + j], mx);
-                        }
-                    }
-                    epi_barrier();
-                    if (threadIdx.x < kTileBlocks)
-                        ms->tau[threadIdx.x] =
-                            args.lambda_rel * __uint_as_float(ms->colmax[threadIdx.x]) * args.inv_l;
-                    epi_barrier();
-                }
-                const float bk = args.beta[k];
-                const bool want_z = k + 1 < args.iters;
-                const bool z_split = k + 1 >= args.split_from;
-                for (int slab = 0; slab < 2; ++slab) {
-                    uint32_t g[32], z[32], s[32];
-                    tmem_ld32(lane_addr + kColG + 64 * slab + 32 * half, g);
-                    tmem_ld32(lane_addr + kColZ + 64 * slab + 32 * half, z);
-                    tmem_ld32(lane_addr + kColS + 64 * slab + 32 * half, s);
+                for (int ch = 0; ch < kPerThread / 8; ++ch) {
+                    uint32_t g[8];
+                    tmem_ld8(lane_addr + kColAcc + coef_of(cgrp, ch >> 2, ch & 3), g);
                     tmem_wait_ld();
-                    float zn[32];
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float tau = ms->tau[32 * half + j];
-                        const float v = fmaf(-__uint_as_float(g[j]), ginv, __uint_as_float(z[j]));
-                        const float sv = v - fminf(fmaxf(v, -tau), tau);
-                        const float znew = fmaf(bk, sv - __uint_as_float(s[j]), sv);
-                        zn[j] = znew;
-                        z[j] = __float_as_uint(znew);
-                        s[j] = __float_as_uint(sv);
+                    for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(__uint_as_float(g[i])));
+                }
+                atomicMax(&ms->colmax[blk], __float_as_uint(mx * J.sg));
+                __syncthreads();
+                tau = J.lambda_rel * __uint_as_float(ms->colmax[blk]) * J.inv_l;
+            }
+            const bool want_z = k + 1 < J.iters;
+            const bool z_split = k + 1 >= J.split_from;
+            const float2 b2 = make_float2(bk, bk);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int ch = 0; ch < 4; ++ch) {
+                    const int o = coef_of(cgrp, h, ch);               // first coefficient
+                    uint32_t g[8], zh[4], zl[4];
+                    tmem_ld8(lane_addr + kColAcc + o, g);
+                    tmem_ld4(lane_addr + kColZHi + o / 2, zh);
+                    tmem_ld4(lane_addr + kColZLo + o / 2, zl);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int si = 16 * h + 4 * ch + e;
+                        const float2 zhf = unpack2<BF>(zh[e]), zlf = unpack2<BF>(zl[e]);
+                        const float2 z2 = make_float2(zhf.x + zlf.x, zhf.y + zlf.y);
+                        const float2 v = fma2(u2f2(g[2 * e], g[2 * e + 1]), ginv2, z2);
+                        const float2 cl = make_float2(fminf(fmaxf(v.x, -tau), tau),
+                                                      fminf(fmaxf(v.y, -tau), tau));
+                        const float2 sv = sub2(v, cl);
+                        const float2 zn = fma2(b2, sub2(sv, sp[si]), sv);
+                        sp[si] = sv;
+                        zh[e] = pack2<BF>(zn);
+                        zl[e] = pack2<BF>(sub2(zn, unpack2<BF>(zh[e])));
                     }
-                    tmem_st32(lane_addr + kColZ + 64 * slab + 32 * half, z);
-                    tmem_st32(lane_addr + kColS + 64 * slab + 32 * half, s);
-                    if (want_z && ok_g) write_operand_row<BF>(z_hi, z_lo, 128 * slab + lrow, half, zn, z_split);
+                    if (want_z && ok_g) {
+                        tmem_st4(lane_addr + kColZHi + o / 2, zh);
+                        tmem_st4(lane_addr + kColZLo + o / 2, zl);
+                    }
                 }
                 tmem_wait_st();
                 if (want_z) {
-                    fence_proxy_async_smem();
                     fence_before_sync();
                     __syncwarp();
-                    if (lane == 0) mbar_arrive(&ms->bar_z);
-                }
-            }
-            // --- reconstruct: S (= s^K) -> R = C^T S C, add the key, store ---
-            epi_barrier();   // the operand area is free: no MMA is pending for this tile
-            float* s_f = reinterpret_cast<float*>(sm + kOffZHi);          // [64][256]
-            float* c_s = reinterpret_cast<float*>(sm + kOffPHi);          // [16][16]
-            float* t_w = c_s + 256 + warp * 256;                          // per-warp [16][16]
-            for (int slab = 0; slab < 2; ++slab) {
-                uint32_t s[32];
-                tmem_ld32(lane_addr + kColS + 64 * slab + 32 * half, s);
-                tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 32; ++j)
-                    s_f[(32 * half + j) * kN + 128 * slab + lrow] = __uint_as_float(s[j]);
-            }
-            for (int i = threadIdx.x; i < 256; i += kEpiWarps * 32) c_s[i] = args.dct[i];
-            epi_barrier();
-            const size_t frame_px = (size_t)gs.h * gs.w;
-            for (int bl = warp; bl < kTileBlocks; bl += kEpiWarps) {
-                const long long row = row0 + bl;
-                if (row >= args.rows) break;
-                const float* sb = s_f + bl * kN;
-                const int qc = lane & 15, r0 = lane >> 4;
-                // T = S C (rows k = r0, r0+2, ...)
-#pragma unroll
-                for (int kk = r0; kk < 16; kk += 2) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int l = 0; l < 16; ++l) acc = fmaf(sb[kk * 16 + l], c_s[l * 16 + qc], acc);
-                    t_w[kk * 16 + qc] = acc;
-                }
-                __syncwarp();
-                const int c = (int)(row / gs.nblk), blk = (int)(row % gs.nblk);
-                const int g = c / (gs.g - 1);
-                const int bi = blk / gs.nbc, bj = blk % gs.nbc;
-#pragma unroll
-                for (int pp = r0; pp < 16; pp += 2) {
-                    float acc = 0.f;
-#pragma unroll
-                    for (int kk = 0; kk < 16; ++kk) acc = fmaf(c_s[kk * 16 + pp], t_w[kk * 16 + qc], acc);
-                    const int py = bi * 16 + pp, px = bj * 16 + qc;
-                    if (py < gs.h && px < gs.w) {
-                        const size_t off = (size_t)py * gs.w + px;
-                        const float v = (float)args.keys[(size_t)g * frame_px + off] + acc;
-                        if (args.out_f32) args.out_f32[(size_t)c * frame_px + off] = v;
-                        if (args.out_u8)
-                            args.out_u8[(size_t)c * frame_px + off] =
-                                (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
+                    if (lane == 0) mbar_arrive(h ? &ms->bar_z1 : &ms->bar_z0);
+                    if (issuer) {
+                        ok = wait_bar(ms, h ? &ms->bar_z1 : &ms->bar_z0, h ? ph_z1 : ph_z0, L.err) && ok;
+                        if (h) ph_z1 ^= 1; else ph_z0 ^= 1;
+                        fence_after_sync();
+                        if (ok) {
+                            issue_gemm1_half<BF>(tbase, s_base, J.m16, h, z_split);
+                            if (h) mma_commit(&ms->bar_u);
+                        }
                     }
                 }
-                __syncwarp();
             }
-            epi_barrier();   // s_f / c_s are overwritten by the next tile's init
+            // GEMM2 has consumed P: stage y for the next residual step in its slots,
+            // while GEMM1 runs (warp 0, which issues the MMAs, stages nothing)
+            if (k + 1 < J.iters && warp > 0)
+                stage_y(p_hi, p_lo, y_tile, J.rows - tile_row0, gs.m, warp - 1, lane, kEpiWarps - 1);
         }
+        // --- reconstruct: R = C^T S C, S = s^K (rows 4 cgrp .. 4 cgrp + 3 here) ---
+        fence_before_sync();
+        __syncthreads();   // every MMA of the tile has completed: the accumulator is free
+        fence_after_sync();
+#pragma unroll
+        for (int kr = 0; kr < 4; ++kr) {
+            // this thread holds S rows 2 cgrp, 2 cgrp + 1, 8 + 2 cgrp, 9 + 2 cgrp;
+            // row (kr) = slice kr / 2, chunks 2 (kr % 2) and 2 (kr % 2) + 1
+            uint32_t t[16];
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) {
+                float acc = 0.f;
+#pragma unroll
+                for (int l = 0; l < 16; l += 2) {
+                    const float2 s2 = sp[16 * (kr >> 1) + 8 * (kr & 1) + l / 2];
+                    acc = fmaf(s2.x, c_s[l * 16 + qq], acc);
+                    acc = fmaf(s2.y, c_s[(l + 1) * 16 + qq], acc);
+                }
+                t[qq] = __float_as_uint(acc);
+            }
+            const int krow = 8 * (kr >> 1) + 2 * cgrp + (kr & 1);
+            tmem_st16(lane_addr + kColAcc + 16 * krow, t);
+        }
+        tmem_wait_st();
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        const int c_idx = live ? (int)(row / gs.nblk) : 0, bl = live ? (int)(row % gs.nblk) : 0;
+        const int g_key = c_idx / (gs.g - 1);
+        const int bi = bl / gs.nbc, bj = bl % gs.nbc;
+        const size_t frame_px = (size_t)gs.h * gs.w;
+        for (int pr = 0; pr < 4; ++pr) {                   // output rows 4 cgrp + pr
+            float r[16];
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) r[qq] = 0.f;
+            for (int kr = 0; kr < 16; ++kr) {
+                uint32_t t[16];
+                tmem_ld16(lane_addr + kColAcc + 16 * kr, t);
+                tmem_wait_ld();
+                const float cv = c_s[kr * 16 + 4 * cgrp + pr];
+#pragma unroll
+                for (int qq = 0; qq < 16; ++qq) r[qq] = fmaf(cv, __uint_as_float(t[qq]), r[qq]);
+            }
+            const int py = bi * 16 + 4 * cgrp + pr;
+            if (!live || py >= gs.h) continue;
+#pragma unroll
+            for (int qq = 0; qq < 16; ++qq) {
+                const int px = bj * 16 + qq;
+                if (px >= gs.w) continue;
+                const size_t off = (size_t)py * gs.w + px;
+                const float v = (float)J.keys[(size_t)g_key * frame_px + off] + r[qq];
+                if (J.out_f32) J.out_f32[(size_t)c_idx * frame_px + off] = v;
+                if (J.out_u8)
+                    J.out_u8[(size_t)c_idx * frame_px + off] = (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
+            }
+        }
+        fence_before_sync();
+        __syncthreads();   // the accumulator (holding T) is reused by the next tile
+        fence_after_sync();
+    }
+    if (issuer) {
+        // drain: every MMA issued so far has completed before TMEM is freed
+        mma_commit(&ms->bar_drain);
+        mbar_wait(&ms->bar_drain, 0, kWaitNs);
+        if (!ok) mbar_wait(&ms->bar_load, ph_load, kWaitNs);
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (warp == kEpiWarps) tmem_dealloc(tbase, 512);
+    if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
 // Scales of the fp16 operands: max |A| and max_m sum_n |Phi[m][n]|.
@@ -448,29 +531,33 @@ __global__ void k_tc_ranges(const float* __restrict__ a, const float* __restrict
     }
 }
 
-// The four 64 KB shared-memory images of A * 2^ea: fp16 hi, fp16 lo, bf16 hi,
-// bf16 lo, rows >= M zero, 128-byte swizzled as in the kernel.
+// The four shared-memory images of A * 2^ea: fp16 hi, fp16 lo, bf16 hi, bf16
+// lo, each m16 rows x 256, rows >= M zero, 128-byte swizzled atoms of 8 rows x
+// 64 columns (atom (col/64, row/8) at ((col/64) * m16/8 + row/8) * 1024).
 __global__ void k_tc_images(const float* __restrict__ a, uint8_t* __restrict__ img, int n, int m,
-                            float scale) {
+                            int m16, float scale) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= kMPad * kN) return;
+    if (idx >= m16 * kN) return;
     const int row = idx / kN, col = idx % kN;
     const float v = row < m ? a[(size_t)row * n + col] * scale : 0.f;
-    const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)col, kMPad / 8);
+    const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)col, (uint32_t)m16 / 8);
+    const size_t img_bytes = (size_t)m16 * kN * 2;
     const __half hh = __float2half_rn(v);
     const __half hl = __float2half_rn(v - __half2float(hh));
     const __nv_bfloat16 bh = __float2bfloat16_rn(v);
     const __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(bh));
     *reinterpret_cast<__half*>(img + off) = hh;
-    *reinterpret_cast<__half*>(img + kImgBytes + off) = hl;
-    *reinterpret_cast<__nv_bfloat16*>(img + 2 * kImgBytes + off) = bh;
-    *reinterpret_cast<__nv_bfloat16*>(img + 3 * kImgBytes + off) = bl;
+    *reinterpret_cast<__half*>(img + img_bytes + off) = hl;
+    *reinterpret_cast<__nv_bfloat16*>(img + 2 * img_bytes + off) = bh;
+    *reinterpret_cast<__nv_bfloat16*>(img + 3 * img_bytes + off) = bl;
 }
+
+int m16_of(int m) { return (m + 15) / 16 * 16; }
 
 }  // namespace
 
-bool tc_plan_supported(int n, int m) { return n == kN && m >= 1 && m <= kMPad; }
-size_t tc_operand_bytes() { return 4ull * kImgBytes; }
+bool tc_plan_supported(int n, int m) { return n == kN && m >= 1 && m <= kMaxM16; }
+size_t tc_operand_bytes(int m) { return 4ull * (size_t)m16_of(m) * kN * 2; }
 
 cudaError_t launch_tc_ranges(const float* a, const float* phi, int n, int m, float* out,
                              cudaStream_t s) {
@@ -479,8 +566,9 @@ cudaError_t launch_tc_ranges(const float* a, const float* phi, int n, int m, flo
 }
 
 cudaError_t launch_tc_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s) {
-    const int total = kMPad * kN;
-    k_tc_images<<<(total + 255) / 256, 256, 0, s>>>(a, img, n, m, ldexpf(1.f, ea));
+    const int m16 = m16_of(m);
+    const int total = m16 * kN;
+    k_tc_images<<<(total + 255) / 256, 256, 0, s>>>(a, img, n, m, m16, ldexpf(1.f, ea));
     return cudaGetLastError();
 }
 
@@ -489,47 +577,72 @@ bool tc_supported(const cs_plan* plan, int precision) {
     return plan->a_tc != nullptr && tc_plan_supported(plan->n, plan->m);
 }
 
-cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s) {
-    const GopShape& gs = d.gs;
-    const long long rows = (long long)gs.n_cs * gs.nblk;
-    if (rows == 0) return cudaSuccess;
+static void fill_job(const DecodeArgs& d, int tile_begin, TcJob* J, bool* bf) {
     const cs_plan* p = d.plan;
-    TcArgs a;
-    const bool bf = d.precision == CS_BF16 || d.precision == CS_BF16X2;
-    a.a_img = p->a_tc + (bf ? 2 * kImgBytes : 0);
-    a.y = d.y;
-    a.keys = d.key;
-    a.out_f32 = d.out_f32;
-    a.out_u8 = d.out_u8;
-    a.dct = p->dct;
-    a.beta = d.beta;
-    a.err = p->ctx->err_dev;
-    a.gs = gs;
-    a.rows = rows;
-    a.n_tiles = (int)((rows + kTileBlocks - 1) / kTileBlocks);
-    a.iters = d.iters;
+    const GopShape& gs = d.gs;
+    *bf = d.precision == CS_BF16 || d.precision == CS_BF16X2;
+    const int m16 = m16_of(p->m);
+    const size_t img = (size_t)m16 * kN * 2;
+    J->a_img = p->a_tc + (*bf ? 2 * img : 0);
+    J->y = d.y;
+    J->keys = d.key;
+    J->out_f32 = d.out_f32;
+    J->out_u8 = d.out_u8;
+    J->dct = p->dct;
+    J->gs = gs;
+    J->rows = (long long)gs.n_cs * gs.nblk;
+    J->tile_begin = tile_begin;
+    J->m16 = m16;
+    J->iters = d.iters;
     const bool mixed = d.precision == CS_BF16 || d.precision == CS_FP16;
-    a.split_from = mixed ? (d.iters > d.tail_iters ? d.iters - d.tail_iters : 0) : 0;
-    a.lambda_rel = d.lambda_rel;
-    a.inv_l = (float)(1.0 / p->lipschitz);
-    a.su = ldexpf(1.f, -p->tc_ea);
-    a.sg = ldexpf(1.f, -(p->tc_ea + p->tc_ep));
-    a.sp = ldexpf(1.f, p->tc_ep);
-    const int sms = p->ctx->sm_count;
-    const int grid = a.n_tiles < sms ? a.n_tiles : sms;
+    J->split_from = mixed ? (d.iters > d.tail_iters ? d.iters - d.tail_iters : 0) : 0;
+    J->lambda_rel = d.lambda_rel;
+    J->inv_l = (float)(1.0 / p->lipschitz);
+    J->su = ldexpf(1.f, -p->tc_ea);
+    J->sg = ldexpf(1.f, -(p->tc_ea + p->tc_ep));
+    J->sp = ldexpf(1.f, p->tc_ep);
+}
+
+cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
+    if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;
+    TcLaunch L{};
+    L.beta = jobs[0].beta;
+    L.err = jobs[0].plan->ctx->err_dev;
+    int tiles = 0;
+    bool bf0 = false;
+    int nj = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        const long long rows = (long long)jobs[i].gs.n_cs * jobs[i].gs.nblk;
+        if (rows == 0) continue;
+        bool bf = false;
+        fill_job(jobs[i], tiles, &L.jobs[nj], &bf);
+        if (nj == 0) bf0 = bf;
+        else if (bf != bf0) return cudaErrorInvalidValue;   // one operand type per launch
+        tiles += (int)((rows + kTile - 1) / kTile);
+        ++nj;
+    }
+    if (nj == 0) return cudaSuccess;
+    L.n_jobs = nj;
+    L.n_tiles = tiles;
+    const int sms = jobs[0].plan->ctx->sm_count;
+    const int grid = tiles < sms ? tiles : sms;
     cudaError_t e;
-    if (bf) {
+    if (bf0) {
         e = cudaFuncSetAttribute(k_fista_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmemBytes);
         if (e != cudaSuccess) return e;
-        k_fista_tc<true><<<grid, kThreads, kSmemBytes, s>>>(a);
+        k_fista_tc<true><<<grid, kThreads, kSmemBytes, s>>>(L);
     } else {
         e = cudaFuncSetAttribute(k_fista_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmemBytes);
         if (e != cudaSuccess) return e;
-        k_fista_tc<false><<<grid, kThreads, kSmemBytes, s>>>(a);
+        k_fista_tc<false><<<grid, kThreads, kSmemBytes, s>>>(L);
     }
     return cudaGetLastError();
+}
+
+cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s) {
+    return launch_decode_tc_batch(&d, 1, s);
 }
 
 }  // namespace csvc

@@ -96,6 +96,7 @@ struct DecodeArgs {
 cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s);
 bool tc_supported(const cs_plan* plan, int precision);
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
+cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
 
 // metrics (metrics.cu)
 cudaError_t launch_psnr(const uint8_t* ref, const float* test, int n_frames, int h, int w,
@@ -103,7 +104,7 @@ cudaError_t launch_psnr(const uint8_t* ref, const float* test, int n_frames, int
 
 // tensor-core operand preparation (decode_tc.cu)
 bool tc_plan_supported(int n, int m);
-size_t tc_operand_bytes();
+size_t tc_operand_bytes(int m);
 cudaError_t launch_tc_ranges(const float* a, const float* phi, int n, int m, float* out,
                              cudaStream_t s);
 cudaError_t launch_tc_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s);
