@@ -139,6 +139,21 @@ int cs_decode_gop(cs_plan* plan, const cs_params* params, const uint8_t* key_dev
                   const float* y_dev, float* frames_f32_dev, uint8_t* frames_u8_dev,
                   cs_stream_t stream);
 
+/* ---- batched decode ---------------------------------------------------------
+ * cs_decode_batch: decode n_jobs GOP calls (cs_decode_gop semantics, job i =
+ * plans[i], params[i], key_dev[i], y_dev[i], frames_f32_dev[i] and
+ * frames_u8_dev[i]; the two output arrays may be NULL, or hold NULL entries)
+ * as one persistent tensor-core launch per operand type: plans of different M
+ * and calls of different frame size, GOP size, iteration count and precision
+ * share the SMs, each CTA taking the next 128-block tile.  All plans belong
+ * to ctx.  Jobs the tensor-core kernel does not cover (or that ask for
+ * CS_ENGINE_PLAIN) run on the plain kernel on the same stream.  Results are
+ * identical to decoding each job alone.  Host arrays, device buffers. */
+int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs_params* params,
+                    const uint8_t* const* key_dev, const float* const* y_dev,
+                    float* const* frames_f32_dev, uint8_t* const* frames_u8_dev,
+                    cs_stream_t stream);
+
 /* ---- quality and compression accounting (Sec. 4, Table I) ----------------
  * cs_psnr: per-frame PSNR 10 log10(255^2 / MSE) of test_dev (float32
  * [n][H][W]) against ref_dev (uint8 [n][H][W]), FP64 reductions on the device;

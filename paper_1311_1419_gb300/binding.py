@@ -70,6 +70,9 @@ _SIGS = {
     "cs_plan_lipschitz": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "cs_encode_gop": (ctypes.c_int, [_vp, ctypes.POINTER(cs_params), _vp, _vp, _vp]),
     "cs_decode_gop": (ctypes.c_int, [_vp, ctypes.POINTER(cs_params), _vp, _vp, _vp, _vp, _vp]),
+    "cs_decode_batch": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(cs_params),
+                                       ctypes.POINTER(_vp), ctypes.POINTER(_vp),
+                                       ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     "cs_psnr": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "cs_total_cr": (ctypes.c_double, [_i32, ctypes.c_double, ctypes.c_double]),
     "cs_raw_key_cr": (ctypes.c_double, [_i32, _i32, _i32, _i32, _i32]),
@@ -186,6 +189,25 @@ def cs_decode_gop(plan: int, params: cs_params, key_dev, y_dev, frames_f32_dev=N
                   frames_u8_dev=None, stream=None) -> None:
     _check(load().cs_decode_gop(plan, ctypes.byref(params), _ptr(key_dev), _ptr(y_dev),
                                 _ptr(frames_f32_dev), _ptr(frames_u8_dev), _stream(stream)))
+
+
+def cs_decode_batch(ctx: int, plans, params, key_dev, y_dev, frames_f32_dev=None,
+                    frames_u8_dev=None, stream=None) -> None:
+    """Sequences of equal length; device buffers as ints or tensors (None allowed)."""
+    n = len(plans)
+
+    def arr(xs):
+        if xs is None:
+            return None
+        a = (_vp * n)()
+        for i, x in enumerate(xs):
+            a[i] = _ptr(x)
+        return a
+
+    pl = (_vp * n)(*plans)
+    pa = (cs_params * n)(*params)
+    _check(load().cs_decode_batch(ctx, n, pl, pa, arr(key_dev), arr(y_dev), arr(frames_f32_dev),
+                                  arr(frames_u8_dev), _stream(stream)))
 
 
 def cs_psnr(ref_dev, test_dev, n_frames: int, height: int, width: int, psnr_dev,

@@ -83,8 +83,10 @@ int check_decode_params(const cs_params* p) {
     return CS_OK;
 }
 
-int decode_impl(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
-                float* out_f32, uint8_t* out_u8, cudaStream_t stream) {
+// Check one decode request and fill its launch arguments; *engine gets the
+// kernel that will run it.
+int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
+                   float* out_f32, uint8_t* out_u8, DecodeArgs* d, int* engine) {
     GopShape gs;
     int st = make_shape(plan, params, &gs);
     if (st) return st;
@@ -92,25 +94,34 @@ int decode_impl(cs_plan* plan, const cs_params* params, const uint8_t* key, cons
     if (st) return st;
     if (!out_f32 && !out_u8) return fail(CS_EINVAL, "both outputs are NULL");
     if (gs.n_cs > 0 && (!key || !y)) return fail(CS_EINVAL, "null input pointer");
-    DecodeArgs d;
-    d.plan = plan;
-    d.gs = gs;
-    d.key = key;
-    d.y = y;
-    d.out_f32 = out_f32;
-    d.out_u8 = out_u8;
-    d.iters = params->iters;
-    d.tail_iters = params->fp32_tail_iters;
-    d.lambda_rel = params->lambda_rel;
-    d.precision = params->precision;
-    d.beta = plan->ctx->beta_dev;
-    int engine = params->engine;
+    d->plan = plan;
+    d->gs = gs;
+    d->key = key;
+    d->y = y;
+    d->out_f32 = out_f32;
+    d->out_u8 = out_u8;
+    d->iters = params->iters;
+    d->tail_iters = params->fp32_tail_iters;
+    d->lambda_rel = params->lambda_rel;
+    d->precision = params->precision;
+    d->beta = plan->ctx->beta_dev;
+    int eng = params->engine;
     const bool tc_ok = tc_supported(plan, params->precision);
-    if (engine == CS_ENGINE_TC && !tc_ok)
+    if (eng == CS_ENGINE_TC && !tc_ok)
         return fail(CS_EINVAL, "tensor-core decode does not support this (N, M, precision)");
-    if (engine == CS_ENGINE_AUTO) engine = tc_ok ? CS_ENGINE_TC : CS_ENGINE_PLAIN;
-    if (engine == CS_ENGINE_PLAIN && params->precision != CS_FP32)
+    if (eng == CS_ENGINE_AUTO) eng = tc_ok ? CS_ENGINE_TC : CS_ENGINE_PLAIN;
+    if (eng == CS_ENGINE_PLAIN && params->precision != CS_FP32)
         return fail(CS_EINVAL, "the plain engine computes in FP32 only");
+    *engine = eng;
+    return CS_OK;
+}
+
+int decode_impl(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
+                float* out_f32, uint8_t* out_u8, cudaStream_t stream) {
+    DecodeArgs d;
+    int engine = 0;
+    int st = prepare_decode(plan, params, key, y, out_f32, out_u8, &d, &engine);
+    if (st) return st;
     cudaError_t e = engine == CS_ENGINE_TC ? launch_decode_tc(d, stream)
                                            : launch_decode_plain(d, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
@@ -155,6 +166,7 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
         e = cudaMemcpy(ctx->beta_dev, beta.data(), sizeof(float) * kMaxIters, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->err_dev, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->err_dev, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->counters_dev, sizeof(int) * kTileCounters);
     for (int i = 0; e == cudaSuccess && i < 8; ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -180,6 +192,7 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
     if (ctx->beta_dev) cudaFree(ctx->beta_dev);
     if (ctx->err_dev) cudaFree(ctx->err_dev);
+    if (ctx->counters_dev) cudaFree(ctx->counters_dev);
     delete ctx;
     return CS_OK;
 }
@@ -293,6 +306,32 @@ int cs_decode_gop(cs_plan* plan, const cs_params* params, const uint8_t* key_dev
                   float* frames_f32_dev, uint8_t* frames_u8_dev, cs_stream_t stream) {
     return decode_impl(plan, params, key_dev, y_dev, frames_f32_dev, frames_u8_dev,
                        (cudaStream_t)stream);
+}
+
+int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs_params* params,
+                    const uint8_t* const* key_dev, const float* const* y_dev,
+                    float* const* frames_f32_dev, uint8_t* const* frames_u8_dev,
+                    cs_stream_t stream) {
+    if (!ctx || n_jobs < 0 || (n_jobs > 0 && (!plans || !params || !key_dev || !y_dev)))
+        return fail(CS_EINVAL, "null argument");
+    std::vector<DecodeArgs> tc_jobs, plain_jobs;
+    tc_jobs.reserve(n_jobs);
+    for (int i = 0; i < n_jobs; ++i) {
+        if (!plans[i] || plans[i]->ctx != ctx) return fail(CS_EINVAL, "plan of another context");
+        DecodeArgs d;
+        int engine = 0;
+        int st = prepare_decode(plans[i], &params[i], key_dev[i], y_dev[i],
+                                frames_f32_dev ? frames_f32_dev[i] : nullptr,
+                                frames_u8_dev ? frames_u8_dev[i] : nullptr, &d, &engine);
+        if (st) return fail(st, std::string("job ") + std::to_string(i) + ": " + cs_last_error());
+        (engine == CS_ENGINE_TC ? tc_jobs : plain_jobs).push_back(d);
+    }
+    cudaError_t e = cudaSuccess;
+    if (!tc_jobs.empty()) e = launch_decode_tc_batch(tc_jobs.data(), (int)tc_jobs.size(), (cudaStream_t)stream);
+    for (size_t i = 0; e == cudaSuccess && i < plain_jobs.size(); ++i)
+        e = launch_decode_plain(plain_jobs[i], (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");
+    return CS_OK;
 }
 
 int cs_psnr(const uint8_t* ref_dev, const float* test_dev, int32_t n_frames, int32_t height,

@@ -35,6 +35,9 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "internal.h"
 #include "tc_ptx.h"
 
@@ -63,6 +66,7 @@ struct Misc {
     uint64_t bar_load, bar_u, bar_g, bar_p, bar_z0, bar_z1, bar_drain;
     uint32_t tmem_base;
     int abort;
+    int next_tile;
     uint32_t colmax[kTile];
 };
 
@@ -90,6 +94,7 @@ constexpr int kMaxJobs = 48;
 struct TcLaunch {
     const float* beta;
     int* err;
+    int* tile_counter;      // zeroed before the launch; tiles are handed out in order
     int n_jobs;
     int n_tiles;
     TcJob jobs[kMaxJobs];
@@ -258,7 +263,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
     uint32_t ph_z0 = 0, ph_z1 = 0, ph_p = 0, ph_load = 0;   // the issuer only
     bool ok = true;
     int cur = -1;
-    for (int tile = blockIdx.x; tile < L.n_tiles; tile += gridDim.x) {
+    for (;;) {
+        // persistent CTAs take the next tile (jobs are ordered heaviest first)
+        if (threadIdx.x == 0) ms->next_tile = atomicAdd(L.tile_counter, 1);
+        __syncthreads();
+        const int tile = ms->next_tile;
+        if (tile >= L.n_tiles) break;
         const int jid = job_of(L, tile);
         const TcJob& J = L.jobs[jid];
         const GopShape& gs = J.gs;
@@ -603,31 +613,31 @@ static void fill_job(const DecodeArgs& d, int tile_begin, TcJob* J, bool* bf) {
     J->sp = ldexpf(1.f, p->tc_ep);
 }
 
-cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
-    if (n_jobs < 1 || n_jobs > kMaxJobs) return cudaErrorInvalidValue;
+// One launch for up to kMaxJobs jobs of one operand type (fp16 or bf16).  Jobs
+// are laid out heaviest first (iterations x work per iteration) so that the
+// dynamic tile order approximates longest-processing-time scheduling.
+static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool bf, cudaStream_t s) {
     TcLaunch L{};
-    L.beta = jobs[0].beta;
-    L.err = jobs[0].plan->ctx->err_dev;
-    int tiles = 0;
-    bool bf0 = false;
-    int nj = 0;
-    for (int i = 0; i < n_jobs; ++i) {
-        const long long rows = (long long)jobs[i].gs.n_cs * jobs[i].gs.nblk;
-        if (rows == 0) continue;
-        bool bf = false;
-        fill_job(jobs[i], tiles, &L.jobs[nj], &bf);
-        if (nj == 0) bf0 = bf;
-        else if (bf != bf0) return cudaErrorInvalidValue;   // one operand type per launch
-        tiles += (int)((rows + kTile - 1) / kTile);
-        ++nj;
+    L.beta = jobs[0]->beta;
+    L.err = jobs[0]->plan->ctx->err_dev;
+    cs_ctx* ctx = jobs[0]->plan->ctx;
+    {
+        std::lock_guard<std::mutex> lock(ctx->mu);
+        L.tile_counter = ctx->counters_dev + (ctx->next_counter++ % kTileCounters);
     }
-    if (nj == 0) return cudaSuccess;
-    L.n_jobs = nj;
+    cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    int tiles = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        bool jbf = false;
+        fill_job(*jobs[i], tiles, &L.jobs[i], &jbf);
+        tiles += (int)((L.jobs[i].rows + kTile - 1) / kTile);
+    }
+    L.n_jobs = n_jobs;
     L.n_tiles = tiles;
-    const int sms = jobs[0].plan->ctx->sm_count;
+    const int sms = ctx->sm_count;
     const int grid = tiles < sms ? tiles : sms;
-    cudaError_t e;
-    if (bf0) {
+    if (bf) {
         e = cudaFuncSetAttribute(k_fista_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmemBytes);
         if (e != cudaSuccess) return e;
@@ -639,6 +649,37 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
         k_fista_tc<false><<<grid, kThreads, kSmemBytes, s>>>(L);
     }
     return cudaGetLastError();
+}
+
+static double job_cost(const DecodeArgs& d) {
+    const bool mixed = d.precision == CS_BF16 || d.precision == CS_FP16;
+    const double split_iters = mixed ? (double)(d.tail_iters < d.iters ? d.tail_iters : d.iters)
+                                     : (double)d.iters;
+    const double m16 = (double)m16_of(d.plan->m);
+    // per iteration: 16 GEMM1 steps + m16/16 GEMM2 steps, x3 when split, plus the epilogue
+    const double per = 16.0 + m16 / 16.0 + 24.0;
+    return (double)d.iters * per + 2.0 * split_iters * (16.0 + m16 / 16.0);
+}
+
+cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
+    std::vector<const DecodeArgs*> groups[2];
+    for (int i = 0; i < n_jobs; ++i) {
+        if ((long long)jobs[i].gs.n_cs * jobs[i].gs.nblk == 0) continue;
+        const bool bf = jobs[i].precision == CS_BF16 || jobs[i].precision == CS_BF16X2;
+        groups[bf ? 1 : 0].push_back(&jobs[i]);
+    }
+    for (int bf = 0; bf < 2; ++bf) {
+        std::vector<const DecodeArgs*>& g = groups[bf];
+        std::stable_sort(g.begin(), g.end(), [](const DecodeArgs* a, const DecodeArgs* b) {
+            return job_cost(*a) > job_cost(*b);
+        });
+        for (size_t i = 0; i < g.size(); i += kMaxJobs) {
+            const int n = (int)(g.size() - i < (size_t)kMaxJobs ? g.size() - i : (size_t)kMaxJobs);
+            cudaError_t e = launch_group(g.data() + i, n, bf == 1, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s) {

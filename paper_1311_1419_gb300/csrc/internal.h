@@ -15,6 +15,7 @@ namespace csvc {
 // Maximum FISTA iteration count accepted by a call (size of the momentum table).
 constexpr int kMaxIters = 1 << 17;
 constexpr int kMaxN = 4096;
+constexpr int kTileCounters = 256;   // per-launch tile counters of the persistent decode
 
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
@@ -36,6 +37,8 @@ struct cs_ctx {
     size_t hbm_budget = 0;
     float* beta_dev = nullptr;          // FISTA momentum (t_k - 1)/t_{k+1}, k = 1..kMaxIters
     int* err_dev = nullptr;             // set to 1 by a kernel whose bounded wait gave up
+    int* counters_dev = nullptr;        // csvc::kTileCounters tile counters, used round robin
+    uint64_t next_counter = 0;
     // serving state
     std::mutex mu;
     size_t hbm_in_use = 0;
