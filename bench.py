@@ -118,6 +118,95 @@ def decode_flops(blocks: int, m: int, n: int, iters: int) -> float:
     return float(blocks) * (4.0 * m * n * iters + 2.0 * m * n)
 
 
+SERVING = {
+    "workload": "256 synthetic cameras, resolution QCIF/CIF/720p/1080p (p = .4/.3/.2/.1), "
+                "GOP uniform 4..32, 16x16 blocks, M/N uniform 5%..25%, Phi seed = camera id, "
+                "FISTA 200 iters; one request = one GOP decode; Poisson arrivals",
+    "cameras": 256, "iters": 200, "seed": 7,
+}
+
+
+def serving_run(B, torch, dev, precision, tail, rates, seconds, hbm_budget=8 << 30):
+    """Open-loop serving: Poisson arrivals over the camera mix at each rate;
+    returns one dict per rate (p50/p99 latency, Mpixel/s, admitted, refused)."""
+    from paper_1311_1419_gb300 import scenes
+
+    rng = np.random.default_rng(SERVING["seed"])
+    res = [scenes.RESOLUTIONS[k] for k in ("qcif", "cif", "720p", "1080p")]
+    base = {r: scenes.surveillance_video(32, r[0], r[1], seed=i) for i, r in enumerate(res)}
+    ctx = B.cs_ctx_create(dev.index, hbm_budget)
+    cams = []
+    stream = torch.cuda.Stream(dev)
+    try:
+        for cid in range(SERVING["cameras"]):
+            h, w = res[rng.choice(4, p=[0.4, 0.3, 0.2, 0.1])]
+            gop = int(rng.integers(4, 33))
+            m = max(1, int(np.rint(256 * rng.uniform(0.05, 0.25))))
+            plan = B.cs_make_phi(ctx, 256, m, cid)
+            p = B.make_params(h, w, gop, 16, m, iters=SERVING["iters"], precision=precision,
+                              fp32_tail_iters=tail)
+            off = cid % (33 - gop)
+            clip = base[(h, w)][off:off + gop]
+            nblk = (-(-h // 16)) * (-(-w // 16))
+            y = torch.empty((gop - 1, nblk, m), dtype=torch.float32, device=dev)
+            B.cs_encode_gop(plan, p, torch.from_numpy(np.ascontiguousarray(clip)).to(dev), y,
+                            stream)
+            stream.synchronize()
+            cams.append({"plan": plan, "p": p, "key": torch.from_numpy(
+                np.ascontiguousarray(clip[:1])).pin_memory(), "y": y.cpu().pin_memory(),
+                "shape": (gop - 1, h, w), "pixels": (gop - 1) * h * w, "free": []})
+        results = []
+        for rate in rates:
+            t_next = 0.0
+            arrivals = []
+            while t_next < seconds:
+                t_next += rng.exponential(1.0 / rate)
+                arrivals.append((t_next, int(rng.integers(len(cams)))))
+            inflight, lat, pixels, refused = {}, [], 0, 0
+            backlog = []
+            t0 = time.perf_counter()
+            i = 0
+            while i < len(arrivals) or backlog or inflight:
+                now = time.perf_counter() - t0
+                while i < len(arrivals) and arrivals[i][0] <= now:
+                    backlog.append((arrivals[i][1], t0 + arrivals[i][0]))
+                    i += 1
+                while backlog:                      # admit as slots and memory free up
+                    c = cams[backlog[0][0]]
+                    out = c["free"].pop() if c["free"] else torch.empty(
+                        c["shape"], dtype=torch.uint8).pin_memory()
+                    try:
+                        t = B.cs_submit(ctx, c["plan"], c["p"], c["key"], c["y"], out)
+                    except B.CsError as e:
+                        c["free"].append(out)
+                        if e.status != B.CS_EAGAIN:
+                            raise
+                        refused += 1
+                        break
+                    cid, t_arr = backlog.pop(0)
+                    inflight[t] = (cid, out, time.perf_counter() - t_arr)
+                for t in list(inflight):
+                    done, ms = B.cs_poll(ctx, t)
+                    if done:
+                        cid, out, queued = inflight.pop(t)
+                        # arrival to completion: admission queueing + submit-to-done
+                        lat.append(1e3 * queued + ms)
+                        pixels += cams[cid]["pixels"]
+                        cams[cid]["free"].append(out)
+            wall = time.perf_counter() - t0
+            B.cs_ctx_status(ctx)
+            lat_ms = np.array(lat)
+            results.append({"rate_per_s": rate, "requests": len(lat), "refused_retries": refused,
+                            "p50_ms": float(np.percentile(lat_ms, 50)),
+                            "p99_ms": float(np.percentile(lat_ms, 99)),
+                            "mpixel_per_s": pixels / wall / 1e6})
+        return results
+    finally:
+        for c in cams:
+            B.cs_plan_destroy(c["plan"])
+        B.cs_ctx_destroy(ctx)
+
+
 def oracle_sample(frames, wl, n_cs_frames: int):
     """Time the FP64 oracle on the first n_cs_frames CS frames at every M.
 
@@ -183,6 +272,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
     ap.add_argument("--no-batch", action="store_true",
                     help="one decode call per M instead of one batched launch")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serving-sweep", action="store_true",
+                    help="sweep the arrival rate to saturation, FP32 and mixed precision")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps, always
     rank, world, local = dist_env()
@@ -353,6 +445,15 @@ def main():
         bound = "alu"
     psnr = {m: float(np.mean(psnr_dev[m].cpu().numpy())) for m in wl["ms"]}
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        rates = [50, 100, 200, 300, 400, 600] if args.serving_sweep else [100]
+        secs = 3.0 if args.serving_sweep else 2.0
+        serving = {"workload": SERVING["workload"],
+                   "fp32": serving_run(B, torch, dev, B.CS_FP32, 0, rates, secs)}
+        if args.serving_sweep:
+            serving["fp16_tail20"] = serving_run(B, torch, dev, B.CS_FP16, 20, rates, secs)
+
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -400,6 +501,7 @@ def main():
             "decode_gflop_per_step": flops / 1e9,
             "psnr_db": {str(m): psnr[m] for m in wl["ms"]},
             "parity_vs_oracle": parity,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
 

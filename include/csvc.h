@@ -168,14 +168,21 @@ double cs_raw_key_cr(int32_t gop, int32_t height, int32_t width, int32_t block, 
 
 /* ---- serving --------------------------------------------------------------
  * cs_submit: enqueue the decode of one request (cs_decode_gop semantics,
- * frames_u8_dev output) on the context's serving streams.  Admission charges
- * the request's device working set against the context's HBM budget and the
- * number of free slots; when either is exhausted the call returns CS_EAGAIN
- * and enqueues nothing.  *ticket identifies the request.
- * cs_poll: non-blocking; *done = 1 once the request's output is complete,
- * then *latency_ms is submit-to-completion time and the ticket is retired. */
-int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t* key_dev,
-              const float* y_dev, uint8_t* frames_u8_dev, uint64_t* ticket);
+ * uint8 output) from HOST buffers: key_host uint8 [n_gops][H][W], y_host float32
+ * [n_cs][nblk][M], frames_u8_host uint8 [n_cs][H][W] (the output).  Use pinned
+ * memory for overlap; the buffers must stay valid until cs_poll reports done.
+ * Admission takes one of the context's slots (64) and carves the request's
+ * device working set (key + y + output) out of a device pool of
+ * hbm_budget_bytes (1 GiB if the context was created with 0), first fit; when
+ * either is exhausted the call returns CS_EAGAIN and enqueues nothing (a
+ * request larger than the whole pool returns CS_ENOMEM).  Admitted requests
+ * run on the context's streams and overlap on the device.  *ticket identifies
+ * the request.
+ * cs_poll: non-blocking; *done = 1 once the output is in frames_u8_host, then
+ * *latency_ms is the submit-to-completion time, the request's device memory
+ * and slot are released and the ticket is retired. */
+int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t* key_host,
+              const float* y_host, uint8_t* frames_u8_host, uint64_t* ticket);
 int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms);
 
 /* ---- allocation-free Lipschitz estimate -------------------------------------

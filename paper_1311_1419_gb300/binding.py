@@ -224,10 +224,19 @@ def cs_raw_key_cr(gop: int, height: int, width: int, block: int, m: int) -> floa
     return load().cs_raw_key_cr(int(gop), int(height), int(width), int(block), int(m))
 
 
-def cs_submit(ctx: int, plan: int, params: cs_params, key_dev, y_dev, frames_u8_dev) -> int:
+def _host_ptr(x):
+    """Host buffer address: an int, a numpy array or a CPU tensor."""
+    if x is None or isinstance(x, int):
+        return x
+    if hasattr(x, "ctypes"):
+        return int(x.ctypes.data)
+    return int(x.data_ptr())
+
+
+def cs_submit(ctx: int, plan: int, params: cs_params, key_host, y_host, frames_u8_host) -> int:
     t = ctypes.c_uint64()
-    _check(load().cs_submit(ctx, plan, ctypes.byref(params), _ptr(key_dev), _ptr(y_dev),
-                            _ptr(frames_u8_dev), ctypes.byref(t)))
+    _check(load().cs_submit(ctx, plan, ctypes.byref(params), _host_ptr(key_host),
+                            _host_ptr(y_host), _host_ptr(frames_u8_host), ctypes.byref(t)))
     return t.value
 
 

@@ -5,8 +5,6 @@
 #include <math.h>
 #include <string.h>
 
-#include <atomic>
-#include <chrono>
 #include <cstdio>
 #include <new>
 #include <string>
@@ -17,11 +15,6 @@ namespace csvc {
 
 namespace {
 thread_local std::string g_last_error;
-
-double now_ms() {
-    using namespace std::chrono;
-    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
-}
 }  // namespace
 
 void set_error(const std::string& msg) { g_last_error = msg; }
@@ -36,18 +29,6 @@ int cuda_fail(cudaError_t err, const char* what) {
                    cudaGetErrorString(err) + ")";
     return err == cudaErrorMemoryAllocation ? CS_ENOMEM : CS_ECUDA;
 }
-
-struct Ticket {
-    uint64_t id = 0;
-    size_t bytes = 0;
-    double submit_ms = 0.0;
-    std::atomic<double> done_ms{-1.0};  // written by the host callback after the decode
-    cudaEvent_t done_event = nullptr;
-};
-
-namespace {
-
-void CUDART_CB mark_done(void* p) { static_cast<Ticket*>(p)->done_ms.store(now_ms()); }
 
 // Validate a call's parameters against the plan and derive the GOP shape.
 int make_shape(const cs_plan* plan, const cs_params* p, GopShape* gs) {
@@ -72,6 +53,8 @@ int make_shape(const cs_plan* plan, const cs_params* p, GopShape* gs) {
     gs->n_cs = (int)n_cs;
     return CS_OK;
 }
+
+namespace {
 
 int check_decode_params(const cs_params* p) {
     if (p->iters < 0 || p->iters > kMaxIters) return fail(CS_EINVAL, "iters out of range");
@@ -116,8 +99,10 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
     return CS_OK;
 }
 
-int decode_impl(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
-                float* out_f32, uint8_t* out_u8, cudaStream_t stream) {
+}  // namespace
+
+int decode_enqueue(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
+                   float* out_f32, uint8_t* out_u8, cudaStream_t stream) {
     DecodeArgs d;
     int engine = 0;
     int st = prepare_decode(plan, params, key, y, out_f32, out_u8, &d, &engine);
@@ -128,7 +113,6 @@ int decode_impl(cs_plan* plan, const cs_params* params, const uint8_t* key, cons
     return CS_OK;
 }
 
-}  // namespace
 }  // namespace csvc
 
 using namespace csvc;
@@ -185,10 +169,7 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     if (!ctx) return CS_OK;
     cudaSetDevice(ctx->device);
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
-    for (Ticket* t : ctx->live) {
-        if (t->done_event) cudaEventDestroy(t->done_event);
-        delete t;
-    }
+    serving_destroy(ctx);
     for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
     if (ctx->beta_dev) cudaFree(ctx->beta_dev);
     if (ctx->err_dev) cudaFree(ctx->err_dev);
@@ -304,8 +285,8 @@ int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_
 
 int cs_decode_gop(cs_plan* plan, const cs_params* params, const uint8_t* key_dev, const float* y_dev,
                   float* frames_f32_dev, uint8_t* frames_u8_dev, cs_stream_t stream) {
-    return decode_impl(plan, params, key_dev, y_dev, frames_f32_dev, frames_u8_dev,
-                       (cudaStream_t)stream);
+    return decode_enqueue(plan, params, key_dev, y_dev, frames_f32_dev, frames_u8_dev,
+                          (cudaStream_t)stream);
 }
 
 int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs_params* params,
@@ -354,75 +335,6 @@ double cs_raw_key_cr(int32_t gop, int32_t height, int32_t width, int32_t block, 
     const double nblk = (double)((height + block - 1) / block) * ((width + block - 1) / block);
     const double px = (double)height * width;
     return gop * px / (px + (gop - 1) * nblk * m);
-}
-
-int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t* key_dev,
-              const float* y_dev, uint8_t* frames_u8_dev, uint64_t* ticket) {
-    if (!ctx || !plan || !params || !ticket) return fail(CS_EINVAL, "null argument");
-    if (plan->ctx != ctx) return fail(CS_EINVAL, "plan belongs to another context");
-    GopShape gs;
-    int st = make_shape(plan, params, &gs);
-    if (st) return st;
-    // working set charged to the budget: the request's inputs and outputs
-    const size_t bytes = (size_t)gs.n_gops * gs.h * gs.w +
-                         (size_t)gs.n_cs * gs.nblk * gs.m * sizeof(float) +
-                         (size_t)gs.n_cs * gs.h * gs.w;
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    if ((int)ctx->live.size() >= ctx->max_slots) return fail(CS_EAGAIN, "no free serving slot");
-    if (ctx->hbm_budget && ctx->hbm_in_use + bytes > ctx->hbm_budget)
-        return fail(CS_EAGAIN, "HBM budget exhausted");
-    Ticket* t = new (std::nothrow) Ticket();
-    if (!t) return fail(CS_ENOMEM, "host allocation failed");
-    cudaStream_t s = ctx->streams[ctx->next_stream++ % ctx->streams.size()];
-    cudaError_t e = cudaSetDevice(ctx->device);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&t->done_event, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-        delete t;
-        return cuda_fail(e, "cs_submit");
-    }
-    t->id = ctx->next_ticket++;
-    t->bytes = bytes;
-    t->submit_ms = now_ms();
-    st = decode_impl(plan, params, key_dev, y_dev, nullptr, frames_u8_dev, s);
-    if (st == CS_OK) {
-        e = cudaLaunchHostFunc(s, mark_done, t);
-        if (e == cudaSuccess) e = cudaEventRecord(t->done_event, s);
-        if (e != cudaSuccess) st = cuda_fail(e, "cs_submit completion hook");
-    }
-    if (st != CS_OK) {
-        // anything already enqueued still runs; keep the ticket alive until it does
-        cudaStreamSynchronize(s);
-        cudaEventDestroy(t->done_event);
-        delete t;
-        return st;
-    }
-    ctx->hbm_in_use += bytes;
-    ctx->live.push_back(t);
-    *ticket = t->id;
-    return CS_OK;
-}
-
-int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms) {
-    if (!ctx || !done) return fail(CS_EINVAL, "null argument");
-    std::lock_guard<std::mutex> lock(ctx->mu);
-    for (size_t i = 0; i < ctx->live.size(); ++i) {
-        Ticket* t = ctx->live[i];
-        if (t->id != ticket) continue;
-        cudaError_t e = cudaEventQuery(t->done_event);
-        if (e == cudaErrorNotReady || t->done_ms.load() < 0.0) {
-            *done = 0;
-            return CS_OK;
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "cs_poll");
-        *done = 1;
-        if (latency_ms) *latency_ms = (float)(t->done_ms.load() - t->submit_ms);
-        ctx->hbm_in_use -= t->bytes;
-        cudaEventDestroy(t->done_event);
-        delete t;
-        ctx->live.erase(ctx->live.begin() + i);
-        return CS_OK;
-    }
-    return fail(CS_ENOTFOUND, "unknown or retired ticket");
 }
 
 int cs_ctx_status(cs_ctx* ctx) {

@@ -621,10 +621,7 @@ static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool 
     L.beta = jobs[0]->beta;
     L.err = jobs[0]->plan->ctx->err_dev;
     cs_ctx* ctx = jobs[0]->plan->ctx;
-    {
-        std::lock_guard<std::mutex> lock(ctx->mu);
-        L.tile_counter = ctx->counters_dev + (ctx->next_counter++ % kTileCounters);
-    }
+    L.tile_counter = ctx->counters_dev + (ctx->next_counter.fetch_add(1) % kTileCounters);
     cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     int tiles = 0;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -28,6 +29,7 @@ int cuda_fail(cudaError_t err, const char* what);
     } while (0)
 
 struct Ticket;
+struct Pool;
 
 }  // namespace csvc
 
@@ -38,10 +40,10 @@ struct cs_ctx {
     float* beta_dev = nullptr;          // FISTA momentum (t_k - 1)/t_{k+1}, k = 1..kMaxIters
     int* err_dev = nullptr;             // set to 1 by a kernel whose bounded wait gave up
     int* counters_dev = nullptr;        // csvc::kTileCounters tile counters, used round robin
-    uint64_t next_counter = 0;
+    std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
     // serving state
     std::mutex mu;
-    size_t hbm_in_use = 0;
+    csvc::Pool* pool = nullptr;         // device pool carved from the HBM budget, on first use
     int max_slots = 64;
     std::vector<csvc::Ticket*> live;
     uint64_t next_ticket = 1;
@@ -100,6 +102,9 @@ cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s);
 bool tc_supported(const cs_plan* plan, int precision);
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
 cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
+
+// serving (serving.cu)
+void serving_destroy(cs_ctx* ctx);
 
 // metrics (metrics.cu)
 cudaError_t launch_psnr(const uint8_t* ref, const float* test, int n_frames, int h, int w,
