@@ -17,7 +17,8 @@
 //   shared memory : A (hi and lo 16-bit images, 128-byte swizzled, loaded by the
 //                   bulk-copy engine), the residual operand P (hi, lo), the DCT
 //   tensor memory : the accumulator (U, then G), Z hi and Z lo (GEMM1's A)
-//   registers     : s^{k-1} of the thread's 64 coefficients (the momentum state)
+//   registers     : s^{k-1} of the thread's 64 coefficients (the momentum state;
+//                   16 of them in shared memory, interleaved by thread)
 // y is re-read from L2 each iteration, by coalesced asynchronous copies into the
 // P operand's slots while the tensor cores and the gradient step run.  The iterate z is kept as its hi + lo
 // halves (22 significant bits with fp16).  FP32-grade products use three MMAs
@@ -58,7 +59,9 @@ constexpr uint32_t kOffAHi = 0, kOffALo = kAImgMax;
 constexpr uint32_t kOffPHi = 2 * kAImgMax, kOffPLo = kOffPHi + kPImg;
 constexpr uint32_t kOffC = kOffPLo + kPImg;             // DCT matrix, 1 KB
 constexpr uint32_t kOffMisc = kOffC + 1024;
-constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024; // misc + alignment slack
+constexpr int kSpReg = 24;            // momentum-state pairs kept in registers; the rest in smem
+constexpr uint32_t kOffSp = kOffMisc + 1024;             // [kPerThread/2 - kSpReg][kThreads] float2
+constexpr uint32_t kSmemBytes = kOffSp + (kPerThread / 2 - kSpReg) * kThreads * 8 + 1024;
 constexpr uint32_t kColAcc = 0, kColZHi = 256, kColZLo = 384;
 constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s per wait
 
@@ -67,6 +70,9 @@ struct Misc {
     uint32_t tmem_base;
     int abort;
     int next_tile;
+    // the issuing thread's state (kept here, not in every thread's registers)
+    uint32_t ph_z0, ph_z1, ph_p, ph_load;
+    int cur_job, ok;
     uint32_t colmax[kTile];
 };
 
@@ -167,13 +173,27 @@ __device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t k, uint32_
 __device__ __forceinline__ void stage_y(uint8_t* p_hi, uint8_t* p_lo, const float* y_tile,
                                         long long rows_left, int m_rows, int wi, int lane, int nw) {
     const int nrows = rows_left < kTile ? (int)rows_left : kTile;
+    // slot of (b, m) = kmajor_off(b, m & ~3) + 4 (m & 1) in P hi (m & 2 == 0) or P lo.
+    // With m = lane + 32 j the low five bits of m are the lane's, so the slot is
+    //   row(b) + lane_col + (j / 2) * 16 KB + ((lane_chunk ^ 16 (b & 7)) ^ 64 (j & 1)),
+    // row(b) = (b / 8) * 1024 + (b % 8) * 128 and lane_chunk = 16 (lane / 8): the
+    // 16-byte chunk index XORed with b & 7 is the 128-byte swizzle.
+    const uint32_t lane_col = (((uint32_t)lane & 4u) << 1) + 4u * ((uint32_t)lane & 1u) +
+                              (((uint32_t)lane & 2u) ? kPImg : 0u);
+    const uint32_t lane_chunk = ((uint32_t)lane >> 3) << 4;
     for (int b = wi; b < nrows; b += nw) {
         const float* src = y_tile + (long long)b * m_rows;
-        for (int m = lane; m < m_rows; m += 32) {
-            const uint32_t off = kmajor_off((uint32_t)b, (uint32_t)(m & ~3), kTile / 8);
-            cp_async4(((m & 2) ? p_lo : p_hi) + off + 4 * (m & 1), src + m, true);
+        uint8_t* row = p_hi + (uint32_t)(b >> 3) * 1024u + (uint32_t)(b & 7) * 128u + lane_col;
+        const uint32_t x = lane_chunk ^ ((uint32_t)(b & 7) << 4);
+#pragma unroll
+        for (int j = 0; j < kMaxM16 / 32; ++j) {
+            const int m = lane + 32 * j;
+            if (m < m_rows)
+                cp_async4(row + (uint32_t)(j >> 1) * (kTile / 8) * 1024u + (x ^ (64u * (j & 1))),
+                          src + m, true);
         }
     }
+    (void)p_lo;   // P lo follows P hi at kPImg
     cp_async_commit();
 }
 
@@ -241,6 +261,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
             mbar_init(&ms->bar_z1, kEpiWarps);
             mbar_init(&ms->bar_drain, 1);
             ms->abort = 0;
+            ms->ph_z0 = ms->ph_z1 = ms->ph_p = ms->ph_load = 0;
+            ms->cur_job = -1;
+            ms->ok = 1;
             fence_mbar_init();
         }
         __syncwarp();
@@ -259,10 +282,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
     const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
     uint8_t* p_hi = sm + kOffPHi;
     uint8_t* p_lo = sm + kOffPLo;
+    float2* sp_smem = reinterpret_cast<float2*>(sm + kOffSp) + threadIdx.x;
     uint32_t ph_u = 0, ph_g = 0;                            // every thread
-    uint32_t ph_z0 = 0, ph_z1 = 0, ph_p = 0, ph_load = 0;   // the issuer only
-    bool ok = true;
-    int cur = -1;
     for (;;) {
         // persistent CTAs take the next tile (jobs are ordered heaviest first)
         if (threadIdx.x == 0) ms->next_tile = atomicAdd(L.tile_counter, 1);
@@ -277,9 +298,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
         const int mq = J.m16 / 4;                           // residual rows of this thread
         const int mbase = cgrp * mq;
         const float2 ginv2 = make_float2(-J.sg * J.inv_l, -J.sg * J.inv_l);
-        float2 sp[kPerThread / 2];
+        // s^{k-1}: pairs 0 .. kSpReg-1 in registers, the rest in shared memory
+        float2 sp[kSpReg];
 #pragma unroll
-        for (int i = 0; i < kPerThread / 2; ++i) sp[i] = make_float2(0.f, 0.f);
+        for (int i = 0; i < kSpReg; ++i) sp[i] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = kSpReg; i < kPerThread / 2; ++i) sp_smem[(i - kSpReg) * kThreads] = make_float2(0.f, 0.f);
         float tau = 0.f;
         // --- tile init: Z = 0 in TMEM ---
         {
@@ -303,16 +327,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
         __syncthreads();   // also: every MMA of the previous tile has completed (its last G was waited)
         fence_after_sync();
         if (issuer) {
-            if (jid != cur) {
+            if (jid != ms->cur_job) {
                 const uint32_t img = (uint32_t)J.m16 * kN * 2;
                 mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
                 bulk_g2s(sm + kOffAHi, J.a_img, img, &ms->bar_load);
                 bulk_g2s(sm + kOffALo, J.a_img + img, img, &ms->bar_load);
-                ok = wait_bar(ms, &ms->bar_load, ph_load, L.err) && ok;
-                ph_load ^= 1;
-                cur = jid;
+                ms->ok = wait_bar(ms, &ms->bar_load, ms->ph_load, L.err) && ms->ok;
+                ms->ph_load ^= 1;
+                ms->cur_job = jid;
             }
-            if (J.iters > 0 && ok) {
+            if (J.iters > 0 && ms->ok) {
                 issue_gemm1_half<BF>(tbase, s_base, J.m16, 0, 0 >= J.split_from);
                 issue_gemm1_half<BF>(tbase, s_base, J.m16, 1, 0 >= J.split_from);
                 mma_commit(&ms->bar_u);
@@ -356,10 +380,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
             __syncwarp();
             if (lane == 0) mbar_arrive(&ms->bar_p);
             if (issuer) {
-                ok = wait_bar(ms, &ms->bar_p, ph_p, L.err) && ok;
-                ph_p ^= 1;
+                ms->ok = wait_bar(ms, &ms->bar_p, ms->ph_p, L.err) && ms->ok;
+                ms->ph_p ^= 1;
                 fence_after_sync();
-                if (ok) {
+                if (ms->ok) {
                     issue_gemm2<BF>(tbase, s_base, J.m16, p_split);
                     mma_commit(&ms->bar_g);
                 }
@@ -407,8 +431,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                         const float2 cl = make_float2(fminf(fmaxf(v.x, -tau), tau),
                                                       fminf(fmaxf(v.y, -tau), tau));
                         const float2 sv = sub2(v, cl);
-                        const float2 zn = fma2(b2, sub2(sv, sp[si]), sv);
-                        sp[si] = sv;
+                        float2& spv = si < kSpReg ? sp[si < kSpReg ? si : 0]
+                                                  : sp_smem[(si - kSpReg) * kThreads];
+                        const float2 zn = fma2(b2, sub2(sv, spv), sv);
+                        spv = sv;
                         zh[e] = pack2<BF>(zn);
                         zl[e] = pack2<BF>(sub2(zn, unpack2<BF>(zh[e])));
                     }
@@ -423,10 +449,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                     __syncwarp();
                     if (lane == 0) mbar_arrive(h ? &ms->bar_z1 : &ms->bar_z0);
                     if (issuer) {
-                        ok = wait_bar(ms, h ? &ms->bar_z1 : &ms->bar_z0, h ? ph_z1 : ph_z0, L.err) && ok;
-                        if (h) ph_z1 ^= 1; else ph_z0 ^= 1;
+                        uint32_t* ph = h ? &ms->ph_z1 : &ms->ph_z0;
+                        ms->ok = wait_bar(ms, h ? &ms->bar_z1 : &ms->bar_z0, *ph, L.err) && ms->ok;
+                        *ph ^= 1;
                         fence_after_sync();
-                        if (ok) {
+                        if (ms->ok) {
                             issue_gemm1_half<BF>(tbase, s_base, J.m16, h, z_split);
                             if (h) mma_commit(&ms->bar_u);
                         }
@@ -452,7 +479,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                 float acc = 0.f;
 #pragma unroll
                 for (int l = 0; l < 16; l += 2) {
-                    const float2 s2 = sp[16 * (kr >> 1) + 8 * (kr & 1) + l / 2];
+                    const int si = 16 * (kr >> 1) + 8 * (kr & 1) + l / 2;
+                    const float2 s2 = si < kSpReg ? sp[si < kSpReg ? si : 0]
+                                                  : sp_smem[(si - kSpReg) * kThreads];
                     acc = fmaf(s2.x, c_s[l * 16 + qq], acc);
                     acc = fmaf(s2.y, c_s[(l + 1) * 16 + qq], acc);
                 }
@@ -502,7 +531,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
         // drain: every MMA issued so far has completed before TMEM is freed
         mma_commit(&ms->bar_drain);
         mbar_wait(&ms->bar_drain, 0, kWaitNs);
-        if (!ok) mbar_wait(&ms->bar_load, ph_load, kWaitNs);
+        if (!ms->ok) mbar_wait(&ms->bar_load, ms->ph_load, kWaitNs);
     }
     fence_before_sync();
     __syncthreads();
