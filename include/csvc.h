@@ -95,6 +95,14 @@ int cs_ctx_destroy(cs_ctx* ctx);
  * bounded device-side waits since the last call: its outputs are incomplete.
  * Otherwise CS_OK.  The context stays usable either way. */
 int cs_ctx_status(cs_ctx* ctx);
+/* cs_ctx_set_debug: test hooks for the failure path, consumed by the next
+ * tensor-core decode launch of the context.  CS_DEBUG_DROP_ARRIVAL makes one
+ * warp of that launch withhold one barrier arrival, so that a device-side wait
+ * runs out (after 1 s): the launch then drains, its outputs are incomplete and
+ * cs_ctx_status reports CS_ETIMEDOUT; the context stays usable.  No GPU fault
+ * is involved. */
+#define CS_DEBUG_DROP_ARRIVAL 1
+int cs_ctx_set_debug(cs_ctx* ctx, int32_t flags);
 
 /* ---- plans: Phi, A = Phi Psi and the FISTA step --------------------------
  * cs_make_phi: build the plan for blocks of N = B*B pixels and M measurements

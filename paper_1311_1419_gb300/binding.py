@@ -63,6 +63,7 @@ _SIGS = {
     "cs_ctx_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_size_t]),
     "cs_ctx_destroy": (ctypes.c_int, [_vp]),
     "cs_ctx_status": (ctypes.c_int, [_vp]),
+    "cs_ctx_set_debug": (ctypes.c_int, [_vp, _i32]),
     "cs_make_phi": (ctypes.c_int, [_vp, _i32, _i32, ctypes.c_uint64, ctypes.POINTER(_vp)]),
     "cs_plan_destroy": (ctypes.c_int, [_vp]),
     "cs_plan_phi": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
@@ -150,6 +151,13 @@ def cs_ctx_destroy(ctx: int) -> None:
 
 def cs_ctx_status(ctx: int) -> None:
     _check(load().cs_ctx_status(ctx))
+
+
+CS_DEBUG_DROP_ARRIVAL = 1
+
+
+def cs_ctx_set_debug(ctx: int, flags: int) -> None:
+    _check(load().cs_ctx_set_debug(ctx, int(flags)))
 
 
 def cs_make_phi(ctx: int, n: int, m: int, seed: int) -> int:

@@ -337,6 +337,13 @@ double cs_raw_key_cr(int32_t gop, int32_t height, int32_t width, int32_t block, 
     return gop * px / (px + (gop - 1) * nblk * m);
 }
 
+int cs_ctx_set_debug(cs_ctx* ctx, int32_t flags) {
+    if (!ctx) return fail(CS_EINVAL, "null ctx");
+    if (flags & ~CS_DEBUG_DROP_ARRIVAL) return fail(CS_EINVAL, "unknown debug flag");
+    ctx->debug_flags.store(flags);
+    return CS_OK;
+}
+
 int cs_ctx_status(cs_ctx* ctx) {
     if (!ctx) return fail(CS_EINVAL, "null ctx");
     CS_CUDA_TRY(cudaSetDevice(ctx->device));

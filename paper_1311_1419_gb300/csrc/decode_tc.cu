@@ -63,7 +63,7 @@ constexpr int kSpReg = 24;            // momentum-state pairs kept in registers;
 constexpr uint32_t kOffSp = kOffMisc + 1024;             // [kPerThread/2 - kSpReg][kThreads] float2
 constexpr uint32_t kSmemBytes = kOffSp + (kPerThread / 2 - kSpReg) * kThreads * 8 + 1024;
 constexpr uint32_t kColAcc = 0, kColZHi = 256, kColZLo = 384;
-constexpr uint64_t kWaitNs = 2000000000ull;             // 2 s per wait
+constexpr uint64_t kWaitNs = 1000000000ull;             // 1 s per wait
 
 struct Misc {
     uint64_t bar_load, bar_u, bar_g, bar_p, bar_z0, bar_z1, bar_drain;
@@ -72,7 +72,7 @@ struct Misc {
     int next_tile;
     // the issuing thread's state (kept here, not in every thread's registers)
     uint32_t ph_z0, ph_z1, ph_p, ph_load;
-    int cur_job, ok;
+    int cur_job, ok, load_failed;
     uint32_t colmax[kTile];
 };
 
@@ -101,6 +101,7 @@ struct TcLaunch {
     const float* beta;
     int* err;
     int* tile_counter;      // zeroed before the launch; tiles are handed out in order
+    int drop_arrival;       // test hook: CTA 0 withholds its first residual-ready arrival
     int n_jobs;
     int n_tiles;
     TcJob jobs[kMaxJobs];
@@ -264,6 +265,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
             ms->ph_z0 = ms->ph_z1 = ms->ph_p = ms->ph_load = 0;
             ms->cur_job = -1;
             ms->ok = 1;
+            ms->load_failed = 0;
             fence_mbar_init();
         }
         __syncwarp();
@@ -284,6 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
     uint8_t* p_lo = sm + kOffPLo;
     float2* sp_smem = reinterpret_cast<float2*>(sm + kOffSp) + threadIdx.x;
     uint32_t ph_u = 0, ph_g = 0;                            // every thread
+    bool first_tile = true;
     for (;;) {
         // persistent CTAs take the next tile (jobs are ordered heaviest first)
         if (threadIdx.x == 0) ms->next_tile = atomicAdd(L.tile_counter, 1);
@@ -332,7 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                 mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
                 bulk_g2s(sm + kOffAHi, J.a_img, img, &ms->bar_load);
                 bulk_g2s(sm + kOffALo, J.a_img + img, img, &ms->bar_load);
-                ms->ok = wait_bar(ms, &ms->bar_load, ms->ph_load, L.err) && ms->ok;
+                const bool loaded = wait_bar(ms, &ms->bar_load, ms->ph_load, L.err);
+                if (!loaded) ms->load_failed = 1;
+                ms->ok = loaded && ms->ok;
                 ms->ph_load ^= 1;
                 ms->cur_job = jid;
             }
@@ -378,7 +383,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
             fence_proxy_async_smem();
             fence_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&ms->bar_p);
+            // (the test hook withholds warp 1's first arrival in CTA 0: the MMA
+            // thread's bounded wait then gives up and the CTA drains)
+            const bool withhold = L.drop_arrival && blockIdx.x == 0 && warp == 1 && k == 0 &&
+                                  first_tile;
+            if (lane == 0 && !withhold) mbar_arrive(&ms->bar_p);
             if (issuer) {
                 ms->ok = wait_bar(ms, &ms->bar_p, ms->ph_p, L.err) && ms->ok;
                 ms->ph_p ^= 1;
@@ -526,12 +535,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
         fence_before_sync();
         __syncthreads();   // the accumulator (holding T) is reused by the next tile
         fence_after_sync();
+        first_tile = false;
     }
     if (issuer) {
         // drain: every MMA issued so far has completed before TMEM is freed
         mma_commit(&ms->bar_drain);
         mbar_wait(&ms->bar_drain, 0, kWaitNs);
-        if (!ms->ok) mbar_wait(&ms->bar_load, ms->ph_load, kWaitNs);
+        // an A copy whose wait gave up may still be in flight: wait for it (bounded)
+        if (ms->load_failed) mbar_wait(&ms->bar_load, ms->ph_load ^ 1, kWaitNs);
     }
     fence_before_sync();
     __syncthreads();
@@ -651,6 +662,7 @@ static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool 
     L.err = jobs[0]->plan->ctx->err_dev;
     cs_ctx* ctx = jobs[0]->plan->ctx;
     L.tile_counter = ctx->counters_dev + (ctx->next_counter.fetch_add(1) % kTileCounters);
+    L.drop_arrival = ctx->debug_flags.exchange(0) & CS_DEBUG_DROP_ARRIVAL;
     cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     int tiles = 0;

@@ -41,6 +41,7 @@ struct cs_ctx {
     int* err_dev = nullptr;             // set to 1 by a kernel whose bounded wait gave up
     int* counters_dev = nullptr;        // csvc::kTileCounters tile counters, used round robin
     std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
+    std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
     // serving state
     std::mutex mu;
     csvc::Pool* pool = nullptr;         // device pool carved from the HBM budget, on first use
