@@ -273,6 +273,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true",
                     help="one decode call per M instead of one batched launch")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision decode measurement")
     ap.add_argument("--serving-sweep", action="store_true",
                     help="sweep the arrival rate to saturation, FP32 and mixed precision")
     args = ap.parse_args()
@@ -445,6 +447,38 @@ def main():
         bound = "alu"
     psnr = {m: float(np.mean(psnr_dev[m].cpu().numpy())) for m in wl["ms"]}
 
+    # the same batched decode with mixed precision: bulk products in one 16-bit
+    # MMA, the last 20 iterations FP32-grade (or split bf16 throughout)
+    mixed, mixed_out = None, {}
+    if tc_used and not args.no_mixed:
+        mixed = {}
+        for name, prec, tail in (("fp16_tail20", B.CS_FP16, 20), ("bf16_tail20", B.CS_BF16, 20),
+                                 ("bf16x2", B.CS_BF16X2, 0)):
+            mp = [B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops,
+                                lambda_rel=wl["lambda_rel"], engine=engine, precision=prec,
+                                fp32_tail_iters=tail) for m in wl["ms"]]
+            mo = [torch.empty((n_cs, h, w), dtype=torch.float32, device=dev) for _ in wl["ms"]]
+            evs = []
+            with torch.cuda.stream(stream):
+                for it in range(2 + 3):
+                    flush.zero_()
+                    a0 = torch.cuda.Event(enable_timing=True)
+                    a1 = torch.cuda.Event(enable_timing=True)
+                    a0.record(stream)
+                    B.cs_decode_batch(ctx, plan_list, mp, [keys_dev] * len(wl["ms"]),
+                                      [y_dev[m] for m in wl["ms"]], mo, None, stream)
+                    a1.record(stream)
+                    if it >= 2:
+                        evs.append((a0, a1))
+                torch.cuda.synchronize(dev)
+            B.cs_ctx_status(ctx)
+            mms = sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs)
+            ach = flops / (mms / 1e3) / 1e12
+            mixed[name] = {"decode_ms_per_step": mms, "achieved_tflops": ach,
+                           "frac": ach / peak,
+                           "vs_fp32_decode": dec_ms / mms}
+            mixed_out[name] = {m: mo[i] for i, m in enumerate(wl["ms"])}
+
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         rates = [50, 100, 200, 300, 400, 600] if args.serving_sweep else [100]
@@ -474,6 +508,16 @@ def main():
                 "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
                 "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want)),
             }
+        for name, outs in mixed_out.items():
+            errs = {}
+            for m in wl["ms"]:
+                got = outs[m][:n_sample].cpu().numpy().astype(np.float64)
+                want = ref[m]
+                orig = frames[1:1 + n_sample]
+                errs[str(m)] = {
+                    "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                    "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want))}
+            mixed[name]["vs_oracle"] = errs
 
     if rank == 0:
         line = {
@@ -501,6 +545,7 @@ def main():
             "decode_gflop_per_step": flops / 1e9,
             "psnr_db": {str(m): psnr[m] for m in wl["ms"]},
             "parity_vs_oracle": parity,
+            "mixed_precision": mixed,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

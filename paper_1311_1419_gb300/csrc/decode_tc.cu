@@ -198,23 +198,23 @@ __device__ __forceinline__ void stage_y(uint8_t* p_hi, uint8_t* p_lo, const floa
     cp_async_commit();
 }
 
-// GEMM1 for one half of K (h = 0: coefficients 0 .. 127, h = 1: 128 .. 255),
-// issued by the single MMA thread.
+// GEMM1 K-steps ks0 .. ks0 + nks - 1 (16 coefficients each; steps 0 .. 7 read
+// coefficients 0 .. 127, steps 8 .. 15 the rest), issued by the single MMA thread.
 template <bool BF>
-__device__ __forceinline__ void issue_gemm1_half(uint32_t tbase, uint32_t s_base, int m16, int h,
-                                                 bool split) {
+__device__ __forceinline__ void issue_gemm1_steps(uint32_t tbase, uint32_t s_base, int m16, int ks0,
+                                                  int nks, bool split) {
     const uint32_t rg = (uint32_t)(m16 / 8);
     const uint64_t d_hi = desc_sw128(s_base + kOffAHi, 16, 1024);
     const uint64_t d_lo = desc_sw128(s_base + kOffALo, 16, 1024);
     const uint32_t id1 = idesc_f16(128, (uint32_t)m16, BF ? 1u : 0u, 0u, 0u);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const uint32_t ks = (uint32_t)(8 * h + j);
+    for (int j = 0; j < nks; ++j) {
+        const uint32_t ks = (uint32_t)(ks0 + j);
         const uint32_t n0 = 16 * ks;
         const uint32_t b16 = ((n0 >> 6) * rg * 1024 + ((n0 & 63) >> 4) * 32) >> 4;
         const uint32_t zh = tbase + kColZHi + 8 * ks;
         const uint32_t zl = tbase + kColZLo + 8 * ks;
-        mma_f16_tmem_a(tbase + kColAcc, zh, d_hi + b16, id1, (h | j) != 0);
+        mma_f16_tmem_a(tbase + kColAcc, zh, d_hi + b16, id1, ks != 0);
         if (split) {
             mma_f16_tmem_a(tbase + kColAcc, zl, d_hi + b16, id1, 1);
             mma_f16_tmem_a(tbase + kColAcc, zh, d_lo + b16, id1, 1);
@@ -342,8 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                 ms->cur_job = jid;
             }
             if (J.iters > 0 && ms->ok) {
-                issue_gemm1_half<BF>(tbase, s_base, J.m16, 0, 0 >= J.split_from);
-                issue_gemm1_half<BF>(tbase, s_base, J.m16, 1, 0 >= J.split_from);
+                issue_gemm1_steps<BF>(tbase, s_base, J.m16, 0, 16, 0 >= J.split_from);
                 mma_commit(&ms->bar_u);
             }
         }
@@ -425,6 +424,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
             for (int h = 0; h < 2; ++h) {
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
+                    // the MMA thread feeds GEMM1's first half two K-steps at a time
+                    // between its own chunks of the second half, so that issuing
+                    // (which blocks while the tensor pipe's queue is full) does not
+                    // hold back its warp's share of the second half
+                    if (h == 1 && issuer && want_z && ms->ok)
+                        issue_gemm1_steps<BF>(tbase, s_base, J.m16, 2 * ch, 2, z_split);
                     const int o = coef_of(cgrp, h, ch);               // first coefficient
                     uint32_t g[8], zh[4], zl[4];
                     tmem_ld8(lane_addr + kColAcc + o, g);
@@ -462,9 +467,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                         ms->ok = wait_bar(ms, h ? &ms->bar_z1 : &ms->bar_z0, *ph, L.err) && ms->ok;
                         *ph ^= 1;
                         fence_after_sync();
-                        if (ms->ok) {
-                            issue_gemm1_half<BF>(tbase, s_base, J.m16, h, z_split);
-                            if (h) mma_commit(&ms->bar_u);
+                        if (ms->ok && h) {
+                            issue_gemm1_steps<BF>(tbase, s_base, J.m16, 8, 8, z_split);
+                            mma_commit(&ms->bar_u);
                         }
                     }
                 }
