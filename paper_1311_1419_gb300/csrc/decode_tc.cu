@@ -50,8 +50,16 @@ using namespace tc;
 constexpr int kN = 256;               // coefficients per block (16 x 16 blocks)
 constexpr int kMaxM16 = 128;          // measurement rows kept on chip
 constexpr int kTile = 128;            // blocks per tile = TMEM lanes = MMA M
-constexpr int kEpiWarps = 16;
-constexpr int kThreads = kEpiWarps * 32;     // thread 0 also issues the MMAs
+constexpr int kEpiWarps = 16;         // warps 4 .. 19
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kProdWarps = 4;         // warp 0 issues MMAs and copies A, warps 1 .. 3 stage y
+constexpr int kStageWarps = kProdWarps - 1;
+constexpr int kThreads = (kProdWarps + kEpiWarps) * 32;
+// registers per thread: at launch, then the producer and epilogue warpgroups
+constexpr int kLaunchRegs = 96, kProdRegs = 32, kEpiRegs = 112;
+static_assert(kProdWarps * 32 * kProdRegs + kEpiThreads * kEpiRegs <= kThreads * kLaunchRegs,
+              "register split exceeds the launch allocation");
+constexpr uint32_t kBarEpi = 1, kBarStage = 2;          // named barriers
 constexpr int kPerThread = kN / 4;    // coefficients per epilogue thread
 constexpr uint32_t kAImgMax = kMaxM16 * kN * 2;         // 64 KB per 16-bit image
 constexpr uint32_t kPImg = kTile * kMaxM16 * 2;         // 32 KB per 16-bit image
@@ -60,19 +68,17 @@ constexpr uint32_t kOffPHi = 2 * kAImgMax, kOffPLo = kOffPHi + kPImg;
 constexpr uint32_t kOffC = kOffPLo + kPImg;             // DCT matrix, 1 KB
 constexpr uint32_t kOffMisc = kOffC + 1024;
 constexpr int kSpReg = 24;            // momentum-state pairs kept in registers; the rest in smem
-constexpr uint32_t kOffSp = kOffMisc + 1024;             // [kPerThread/2 - kSpReg][kThreads] float2
-constexpr uint32_t kSmemBytes = kOffSp + (kPerThread / 2 - kSpReg) * kThreads * 8 + 1024;
+constexpr uint32_t kOffSp = kOffMisc + 1024;             // [kPerThread/2 - kSpReg][kEpiThreads] float2
+constexpr uint32_t kSmemBytes = kOffSp + (kPerThread / 2 - kSpReg) * kEpiThreads * 8 + 1024;
 constexpr uint32_t kColAcc = 0, kColZHi = 256, kColZLo = 384;
 constexpr uint64_t kWaitNs = 1000000000ull;             // 1 s per wait
 
 struct Misc {
-    uint64_t bar_load, bar_u, bar_g, bar_p, bar_z0, bar_z1, bar_drain;
+    uint64_t bar_load, bar_u, bar_g, bar_p, bar_z0, bar_z1, bar_y, bar_drain;
     uint32_t tmem_base;
     int abort;
     int next_tile;
-    // the issuing thread's state (kept here, not in every thread's registers)
-    uint32_t ph_z0, ph_z1, ph_p, ph_load;
-    int cur_job, ok, load_failed;
+    int load_failed;
     uint32_t colmax[kTile];
 };
 
@@ -242,56 +248,144 @@ __device__ __forceinline__ void issue_gemm2(uint32_t tbase, uint32_t s_base, int
     }
 }
 
-template <bool BF>
-__global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant__ TcLaunch L) {
-    extern __shared__ uint8_t smem_raw[];
-    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                             ~static_cast<uintptr_t>(1023));
-    Misc* ms = reinterpret_cast<Misc*>(sm + kOffMisc);
-    float* c_s = reinterpret_cast<float*>(sm + kOffC);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool issuer = threadIdx.x == 0;   // the one thread that issues MMAs and copies
-
-    if (warp == 0) {
-        if (lane == 0) {
-            mbar_init(&ms->bar_load, 1);
-            mbar_init(&ms->bar_u, 1);
-            mbar_init(&ms->bar_g, 1);
-            mbar_init(&ms->bar_p, kEpiWarps);
-            mbar_init(&ms->bar_z0, kEpiWarps);
-            mbar_init(&ms->bar_z1, kEpiWarps);
-            mbar_init(&ms->bar_drain, 1);
-            ms->abort = 0;
-            ms->ph_z0 = ms->ph_z1 = ms->ph_p = ms->ph_load = 0;
-            ms->cur_job = -1;
-            ms->ok = 1;
-            ms->load_failed = 0;
-            fence_mbar_init();
-        }
-        __syncwarp();
-        tmem_alloc(&ms->tmem_base, 512);
-        tmem_relinquish();
-    }
-    for (int i = threadIdx.x; i < 256; i += kThreads) c_s[i] = L.jobs[0].dct[i];
+// The tile loop every role runs: a CTA-wide barrier after the tile is fetched
+// (A), after the tile's set-up (B) and after its reconstruction (C).  Roles
+// are warp-uniform, so each warp meets the same barriers at its own code.
+__device__ __forceinline__ int fetch_tile(const TcLaunch& L, Misc* ms) {
+    if (threadIdx.x == 0) ms->next_tile = atomicAdd(L.tile_counter, 1);
+    __syncthreads();   // A
+    return ms->next_tile;
+}
+__device__ __forceinline__ void cta_sync() {
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    const uint32_t tbase = ms->tmem_base;
-    const uint32_t s_base = smem_u32(sm);
+}
 
-    const int q = warp & 3, cgrp = warp >> 2;
+// Warp 0: loads A when the CTA moves to another job and issues every MMA.  Only
+// lane 0 issues; the warp waits together.
+template <bool BF>
+__device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* sm, uint32_t tbase,
+                                         uint32_t s_base, int lane) {
+    uint32_t ph_p = 0, ph_z0 = 0, ph_z1 = 0, ph_load = 0;
+    int cur_job = -1;
+    bool ok = true;
+    for (;;) {
+        const int tile = fetch_tile(L, ms);
+        if (tile >= L.n_tiles) break;
+        const int jid = job_of(L, tile);
+        const TcJob& J = L.jobs[jid];
+        if (jid != cur_job) {
+            if (lane == 0) {
+                const uint32_t img = (uint32_t)J.m16 * kN * 2;
+                mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
+                bulk_g2s(sm + kOffAHi, J.a_img, img, &ms->bar_load);
+                bulk_g2s(sm + kOffALo, J.a_img + img, img, &ms->bar_load);
+            }
+            __syncwarp();
+            const bool loaded = wait_bar(ms, &ms->bar_load, ph_load, L.err);
+            if (!loaded) ms->load_failed = 1;
+            ok = loaded && ok;
+            ph_load ^= 1;
+            cur_job = jid;
+        }
+        cta_sync();   // B: Z = 0 is in tensor memory
+        if (J.iters > 0 && ok && lane == 0) {
+            issue_gemm1_steps<BF>(tbase, s_base, J.m16, 0, 16, 0 >= J.split_from);
+            mma_commit(&ms->bar_u);
+        }
+        __syncwarp();
+        for (int k = 0; k < J.iters; ++k) {
+            ok = wait_bar(ms, &ms->bar_p, ph_p, L.err) && ok;
+            ph_p ^= 1;
+            fence_after_sync();
+            if (ok && lane == 0) {
+                issue_gemm2<BF>(tbase, s_base, J.m16, k >= J.split_from);
+                mma_commit(&ms->bar_g);
+            }
+            __syncwarp();
+            if (k + 1 < J.iters) {
+                const bool z_split = k + 1 >= J.split_from;
+                ok = wait_bar(ms, &ms->bar_z0, ph_z0, L.err) && ok;
+                ph_z0 ^= 1;
+                fence_after_sync();
+                if (ok && lane == 0) issue_gemm1_steps<BF>(tbase, s_base, J.m16, 0, 8, z_split);
+                __syncwarp();
+                ok = wait_bar(ms, &ms->bar_z1, ph_z1, L.err) && ok;
+                ph_z1 ^= 1;
+                fence_after_sync();
+                if (ok && lane == 0) {
+                    issue_gemm1_steps<BF>(tbase, s_base, J.m16, 8, 8, z_split);
+                    mma_commit(&ms->bar_u);
+                }
+                __syncwarp();
+            }
+        }
+        cta_sync();   // C
+    }
+    if (lane == 0) {
+        // drain: every MMA issued so far has completed before TMEM is freed
+        mma_commit(&ms->bar_drain);
+        mbar_wait(&ms->bar_drain, 0, kWaitNs);
+        // an A copy whose wait gave up may still be in flight: wait for it (bounded)
+        if (ms->load_failed) mbar_wait(&ms->bar_load, ph_load ^ 1, kWaitNs);
+    }
+    __syncwarp();
+}
+
+// Warps 1..3: zero the P operand at a tile's start and stage y into its slots
+// for every iteration, as soon as GEMM2 of the previous iteration has consumed P.
+__device__ __forceinline__ void stage_role(const TcLaunch& L, Misc* ms, uint8_t* sm, int wi, int lane) {
+    uint8_t* p_hi = sm + kOffPHi;
+    uint8_t* p_lo = sm + kOffPLo;
+    const int st = wi * 32 + lane;
+    uint32_t ph_g = 0;
+    for (;;) {
+        const int tile = fetch_tile(L, ms);
+        if (tile >= L.n_tiles) break;
+        const TcJob& J = L.jobs[job_of(L, tile)];
+        const long long tile_row0 = (long long)(tile - J.tile_begin) * kTile;
+        const long long rows_left = J.rows - tile_row0;
+        const float* y_tile = J.y + tile_row0 * J.gs.m;
+        // padding rows m >= M and absent blocks stay zero: their U and y are zero
+        for (int i = st; i < (int)(2 * kPImg / 16); i += kStageWarps * 32)
+            reinterpret_cast<uint4*>(p_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
+        named_sync(kBarStage, kStageWarps * 32);
+        if (J.iters > 0) {
+            stage_y(p_hi, p_lo, y_tile, rows_left, J.gs.m, wi, lane, kStageWarps);
+            cp_async_arrive_noinc(&ms->bar_y);
+        }
+        cta_sync();   // B
+        for (int k = 0; k < J.iters; ++k) {
+            wait_bar(ms, &ms->bar_g, ph_g, L.err);   // GEMM2 of iteration k has read P
+            ph_g ^= 1;
+            if (k + 1 < J.iters) {
+                stage_y(p_hi, p_lo, y_tile, rows_left, J.gs.m, wi, lane, kStageWarps);
+                cp_async_arrive_noinc(&ms->bar_y);
+            }
+        }
+        cta_sync();   // C
+    }
+    cp_async_wait_all();
+}
+
+// Warps 4..19: the residual step, the gradient / soft-threshold / momentum step
+// and the reconstruction, on the tile's TMEM lanes.
+template <bool BF>
+__device__ __forceinline__ void epi_role(const TcLaunch& L, Misc* ms, uint8_t* sm, uint32_t tbase,
+                                         int warp, int lane) {
+    const float* c_s = reinterpret_cast<const float*>(sm + kOffC);
+    const int ew = warp - kProdWarps;
+    const int q = warp & 3, cgrp = ew >> 2;                 // TMEM lane quarter = warp % 4
     const int blk = 32 * q + lane;                          // TMEM lane = block of the tile
     const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
     uint8_t* p_hi = sm + kOffPHi;
     uint8_t* p_lo = sm + kOffPLo;
-    float2* sp_smem = reinterpret_cast<float2*>(sm + kOffSp) + threadIdx.x;
-    uint32_t ph_u = 0, ph_g = 0;                            // every thread
+    float2* sp_smem = reinterpret_cast<float2*>(sm + kOffSp) + (ew * 32 + lane);
+    uint32_t ph_u = 0, ph_g = 0, ph_y = 0;
     bool first_tile = true;
     for (;;) {
-        // persistent CTAs take the next tile (jobs are ordered heaviest first)
-        if (threadIdx.x == 0) ms->next_tile = atomicAdd(L.tile_counter, 1);
-        __syncthreads();
-        const int tile = ms->next_tile;
+        const int tile = fetch_tile(L, ms);
         if (tile >= L.n_tiles) break;
         const int jid = job_of(L, tile);
         const TcJob& J = L.jobs[jid];
@@ -306,10 +400,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
 #pragma unroll
         for (int i = 0; i < kSpReg; ++i) sp[i] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int i = kSpReg; i < kPerThread / 2; ++i) sp_smem[(i - kSpReg) * kThreads] = make_float2(0.f, 0.f);
+        for (int i = kSpReg; i < kPerThread / 2; ++i)
+            sp_smem[(i - kSpReg) * kEpiThreads] = make_float2(0.f, 0.f);
         float tau = 0.f;
-        // --- tile init: Z = 0 in TMEM ---
-        {
+        {   // Z = 0 in TMEM
             uint32_t zr[32];
 #pragma unroll
             for (int i = 0; i < 32; ++i) zr[i] = 0u;
@@ -318,42 +412,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
             if (cgrp == 0) ms->colmax[blk] = 0u;
             tmem_wait_st();
         }
-        // P slots start at zero (padding rows m >= M and absent blocks stay zero:
-        // their U and y are zero), then y is staged for the first residual step
-        const long long tile_row0 = (long long)(tile - J.tile_begin) * kTile;
-        const float* y_tile = J.y + tile_row0 * gs.m;
-        for (int i = threadIdx.x; i < (int)(2 * kPImg / 16); i += kThreads)
-            reinterpret_cast<uint4*>(p_hi)[i] = make_uint4(0u, 0u, 0u, 0u);
-        __syncthreads();
-        if (J.iters > 0) stage_y(p_hi, p_lo, y_tile, J.rows - tile_row0, gs.m, warp, lane, kEpiWarps);
-        fence_before_sync();
-        __syncthreads();   // also: every MMA of the previous tile has completed (its last G was waited)
-        fence_after_sync();
-        if (issuer) {
-            if (jid != ms->cur_job) {
-                const uint32_t img = (uint32_t)J.m16 * kN * 2;
-                mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
-                bulk_g2s(sm + kOffAHi, J.a_img, img, &ms->bar_load);
-                bulk_g2s(sm + kOffALo, J.a_img + img, img, &ms->bar_load);
-                const bool loaded = wait_bar(ms, &ms->bar_load, ms->ph_load, L.err);
-                if (!loaded) ms->load_failed = 1;
-                ms->ok = loaded && ms->ok;
-                ms->ph_load ^= 1;
-                ms->cur_job = jid;
-            }
-            if (J.iters > 0 && ms->ok) {
-                issue_gemm1_steps<BF>(tbase, s_base, J.m16, 0, 16, 0 >= J.split_from);
-                mma_commit(&ms->bar_u);
-            }
-        }
+        cta_sync();   // B
         for (int k = 0; k < J.iters; ++k) {
             const float bk = L.beta[k];
             // --- residual P = U - y (this thread: rows mbase .. mbase + mq) ---
             const bool ok_u = wait_bar(ms, &ms->bar_u, ph_u, L.err);
             ph_u ^= 1;
             fence_after_sync();
-            cp_async_wait_all();   // this thread's share of y has landed ...
-            __syncthreads();       // ... and so has everyone else's
+            wait_bar(ms, &ms->bar_y, ph_y, L.err);          // y is in the P slots
+            ph_y ^= 1;
             const float2 su2 = make_float2(J.su, J.su), sp2 = make_float2(J.sp, J.sp);
             const bool p_split = k >= J.split_from;
 #pragma unroll
@@ -382,26 +449,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
             fence_proxy_async_smem();
             fence_before_sync();
             __syncwarp();
-            // (the test hook withholds warp 1's first arrival in CTA 0: the MMA
-            // thread's bounded wait then gives up and the CTA drains)
-            const bool withhold = L.drop_arrival && blockIdx.x == 0 && warp == 1 && k == 0 &&
+            // (the test hook withholds one warp's first arrival in CTA 0: the MMA
+            // warp's bounded wait then gives up and the CTA drains)
+            const bool withhold = L.drop_arrival && blockIdx.x == 0 && ew == 1 && k == 0 &&
                                   first_tile;
             if (lane == 0 && !withhold) mbar_arrive(&ms->bar_p);
-            if (issuer) {
-                ms->ok = wait_bar(ms, &ms->bar_p, ms->ph_p, L.err) && ms->ok;
-                ms->ph_p ^= 1;
-                fence_after_sync();
-                if (ms->ok) {
-                    issue_gemm2<BF>(tbase, s_base, J.m16, p_split);
-                    mma_commit(&ms->bar_g);
-                }
-            }
 
             // --- gradient step, soft threshold, momentum ---
             const bool ok_g = wait_bar(ms, &ms->bar_g, ph_g, L.err);
             ph_g ^= 1;
             fence_after_sync();
-
             if (k == 0) {
                 // lambda_b = lambda_rel ||A^T y_b||_inf; at k = 0, G = -A^T y
                 float mx = 0.f;
@@ -414,22 +471,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                     for (int i = 0; i < 8; ++i) mx = fmaxf(mx, fabsf(__uint_as_float(g[i])));
                 }
                 atomicMax(&ms->colmax[blk], __float_as_uint(mx * J.sg));
-                __syncthreads();
+                named_sync(kBarEpi, kEpiThreads);
                 tau = J.lambda_rel * __uint_as_float(ms->colmax[blk]) * J.inv_l;
             }
             const bool want_z = k + 1 < J.iters;
-            const bool z_split = k + 1 >= J.split_from;
             const float2 b2 = make_float2(bk, bk);
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
 #pragma unroll
                 for (int ch = 0; ch < 4; ++ch) {
-                    // the MMA thread feeds GEMM1's first half two K-steps at a time
-                    // between its own chunks of the second half, so that issuing
-                    // (which blocks while the tensor pipe's queue is full) does not
-                    // hold back its warp's share of the second half
-                    if (h == 1 && issuer && want_z && ms->ok)
-                        issue_gemm1_steps<BF>(tbase, s_base, J.m16, 2 * ch, 2, z_split);
                     const int o = coef_of(cgrp, h, ch);               // first coefficient
                     uint32_t g[8], zh[4], zl[4];
                     tmem_ld8(lane_addr + kColAcc + o, g);
@@ -446,7 +496,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                                                       fminf(fmaxf(v.y, -tau), tau));
                         const float2 sv = sub2(v, cl);
                         float2& spv = si < kSpReg ? sp[si < kSpReg ? si : 0]
-                                                  : sp_smem[(si - kSpReg) * kThreads];
+                                                  : sp_smem[(si - kSpReg) * kEpiThreads];
                         const float2 zn = fma2(b2, sub2(sv, spv), sv);
                         spv = sv;
                         zh[e] = pack2<BF>(zn);
@@ -457,31 +507,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                         tmem_st4(lane_addr + kColZLo + o / 2, zl);
                     }
                 }
-                tmem_wait_st();
                 if (want_z) {
+                    tmem_wait_st();
                     fence_before_sync();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(h ? &ms->bar_z1 : &ms->bar_z0);
-                    if (issuer) {
-                        uint32_t* ph = h ? &ms->ph_z1 : &ms->ph_z0;
-                        ms->ok = wait_bar(ms, h ? &ms->bar_z1 : &ms->bar_z0, *ph, L.err) && ms->ok;
-                        *ph ^= 1;
-                        fence_after_sync();
-                        if (ms->ok && h) {
-                            issue_gemm1_steps<BF>(tbase, s_base, J.m16, 8, 8, z_split);
-                            mma_commit(&ms->bar_u);
-                        }
-                    }
                 }
             }
-            // GEMM2 has consumed P: stage y for the next residual step in its slots,
-            // while GEMM1 runs (warp 0, which issues the MMAs, stages nothing)
-            if (k + 1 < J.iters && warp > 0)
-                stage_y(p_hi, p_lo, y_tile, J.rows - tile_row0, gs.m, warp - 1, lane, kEpiWarps - 1);
         }
         // --- reconstruct: R = C^T S C, S = s^K (rows 4 cgrp .. 4 cgrp + 3 here) ---
+        // every MMA of the tile has completed (the last G was waited); the other
+        // warps of this lane quarter have read their last G columns
         fence_before_sync();
-        __syncthreads();   // every MMA of the tile has completed: the accumulator is free
+        named_sync(kBarEpi, kEpiThreads);
         fence_after_sync();
 #pragma unroll
         for (int kr = 0; kr < 4; ++kr) {
@@ -495,7 +533,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                 for (int l = 0; l < 16; l += 2) {
                     const int si = 16 * (kr >> 1) + 8 * (kr & 1) + l / 2;
                     const float2 s2 = si < kSpReg ? sp[si < kSpReg ? si : 0]
-                                                  : sp_smem[(si - kSpReg) * kThreads];
+                                                  : sp_smem[(si - kSpReg) * kEpiThreads];
                     acc = fmaf(s2.x, c_s[l * 16 + qq], acc);
                     acc = fmaf(s2.y, c_s[(l + 1) * 16 + qq], acc);
                 }
@@ -506,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
         }
         tmem_wait_st();
         fence_before_sync();
-        __syncthreads();
+        named_sync(kBarEpi, kEpiThreads);
         fence_after_sync();
         const int c_idx = live ? (int)(row / gs.nblk) : 0, bl = live ? (int)(row % gs.nblk) : 0;
         const int g_key = c_idx / (gs.g - 1);
@@ -537,21 +575,55 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
                     J.out_u8[(size_t)c_idx * frame_px + off] = (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
             }
         }
-        fence_before_sync();
-        __syncthreads();   // the accumulator (holding T) is reused by the next tile
-        fence_after_sync();
+        cta_sync();   // C: the accumulator (holding T) is reused by the next tile
         first_tile = false;
     }
-    if (issuer) {
-        // drain: every MMA issued so far has completed before TMEM is freed
-        mma_commit(&ms->bar_drain);
-        mbar_wait(&ms->bar_drain, 0, kWaitNs);
-        // an A copy whose wait gave up may still be in flight: wait for it (bounded)
-        if (ms->load_failed) mbar_wait(&ms->bar_load, ms->ph_load ^ 1, kWaitNs);
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant__ TcLaunch L) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+    Misc* ms = reinterpret_cast<Misc*>(sm + kOffMisc);
+    float* c_s = reinterpret_cast<float*>(sm + kOffC);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_init(&ms->bar_load, 1);
+            mbar_init(&ms->bar_u, 1);
+            mbar_init(&ms->bar_g, 1);
+            mbar_init(&ms->bar_p, kEpiWarps);
+            mbar_init(&ms->bar_z0, kEpiWarps);
+            mbar_init(&ms->bar_z1, kEpiWarps);
+            mbar_init(&ms->bar_y, kStageWarps * 32);
+            mbar_init(&ms->bar_drain, 1);
+            ms->abort = 0;
+            ms->load_failed = 0;
+            fence_mbar_init();
+        }
+        __syncwarp();
+        tmem_alloc(&ms->tmem_base, 512);
+        tmem_relinquish();
     }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
+    for (int i = threadIdx.x; i < 256; i += kThreads) c_s[i] = L.jobs[0].dct[i];
+    cta_sync();
+    const uint32_t tbase = ms->tmem_base;
+
+    // registers move from the producer warpgroup to the four epilogue warpgroups
+    // (the launch holds kThreads x kLaunchRegs; the split below sums to at most that)
+    if (warp < kProdWarps) {
+        regs_dec<kProdRegs>();
+        if (warp == 0)
+            mma_role<BF>(L, ms, sm, tbase, smem_u32(sm), lane);
+        else
+            stage_role(L, ms, sm, warp - 1, lane);
+    } else {
+        regs_inc<kEpiRegs>();
+        epi_role<BF>(L, ms, sm, tbase, warp, lane);
+    }
+    cta_sync();
     if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
@@ -680,6 +752,13 @@ static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool 
     L.n_tiles = tiles;
     const int sms = ctx->sm_count;
     const int grid = tiles < sms ? tiles : sms;
+    // The epilogue warpgroups' setmaxnreg.inc draws on the registers the CTA was
+    // launched with: never launch unless that allocation covers the split.
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, bf ? (const void*)k_fista_tc<true> : (const void*)k_fista_tc<false>);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs < kLaunchRegs || fa.maxThreadsPerBlock < kThreads)
+        return cudaErrorInvalidConfiguration;
     if (bf) {
         e = cudaFuncSetAttribute(k_fista_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kSmemBytes);
