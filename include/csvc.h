@@ -162,6 +162,23 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
                     float* const* frames_f32_dev, uint8_t* const* frames_u8_dev,
                     cs_stream_t stream);
 
+/* cs_autotune: pick the decode's launch shape for the plan's (N, M) by timing
+ * every candidate on the device: the persistent tensor-core kernel where the
+ * shape has one, and the plain per-block kernel at 64, 128, 256, 512 and 1024
+ * threads per block (those that cover N with at most 16 coefficients per
+ * thread).  Each runs a synthetic call (random measurements, zero key, up to
+ * 19456 blocks, 8 iterations, FP32); the fastest is recorded in ctx for this
+ * (N, M) and used from then on by FP32 decodes whose engine is
+ * CS_ENGINE_AUTO (an explicit engine still wins; mixed precision always takes
+ * the tensor-core kernel).  Synchronises the device: call it before serving or
+ * before capturing decodes into a CUDA graph.  Outputs (each may be NULL): the
+ * chosen engine (CS_ENGINE_TC or CS_ENGINE_PLAIN), the plain kernel's threads
+ * per block (0 for the tensor-core kernel) and the measured time per block per
+ * iteration in ns.  The paper has no counterpart (its decoder is a MATLAB
+ * solver). */
+int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t* plain_threads,
+                float* ns_per_block_iter);
+
 /* ---- quality and compression accounting (Sec. 4, Table I) ----------------
  * cs_psnr: per-frame PSNR 10 log10(255^2 / MSE) of test_dev (float32
  * [n][H][W]) against ref_dev (uint8 [n][H][W]), FP64 reductions on the device;

@@ -74,6 +74,8 @@ _SIGS = {
     "cs_decode_batch": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(cs_params),
                                        ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                        ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+    "cs_autotune": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                   ctypes.POINTER(ctypes.c_float)]),
     "cs_psnr": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "cs_total_cr": (ctypes.c_double, [_i32, ctypes.c_double, ctypes.c_double]),
     "cs_raw_key_cr": (ctypes.c_double, [_i32, _i32, _i32, _i32, _i32]),
@@ -158,6 +160,14 @@ CS_DEBUG_DROP_ARRIVAL = 1
 
 def cs_ctx_set_debug(ctx: int, flags: int) -> None:
     _check(load().cs_ctx_set_debug(ctx, int(flags)))
+
+
+def cs_autotune(ctx: int, plan: int):
+    """Time the decode shapes of the plan's (N, M) and record the fastest;
+    returns (engine, plain_threads, ns_per_block_iter)."""
+    eng, thr, ns = _i32(), _i32(), ctypes.c_float()
+    _check(load().cs_autotune(ctx, plan, ctypes.byref(eng), ctypes.byref(thr), ctypes.byref(ns)))
+    return eng.value, thr.value, ns.value
 
 
 def cs_make_phi(ctx: int, n: int, m: int, seed: int) -> int:

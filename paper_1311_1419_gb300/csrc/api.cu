@@ -88,10 +88,19 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
     d->lambda_rel = params->lambda_rel;
     d->precision = params->precision;
     d->beta = plan->ctx->beta_dev;
+    d->plain_threads = 0;
     int eng = params->engine;
     const bool tc_ok = tc_supported(plan, params->precision);
     if (eng == CS_ENGINE_TC && !tc_ok)
         return fail(CS_EINVAL, "tensor-core decode does not support this (N, M, precision)");
+    {   // the autotuned shape of this (N, M), if cs_autotune has run for it
+        std::lock_guard<std::mutex> lock(plan->ctx->tune_mu);
+        auto it = plan->ctx->tuned.find({plan->n, plan->m});
+        if (it != plan->ctx->tuned.end()) {
+            if (eng == CS_ENGINE_AUTO && params->precision == CS_FP32) eng = it->second.first;
+            d->plain_threads = it->second.second;
+        }
+    }
     if (eng == CS_ENGINE_AUTO) eng = tc_ok ? CS_ENGINE_TC : CS_ENGINE_PLAIN;
     if (eng == CS_ENGINE_PLAIN && params->precision != CS_FP32)
         return fail(CS_EINVAL, "the plain engine computes in FP32 only");

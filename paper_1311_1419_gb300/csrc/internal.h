@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -42,6 +43,9 @@ struct cs_ctx {
     int* counters_dev = nullptr;        // csvc::kTileCounters tile counters, used round robin
     std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
     std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
+    // autotuned decode shape per (N, M): (engine, plain-kernel threads per block)
+    std::mutex tune_mu;
+    std::map<std::pair<int, int>, std::pair<int, int>> tuned;
     // serving state
     std::mutex mu;
     csvc::Pool* pool = nullptr;         // device pool carved from the HBM budget, on first use
@@ -98,8 +102,11 @@ struct DecodeArgs {
     float lambda_rel;
     int precision;
     const float* beta;
+    int plain_threads;        // threads per block of the plain kernel; 0 = default rule
 };
 cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s);
+bool plain_threads_valid(int threads, int n);
+int plain_threads_default(int n);
 bool tc_supported(const cs_plan* plan, int precision);
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
 cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
