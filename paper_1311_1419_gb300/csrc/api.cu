@@ -183,6 +183,7 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     if (ctx->beta_dev) cudaFree(ctx->beta_dev);
     if (ctx->err_dev) cudaFree(ctx->err_dev);
     if (ctx->counters_dev) cudaFree(ctx->counters_dev);
+    if (ctx->tc8_scratch) cudaFree(ctx->tc8_scratch);
     delete ctx;
     return CS_OK;
 }
@@ -230,9 +231,16 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
         p->tc_ea = (int)floor(log2(16384.0 / (double)ranges[0]));
         const double pbound = 4.0 * 255.0 * (double)ranges[1];
         p->tc_ep = pbound > 16384.0 ? (int)floor(log2(16384.0 / pbound)) : 0;
-        e = cudaMalloc(&p->a_tc, tc_operand_bytes(m));
-        if (e == cudaSuccess) e = launch_tc_images(p->a, p->a_tc, n, m, p->tc_ea, s);
+        e = cudaMalloc(&p->a_tc, tc_operand_bytes(n, m));
+        if (e == cudaSuccess)
+            e = n == 1024 ? launch_tc8_images(p->a, p->a_tc, m, p->tc_ea, s)
+                          : launch_tc_images(p->a, p->a_tc, n, m, p->tc_ea, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && n == 1024) {
+            // the cluster decode's s^K all-gather, one per context
+            std::lock_guard<std::mutex> lock(ctx->mu);
+            if (!ctx->tc8_scratch) e = cudaMalloc(&ctx->tc8_scratch, tc8_scratch_bytes(ctx->sm_count));
+        }
     }
     if (gram) cudaFree(gram);
     if (lam_dev) cudaFree(lam_dev);

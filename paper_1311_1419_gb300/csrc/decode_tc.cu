@@ -683,8 +683,9 @@ int m16_of(int m) { return (m + 15) / 16 * 16; }
 
 }  // namespace
 
-bool tc_plan_supported(int n, int m) { return n == kN && m >= 1 && m <= kMaxM16; }
-size_t tc_operand_bytes(int m) { return 4ull * (size_t)m16_of(m) * kN * 2; }
+// 16 x 16 blocks on this file's kernel, 32 x 32 blocks on the cluster kernel
+bool tc_plan_supported(int n, int m) { return (n == kN || n == 1024) && m >= 1 && m <= kMaxM16; }
+size_t tc_operand_bytes(int n, int m) { return 4ull * (size_t)m16_of(m) * (size_t)n * 2; }
 
 cudaError_t launch_tc_ranges(const float* a, const float* phi, int n, int m, float* out,
                              cudaStream_t s) {
@@ -785,7 +786,12 @@ static double job_cost(const DecodeArgs& d) {
 
 cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
     std::vector<const DecodeArgs*> groups[2];
+    std::vector<DecodeArgs> big;   // 32 x 32 blocks: the cluster kernel
     for (int i = 0; i < n_jobs; ++i) {
+        if (jobs[i].plan->n != kN) {
+            big.push_back(jobs[i]);
+            continue;
+        }
         if ((long long)jobs[i].gs.n_cs * jobs[i].gs.nblk == 0) continue;
         const bool bf = jobs[i].precision == CS_BF16 || jobs[i].precision == CS_BF16X2;
         groups[bf ? 1 : 0].push_back(&jobs[i]);
@@ -801,6 +807,7 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
             if (e != cudaSuccess) return e;
         }
     }
+    if (!big.empty()) return launch_decode_tc8_batch(big.data(), (int)big.size(), s);
     return cudaSuccess;
 }
 

@@ -41,6 +41,7 @@ struct cs_ctx {
     float* beta_dev = nullptr;          // FISTA momentum (t_k - 1)/t_{k+1}, k = 1..kMaxIters
     int* err_dev = nullptr;             // set to 1 by a kernel whose bounded wait gave up
     int* counters_dev = nullptr;        // csvc::kTileCounters tile counters, used round robin
+    float* tc8_scratch = nullptr;       // s^K all-gather of the 32 x 32 cluster decode
     std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
     std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
     // autotuned decode shape per (N, M): (engine, plain-kernel threads per block)
@@ -110,6 +111,10 @@ int plain_threads_default(int n);
 bool tc_supported(const cs_plan* plan, int precision);
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
 cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
+// 32 x 32 blocks (N = 1024): clusters of 8 CTAs (decode_tc8.cu)
+cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
+cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaStream_t s);
+size_t tc8_scratch_bytes(int sm_count);
 
 // serving (serving.cu)
 void serving_destroy(cs_ctx* ctx);
@@ -120,7 +125,7 @@ cudaError_t launch_psnr(const uint8_t* ref, const float* test, int n_frames, int
 
 // tensor-core operand preparation (decode_tc.cu)
 bool tc_plan_supported(int n, int m);
-size_t tc_operand_bytes(int m);
+size_t tc_operand_bytes(int n, int m);
 cudaError_t launch_tc_ranges(const float* a, const float* phi, int n, int m, float* out,
                              cudaStream_t s);
 cudaError_t launch_tc_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s);
