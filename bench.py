@@ -28,14 +28,26 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
-WORKLOAD = {
-    "workload": "CIF 352x288, 64 frames, GOP 8 (1 raw key + 7 CS), 16x16 blocks (N=256), "
-                "M in {26,51,77,128} (CR sweep), Gaussian Phi N(0,1/M) Philox seed 0, "
-                "FISTA 300 iters, lambda=0.01*||A^T y||_inf, synthetic surveillance scene",
-    "height": 288, "width": 352, "frames": 64, "gop": 8, "block": 16,
-    "ms": [26, 51, 77, 128], "iters": 300, "lambda_rel": 0.01, "seed": 0,
+WORKLOADS = {
+    "cif": {
+        "workload": "CIF 352x288, 64 frames, GOP 8 (1 raw key + 7 CS), 16x16 blocks (N=256), "
+                    "M in {26,51,77,128} (CR sweep), Gaussian Phi N(0,1/M) Philox seed 0, "
+                    "FISTA 300 iters, lambda=0.01*||A^T y||_inf, synthetic surveillance scene",
+        "metric": "recovered Mpixel/s at fixed iters (CIF M-sweep, FISTA 300 iters)",
+        "height": 288, "width": 352, "frames": 64, "gop": 8, "block": 16,
+        "ms": [26, 51, 77, 128], "iters": 300, "lambda_rel": 0.01, "seed": 0, "oracle_frames": 5,
+    },
+    "720p": {
+        "workload": "720p 1280x720, 96 frames, GOP 16 (1 raw key + 15 CS), 32x32 blocks (N=1024), "
+                    "M=102 (10%), Gaussian Phi N(0,1/M) Philox seed 0, FISTA 300 iters, "
+                    "lambda=0.01*||A^T y||_inf, synthetic surveillance scene",
+        "metric": "recovered Mpixel/s at fixed iters (720p, 32x32 blocks, FISTA 300 iters)",
+        "height": 720, "width": 1280, "frames": 96, "gop": 16, "block": 32,
+        "ms": [102], "iters": 300, "lambda_rel": 0.01, "seed": 0, "oracle_frames": 1,
+    },
 }
-METRIC = "recovered Mpixel/s at fixed iters (CIF M-sweep, FISTA 300 iters)"
+WORKLOAD = WORKLOADS["cif"]
+METRIC = WORKLOAD["metric"]
 L2_FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
 
@@ -246,7 +258,7 @@ def run_reference(args, wl, frames):
     sample = ("first CS frame of the clip (396 blocks) at each M in %s, %d iters, per step"
               % (wl["ms"], wl["iters"]))
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "Mpixel/s",
+        "impl": "reference", "metric": wl["metric"], "value": value, "unit": "Mpixel/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -266,6 +278,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--engine", choices=["auto", "plain", "tc"], default="auto")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cif",
+                    help="cif: the CIF M-sweep (default); 720p: 32x32 blocks, M = 102")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-m", type=int, default=0,
                     help="run a single M of the sweep (profiling runs)")
@@ -280,7 +294,7 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps, always
     rank, world, local = dist_env()
-    wl = dict(WORKLOAD)
+    wl = dict(WORKLOADS[args.workload])
     if args.only_m:
         if args.only_m not in wl["ms"]:
             ap.error("--only-m must be one of %s" % wl["ms"])
@@ -435,8 +449,9 @@ def main():
     blocks = n_cs * nblk
     flops = sum(decode_flops(blocks, m, n, iters) for m in wl["ms"])
     peaks, peak_kind = read_peaks()
-    # every M of the CIF sweep (N = 256, M <= 128) has a tensor-core kernel
-    tc_used = engine != B.CS_ENGINE_PLAIN
+    # the tensor-core roofline applies when every plan decodes on the tensor cores
+    tc_used = engine == B.CS_ENGINE_TC or (
+        engine == B.CS_ENGINE_AUTO and all(t["engine"] == B.CS_ENGINE_TC for t in tuned.values()))
     achieved = flops / (dec_ms / 1e3) / 1e12
     if tc_used:
         # kind::f16 MMAs (fp16 operands): the measured bf16 peak x the nominal
@@ -494,7 +509,7 @@ def main():
     cpu = None
     parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_sample = 5
+        n_sample = wl["oracle_frames"]
         secs, pix, ref = oracle_sample(frames, wl, n_sample)
         cpu = {"value": pix / secs / 1e6, "unit": "Mpixel/s", "cores": os.cpu_count(),
                "kind": "oracle",
@@ -524,12 +539,13 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": "Mpixel/s", "n_gpus": world,
+            "metric": wl["metric"], "value": value, "unit": "Mpixel/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": wl["workload"], "engine": args.engine,
-                       "decode": "per-M calls" if args.no_batch else "one batched launch (4 plans)",
+                       "decode": "per-M calls" if args.no_batch else
+                       "one batched launch (%d plans)" % len(wl["ms"]),
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "replicas x%d" % world},
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
