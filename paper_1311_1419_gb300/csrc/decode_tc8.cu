@@ -66,9 +66,11 @@ constexpr uint32_t kOffAHi = 0, kOffALo = kAImg;
 constexpr uint32_t kOffPHi = 2 * kAImg, kOffPLo = kOffPHi + kPImg;
 constexpr uint32_t kRecvSlot = kMaxOwnerRows * kTile * 4;   // [row][block] float
 constexpr uint32_t kOffRecv = kOffPLo + kPImg;              // 7 slots
-constexpr uint32_t kOffLam = kOffRecv + (kCl - 1) * kRecvSlot;   // [7][128] float
+constexpr uint32_t kOffOwn = kOffRecv + (kCl - 1) * kRecvSlot;   // own partial of own rows, [row][block]
+constexpr uint32_t kOffLam = kOffOwn + kRecvSlot;                 // [7][128] float
 constexpr uint32_t kOffC = kOffLam + (kCl - 1) * kTile * 4;       // [32][32] float
-constexpr uint32_t kOffMisc = kOffC + kBlk * kBlk * 4;
+constexpr uint32_t kOffRowTab = kOffC + kBlk * kBlk * 4;        // [128] staging offset of row m
+constexpr uint32_t kOffMisc = kOffRowTab + kMaxM16 * 4;
 constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024;
 // tensor memory columns
 constexpr uint32_t kColG = 0, kColU = 128, kColZHi = 256, kColZLo = 320;
@@ -225,6 +227,12 @@ __device__ __forceinline__ void owner_rows(int p, int m16, int* row0, int* rows)
     const int g0 = p * base + (p < extra ? p : extra);
     *row0 = 8 * g0;
     *rows = 8 * ng;
+}
+// Owner of measurement row m (inverse of owner_rows).
+__device__ __forceinline__ int owner_of(int m, int m16) {
+    const int groups = m16 / 8, base = groups / kCl, extra = groups % kCl;
+    const int g = m >> 3, big = extra * (base + 1);
+    return g < big ? g / (base + 1) : extra + (g - big) / base;
 }
 // Slot of sender s in receiver r's incoming buffers (s != r): 0 .. 6.
 __device__ __forceinline__ int slot_of(int s, int r) { return (s - r + kCl - 1) % kCl; }
@@ -405,12 +413,12 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             // partial U of the other owners' rows is staged: send it
             ok = wait_bar(ms, &ms->bar_stage, ph_stage, L.err) && ok;
             ph_stage ^= 1;
-            if (ok && lane == 0) {
-                for (int d = 1; d < kCl; ++d) {
-                    const uint32_t p = (q + (uint32_t)d) % kCl;
-                    int row0_p, rows_p;
-                    owner_rows((int)p, J.m16, &row0_p, &rows_p);
-                    if (rows_p == 0) continue;
+            // (lane d - 1 serves peer q + d: the seven peers' copies go out together)
+            if (ok && lane < kCl - 1) {
+                const uint32_t p = (q + 1u + (uint32_t)lane) % kCl;
+                int row0_p, rows_p;
+                owner_rows((int)p, J.m16, &row0_p, &rows_p);
+                if (rows_p > 0) {
                     const uint32_t half = (uint32_t)rows_p * kTile * 2;   // bytes of each staged half
                     const uint32_t dst = mapa(s_base + kOffRecv + (uint32_t)slot_of((int)q, (int)p) * kRecvSlot, p);
                     const uint32_t rbar = mapa(smem_u32(&ms->bar_urecv), p);
@@ -428,17 +436,15 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             // this CTA's residual rows are written: broadcast them
             ok = wait_bar(ms, &ms->bar_pown, ph_pown, L.err) && ok;
             ph_pown ^= 1;
-            if (ok && lane == 0 && rows_q > 0) {
+            if (ok && lane < kCl - 1 && rows_q > 0) {
                 const uint32_t bytes = (uint32_t)rows_q * kTile * 2;
-                for (int d = 1; d < kCl; ++d) {
-                    const uint32_t p = (q + (uint32_t)d) % kCl;
-                    const uint32_t rbar = mapa(smem_u32(&ms->bar_precv), p);
-                    const uint32_t hi = s_base + kOffPHi + (uint32_t)row0_q * 256u;
-                    bulk_s2peer(mapa(hi, p), hi, bytes, rbar);
-                    if (split) {
-                        const uint32_t lo = s_base + kOffPLo + (uint32_t)row0_q * 256u;
-                        bulk_s2peer(mapa(lo, p), lo, bytes, rbar);
-                    }
+                const uint32_t p = (q + 1u + (uint32_t)lane) % kCl;
+                const uint32_t rbar = mapa(smem_u32(&ms->bar_precv), p);
+                const uint32_t hi = s_base + kOffPHi + (uint32_t)row0_q * 256u;
+                bulk_s2peer(mapa(hi, p), hi, bytes, rbar);
+                if (split) {
+                    const uint32_t lo = s_base + kOffPLo + (uint32_t)row0_q * 256u;
+                    bulk_s2peer(mapa(lo, p), lo, bytes, rbar);
                 }
             }
             __syncwarp();
@@ -529,6 +535,18 @@ __device__ __forceinline__ void epi_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             if (cgrp == 0) ms->colmax[blk] = 0u;
             tmem_wait_st();
         }
+        if (et < J.m16) {
+            // where row m of the partial U is staged: the own rows in kOffOwn, a
+            // peer's in the P slots of its rows (first half hi, the rest lo)
+            const int p = owner_of(et, J.m16);
+            int row0_p, rows_p;
+            owner_rows(p, J.m16, &row0_p, &rows_p);
+            const int r = et - row0_p, half = rows_p / 2;
+            reinterpret_cast<uint32_t*>(sm + kOffRowTab)[et] =
+                (uint32_t)p == q ? kOffOwn + r * 512
+                : r < half       ? kOffPHi + row0_p * 256 + r * 512
+                                 : kOffPLo + row0_p * 256 + (r - half) * 512;
+        }
         cta_sync();   // B
         for (int k = 0; k < J.iters; ++k) {
             const float bk = L.beta[k];
@@ -544,30 +562,20 @@ __device__ __forceinline__ void epi_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             const bool ok_u = wait_bar(ms, &ms->bar_u, ph_u, L.err);
             ph_u ^= 1;
             fence_after_sync();
-            float own[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int p = 0; p < kCl; ++p) {
-                int row0_p, rows_p;
-                owner_rows(p, J.m16, &row0_p, &rows_p);
-                const int per = rows_p / 4;
-                if (per == 0) continue;
-                uint32_t u[4];
-                tmem_ld4(lane_addr + kColU + (uint32_t)(row0_p + per * cgrp), u);
+            {
+                // this thread's quarter of the measurement rows, m = mq cgrp .. mq cgrp + mq - 1,
+                // to their owners' staging ([row][block] floats; the own rows to kOffOwn; a
+                // peer's rows, first half in P hi's slots of its rows, the rest in P lo's)
+                const int mq = J.m16 / 4;
+                uint32_t u[32];
+                tmem_ld32(lane_addr + kColU + (uint32_t)(mq * cgrp), u);
                 tmem_wait_ld();
-                if ((uint32_t)p == q) {
+                if (ok_u) {
+                    const uint32_t* tab = reinterpret_cast<const uint32_t*>(sm + kOffRowTab);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) own[i] = __uint_as_float(u[i]);
-                } else if (ok_u) {
-                    // staged rows r = per cgrp + i of owner p, [row][block] float;
-                    // the first half of the rows in P hi's slots of p's rows, the rest in P lo's
-                    const int half = rows_p / 2;
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        if (i >= per) break;
-                        const int r = per * cgrp + i;
-                        uint8_t* base = r < half ? p_hi + row0_p * 256 + r * 512
-                                                 : p_lo + row0_p * 256 + (r - half) * 512;
-                        *reinterpret_cast<float*>(base + blk * 4) = __uint_as_float(u[i]);
+                    for (int j = 0; j < 32; ++j) {
+                        if (j >= mq) break;
+                        *reinterpret_cast<uint32_t*>(sm + tab[mq * cgrp + j] + blk * 4) = u[j];
                     }
                 }
             }
@@ -582,7 +590,7 @@ __device__ __forceinline__ void epi_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             for (int i = 0; i < 4; ++i) {
                 if (i >= per_q) break;
                 const int r = per_q * cgrp + i;
-                float u = own[i];
+                float u = reinterpret_cast<const float*>(sm + kOffOwn)[r * kTile + blk];
 #pragma unroll
                 for (int s = 0; s < kCl - 1; ++s) u += recv[(s * kMaxOwnerRows + r) * kTile + blk];
                 const float pv = (u * J.su - yv[i]) * J.sp;
