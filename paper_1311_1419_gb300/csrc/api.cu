@@ -165,6 +165,11 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) ctx->streams.push_back(s);
     }
+    for (int i = 0; e == cudaSuccess && i < 3; ++i) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) ctx->fork_streams.push_back(s);
+    }
     if (e != cudaSuccess) {
         int st = cuda_fail(e, "context setup");
         cs_ctx_destroy(ctx);
@@ -180,6 +185,10 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
     serving_destroy(ctx);
     for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
+    for (cudaStream_t s : ctx->fork_streams) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+    }
     if (ctx->beta_dev) cudaFree(ctx->beta_dev);
     if (ctx->err_dev) cudaFree(ctx->err_dev);
     if (ctx->counters_dev) cudaFree(ctx->counters_dev);

@@ -61,15 +61,24 @@ static_assert(kProdWarps * 32 * kProdRegs + kEpiThreads * kEpiRegs <= kThreads *
               "register split exceeds the launch allocation");
 constexpr uint32_t kBarEpi = 1, kBarStage = 2;          // named barriers
 constexpr int kPerThread = kN / 4;    // coefficients per epilogue thread
-constexpr uint32_t kAImgMax = kMaxM16 * kN * 2;         // 64 KB per 16-bit image
-constexpr uint32_t kPImg = kTile * kMaxM16 * 2;         // 32 KB per 16-bit image
-constexpr uint32_t kOffAHi = 0, kOffALo = kAImgMax;
-constexpr uint32_t kOffPHi = 2 * kAImgMax, kOffPLo = kOffPHi + kPImg;
-constexpr uint32_t kOffC = kOffPLo + kPImg;             // DCT matrix, 1 KB
-constexpr uint32_t kOffMisc = kOffC + 1024;
-constexpr int kSpReg = 24;            // momentum-state pairs kept in registers; the rest in smem
-constexpr uint32_t kOffSp = kOffMisc + 1024;             // [kPerThread/2 - kSpReg][kEpiThreads] float2
-constexpr uint32_t kSmemBytes = kOffSp + (kPerThread / 2 - kSpReg) * kEpiThreads * 8 + 1024;
+constexpr uint32_t kPImg = kTile * kMaxM16 * 2;         // 32 KB per 16-bit P image (2 K atoms)
+// Shared-memory layout of a kernel instance for M16 <= MX: the A images take
+// MX x 512 bytes each, and the momentum pairs that do not stay in registers
+// take the rest (MX = 128: 24 pairs in registers, 8 in shared memory; MX = 96:
+// 16 and 16), so that the epilogue does not spill.
+template <int MX>
+struct Lay {
+    static constexpr int kMax = MX;
+    static constexpr int kSpReg = MX > 96 ? 24 : 16;   // momentum pairs in registers
+    static constexpr uint32_t kAImg = (uint32_t)MX * kN * 2;
+    static constexpr uint32_t kOffAHi = 0, kOffALo = kAImg;
+    static constexpr uint32_t kOffPHi = 2 * kAImg, kOffPLo = kOffPHi + kPImg;
+    static constexpr uint32_t kOffC = kOffPLo + kPImg;             // DCT matrix, 1 KB
+    static constexpr uint32_t kOffMisc = kOffC + 1024;
+    static constexpr uint32_t kOffSp = kOffMisc + 1024;             // [32 - kSpReg][kEpiThreads] float2
+    static constexpr uint32_t kSmemBytes = kOffSp + (kPerThread / 2 - kSpReg) * kEpiThreads * 8 + 1024;
+    static_assert(kSmemBytes <= 232448, "shared memory per CTA");
+};
 constexpr uint32_t kColAcc = 0, kColZHi = 256, kColZLo = 384;
 constexpr uint64_t kWaitNs = 1000000000ull;             // 1 s per wait
 
@@ -206,14 +215,14 @@ __device__ __forceinline__ void stage_y(uint8_t* p_hi, uint8_t* p_lo, const floa
 
 // GEMM1 K-steps ks0 .. ks0 + nks - 1 (16 coefficients each; steps 0 .. 7 read
 // coefficients 0 .. 127, steps 8 .. 15 the rest), issued by the single MMA thread.
-template <bool BF>
+template <bool BF, int MX>
 __device__ __forceinline__ void issue_gemm1_steps(uint32_t tbase, uint32_t s_base, int m16, int ks0,
                                                   int nks, bool split) {
     const uint32_t rg = (uint32_t)(m16 / 8);
-    const uint64_t d_hi = desc_sw128(s_base + kOffAHi, 16, 1024);
-    const uint64_t d_lo = desc_sw128(s_base + kOffALo, 16, 1024);
+    const uint64_t d_hi = desc_sw128(s_base + Lay<MX>::kOffAHi, 16, 1024);
+    const uint64_t d_lo = desc_sw128(s_base + Lay<MX>::kOffALo, 16, 1024);
     const uint32_t id1 = idesc_f16(128, (uint32_t)m16, BF ? 1u : 0u, 0u, 0u);
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < nks; ++j) {
         const uint32_t ks = (uint32_t)(ks0 + j);
         const uint32_t n0 = 16 * ks;
@@ -229,13 +238,14 @@ __device__ __forceinline__ void issue_gemm1_steps(uint32_t tbase, uint32_t s_bas
 }
 
 // GEMM2: G = P A at N = 256, K = m16.
-template <bool BF>
+template <bool BF, int MX>
 __device__ __forceinline__ void issue_gemm2(uint32_t tbase, uint32_t s_base, int m16, bool split) {
-    const uint64_t dp_hi = desc_sw128(s_base + kOffPHi, 16, 1024);
-    const uint64_t dp_lo = desc_sw128(s_base + kOffPLo, 16, 1024);
-    const uint64_t da_hi = desc_sw128(s_base + kOffAHi, (uint32_t)(m16 / 8) * 1024, 1024);
-    const uint64_t da_lo = desc_sw128(s_base + kOffALo, (uint32_t)(m16 / 8) * 1024, 1024);
+    const uint64_t dp_hi = desc_sw128(s_base + Lay<MX>::kOffPHi, 16, 1024);
+    const uint64_t dp_lo = desc_sw128(s_base + Lay<MX>::kOffPLo, 16, 1024);
+    const uint64_t da_hi = desc_sw128(s_base + Lay<MX>::kOffAHi, (uint32_t)(m16 / 8) * 1024, 1024);
+    const uint64_t da_lo = desc_sw128(s_base + Lay<MX>::kOffALo, (uint32_t)(m16 / 8) * 1024, 1024);
     const uint32_t id2 = idesc_f16(128, kN, BF ? 1u : 0u, 0u, 1u);
+#pragma unroll 1
     for (int ks = 0; ks < m16 / 16; ++ks) {
         const uint32_t m0 = 16 * (uint32_t)ks;
         const uint32_t a16 = ((m0 >> 6) * (kTile / 8) * 1024 + ((m0 & 63) >> 4) * 32) >> 4;
@@ -264,7 +274,7 @@ __device__ __forceinline__ void cta_sync() {
 
 // Warp 0: loads A when the CTA moves to another job and issues every MMA.  Only
 // lane 0 issues; the warp waits together.
-template <bool BF>
+template <bool BF, int MX>
 __device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* sm, uint32_t tbase,
                                          uint32_t s_base, int lane) {
     uint32_t ph_p = 0, ph_z0 = 0, ph_z1 = 0, ph_load = 0;
@@ -279,8 +289,8 @@ __device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* s
             if (lane == 0) {
                 const uint32_t img = (uint32_t)J.m16 * kN * 2;
                 mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
-                bulk_g2s(sm + kOffAHi, J.a_img, img, &ms->bar_load);
-                bulk_g2s(sm + kOffALo, J.a_img + img, img, &ms->bar_load);
+                bulk_g2s(sm + Lay<MX>::kOffAHi, J.a_img, img, &ms->bar_load);
+                bulk_g2s(sm + Lay<MX>::kOffALo, J.a_img + img, img, &ms->bar_load);
             }
             __syncwarp();
             const bool loaded = wait_bar(ms, &ms->bar_load, ph_load, L.err);
@@ -291,7 +301,7 @@ __device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* s
         }
         cta_sync();   // B: Z = 0 is in tensor memory
         if (J.iters > 0 && ok && lane == 0) {
-            issue_gemm1_steps<BF>(tbase, s_base, J.m16, 0, 16, 0 >= J.split_from);
+            issue_gemm1_steps<BF, MX>(tbase, s_base, J.m16, 0, 16, 0 >= J.split_from);
             mma_commit(&ms->bar_u);
         }
         __syncwarp();
@@ -300,7 +310,7 @@ __device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* s
             ph_p ^= 1;
             fence_after_sync();
             if (ok && lane == 0) {
-                issue_gemm2<BF>(tbase, s_base, J.m16, k >= J.split_from);
+                issue_gemm2<BF, MX>(tbase, s_base, J.m16, k >= J.split_from);
                 mma_commit(&ms->bar_g);
             }
             __syncwarp();
@@ -309,13 +319,13 @@ __device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* s
                 ok = wait_bar(ms, &ms->bar_z0, ph_z0, L.err) && ok;
                 ph_z0 ^= 1;
                 fence_after_sync();
-                if (ok && lane == 0) issue_gemm1_steps<BF>(tbase, s_base, J.m16, 0, 8, z_split);
+                if (ok && lane == 0) issue_gemm1_steps<BF, MX>(tbase, s_base, J.m16, 0, 8, z_split);
                 __syncwarp();
                 ok = wait_bar(ms, &ms->bar_z1, ph_z1, L.err) && ok;
                 ph_z1 ^= 1;
                 fence_after_sync();
                 if (ok && lane == 0) {
-                    issue_gemm1_steps<BF>(tbase, s_base, J.m16, 8, 8, z_split);
+                    issue_gemm1_steps<BF, MX>(tbase, s_base, J.m16, 8, 8, z_split);
                     mma_commit(&ms->bar_u);
                 }
                 __syncwarp();
@@ -335,9 +345,10 @@ __device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* s
 
 // Warps 1..3: zero the P operand at a tile's start and stage y into its slots
 // for every iteration, as soon as GEMM2 of the previous iteration has consumed P.
+template <int MX>
 __device__ __forceinline__ void stage_role(const TcLaunch& L, Misc* ms, uint8_t* sm, int wi, int lane) {
-    uint8_t* p_hi = sm + kOffPHi;
-    uint8_t* p_lo = sm + kOffPLo;
+    uint8_t* p_hi = sm + Lay<MX>::kOffPHi;
+    uint8_t* p_lo = sm + Lay<MX>::kOffPLo;
     const int st = wi * 32 + lane;
     uint32_t ph_g = 0;
     for (;;) {
@@ -371,17 +382,19 @@ __device__ __forceinline__ void stage_role(const TcLaunch& L, Misc* ms, uint8_t*
 
 // Warps 4..19: the residual step, the gradient / soft-threshold / momentum step
 // and the reconstruction, on the tile's TMEM lanes.
-template <bool BF>
+template <bool BF, int MX>
 __device__ __forceinline__ void epi_role(const TcLaunch& L, Misc* ms, uint8_t* sm, uint32_t tbase,
                                          int warp, int lane) {
-    const float* c_s = reinterpret_cast<const float*>(sm + kOffC);
+    using Y = Lay<MX>;
+    constexpr int kSpReg = Y::kSpReg;
+    const float* c_s = reinterpret_cast<const float*>(sm + Y::kOffC);
     const int ew = warp - kProdWarps;
     const int q = warp & 3, cgrp = ew >> 2;                 // TMEM lane quarter = warp % 4
     const int blk = 32 * q + lane;                          // TMEM lane = block of the tile
     const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
-    uint8_t* p_hi = sm + kOffPHi;
-    uint8_t* p_lo = sm + kOffPLo;
-    float2* sp_smem = reinterpret_cast<float2*>(sm + kOffSp) + (ew * 32 + lane);
+    uint8_t* p_hi = sm + Y::kOffPHi;
+    uint8_t* p_lo = sm + Y::kOffPLo;
+    float2* sp_smem = reinterpret_cast<float2*>(sm + Y::kOffSp) + (ew * 32 + lane);
     uint32_t ph_u = 0, ph_g = 0, ph_y = 0;
     bool first_tile = true;
     for (;;) {
@@ -580,13 +593,13 @@ __device__ __forceinline__ void epi_role(const TcLaunch& L, Misc* ms, uint8_t* s
     }
 }
 
-template <bool BF>
+template <bool BF, int MX>
 __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant__ TcLaunch L) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-    Misc* ms = reinterpret_cast<Misc*>(sm + kOffMisc);
-    float* c_s = reinterpret_cast<float*>(sm + kOffC);
+    Misc* ms = reinterpret_cast<Misc*>(sm + Lay<MX>::kOffMisc);
+    float* c_s = reinterpret_cast<float*>(sm + Lay<MX>::kOffC);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (warp == 0) {
@@ -616,12 +629,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
     if (warp < kProdWarps) {
         regs_dec<kProdRegs>();
         if (warp == 0)
-            mma_role<BF>(L, ms, sm, tbase, smem_u32(sm), lane);
+            mma_role<BF, MX>(L, ms, sm, tbase, smem_u32(sm), lane);
         else
-            stage_role(L, ms, sm, warp - 1, lane);
+            stage_role<MX>(L, ms, sm, warp - 1, lane);
     } else {
         regs_inc<kEpiRegs>();
-        epi_role<BF>(L, ms, sm, tbase, warp, lane);
+        epi_role<BF, MX>(L, ms, sm, tbase, warp, lane);
     }
     cta_sync();
     if (warp == 0) tmem_dealloc(tbase, 512);
@@ -734,7 +747,29 @@ static void fill_job(const DecodeArgs& d, int tile_begin, TcJob* J, bool* bf) {
 // One launch for up to kMaxJobs jobs of one operand type (fp16 or bf16).  Jobs
 // are laid out heaviest first (iterations x work per iteration) so that the
 // dynamic tile order approximates longest-processing-time scheduling.
-static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool bf, cudaStream_t s) {
+template <bool BF, int MX>
+static cudaError_t launch_kernel(const TcLaunch& L, int grid, cudaStream_t s) {
+    const void* fn = (const void*)k_fista_tc<BF, MX>;
+    // The epilogue warpgroups' setmaxnreg.inc draws on the registers the CTA was
+    // launched with: never launch unless that allocation covers the split.
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs < kLaunchRegs || fa.maxThreadsPerBlock < kThreads)
+        return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)Lay<MX>::kSmemBytes);
+    if (e != cudaSuccess) return e;
+    k_fista_tc<BF, MX><<<grid, kThreads, Lay<MX>::kSmemBytes, s>>>(L);
+    return cudaGetLastError();
+}
+
+// One launch for up to kMaxJobs jobs of one operand type (fp16 or bf16) and
+// one layout (M16 <= mx).  Jobs are laid out heaviest first (iterations x
+// work per iteration) so that the dynamic tile order approximates
+// longest-processing-time scheduling.
+static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool bf, int mx,
+                                cudaStream_t s) {
     TcLaunch L{};
     L.beta = jobs[0]->beta;
     L.err = jobs[0]->plan->ctx->err_dev;
@@ -753,25 +788,8 @@ static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool 
     L.n_tiles = tiles;
     const int sms = ctx->sm_count;
     const int grid = tiles < sms ? tiles : sms;
-    // The epilogue warpgroups' setmaxnreg.inc draws on the registers the CTA was
-    // launched with: never launch unless that allocation covers the split.
-    cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, bf ? (const void*)k_fista_tc<true> : (const void*)k_fista_tc<false>);
-    if (e != cudaSuccess) return e;
-    if (fa.numRegs < kLaunchRegs || fa.maxThreadsPerBlock < kThreads)
-        return cudaErrorInvalidConfiguration;
-    if (bf) {
-        e = cudaFuncSetAttribute(k_fista_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        k_fista_tc<true><<<grid, kThreads, kSmemBytes, s>>>(L);
-    } else {
-        e = cudaFuncSetAttribute(k_fista_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kSmemBytes);
-        if (e != cudaSuccess) return e;
-        k_fista_tc<false><<<grid, kThreads, kSmemBytes, s>>>(L);
-    }
-    return cudaGetLastError();
+    if (mx <= 96) return bf ? launch_kernel<true, 96>(L, grid, s) : launch_kernel<false, 96>(L, grid, s);
+    return bf ? launch_kernel<true, 128>(L, grid, s) : launch_kernel<false, 128>(L, grid, s);
 }
 
 static double job_cost(const DecodeArgs& d) {
@@ -785,7 +803,9 @@ static double job_cost(const DecodeArgs& d) {
 }
 
 cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
-    std::vector<const DecodeArgs*> groups[2];
+    // groups by operand type and shared-memory layout (M16 <= 96: more of the
+    // momentum state in shared memory, no register spills)
+    std::vector<const DecodeArgs*> groups[2][2];
     std::vector<DecodeArgs> big;   // 32 x 32 blocks: the cluster kernel
     for (int i = 0; i < n_jobs; ++i) {
         if (jobs[i].plan->n != kN) {
@@ -794,21 +814,59 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
         }
         if ((long long)jobs[i].gs.n_cs * jobs[i].gs.nblk == 0) continue;
         const bool bf = jobs[i].precision == CS_BF16 || jobs[i].precision == CS_BF16X2;
-        groups[bf ? 1 : 0].push_back(&jobs[i]);
+        const bool wide = m16_of(jobs[i].plan->m) > 96;
+        groups[bf ? 1 : 0][wide ? 1 : 0].push_back(&jobs[i]);
     }
-    for (int bf = 0; bf < 2; ++bf) {
-        std::vector<const DecodeArgs*>& g = groups[bf];
-        std::stable_sort(g.begin(), g.end(), [](const DecodeArgs* a, const DecodeArgs* b) {
-            return job_cost(*a) > job_cost(*b);
-        });
-        for (size_t i = 0; i < g.size(); i += kMaxJobs) {
-            const int n = (int)(g.size() - i < (size_t)kMaxJobs ? g.size() - i : (size_t)kMaxJobs);
-            cudaError_t e = launch_group(g.data() + i, n, bf == 1, s);
-            if (e != cudaSuccess) return e;
+    struct Launch {
+        const DecodeArgs* const* jobs;
+        int n;
+        bool bf;
+        int mx;
+    };
+    std::vector<Launch> launches;
+    for (int bf = 0; bf < 2; ++bf)
+        for (int w = 1; w >= 0; --w) {
+            std::vector<const DecodeArgs*>& g = groups[bf][w];
+            std::stable_sort(g.begin(), g.end(), [](const DecodeArgs* a, const DecodeArgs* b) {
+                return job_cost(*a) > job_cost(*b);
+            });
+            for (size_t i = 0; i < g.size(); i += kMaxJobs)
+                launches.push_back({g.data() + i, (int)std::min(g.size() - i, (size_t)kMaxJobs),
+                                    bf == 1, w ? 128 : 96});
         }
+    cudaError_t e = cudaSuccess;
+    if (launches.size() <= 1) {
+        if (!launches.empty())
+            e = launch_group(launches[0].jobs, launches[0].n, launches[0].bf, launches[0].mx, s);
+    } else {
+        // several persistent launches: fork them onto the context's own streams so
+        // that one's tail overlaps the next one's start, then join on s
+        cs_ctx* ctx = jobs[0].plan->ctx;
+        cudaEvent_t fork = nullptr;
+        e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+        std::vector<cudaEvent_t> joins;
+        for (size_t i = 0; e == cudaSuccess && i < launches.size(); ++i) {
+            cudaStream_t fs = i == 0 ? s : ctx->fork_streams[(i - 1) % ctx->fork_streams.size()];
+            if (i > 0) e = cudaStreamWaitEvent(fs, fork, 0);
+            if (e == cudaSuccess) e = launch_group(launches[i].jobs, launches[i].n, launches[i].bf,
+                                                   launches[i].mx, fs);
+            if (e == cudaSuccess && i > 0) {
+                cudaEvent_t j = nullptr;
+                e = cudaEventCreateWithFlags(&j, cudaEventDisableTiming);
+                if (e == cudaSuccess) e = cudaEventRecord(j, fs);
+                if (e == cudaSuccess) joins.push_back(j);
+                else if (j) cudaEventDestroy(j);
+            }
+        }
+        for (cudaEvent_t j : joins) {
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, j, 0);
+            cudaEventDestroy(j);
+        }
+        if (fork) cudaEventDestroy(fork);
     }
-    if (!big.empty()) return launch_decode_tc8_batch(big.data(), (int)big.size(), s);
-    return cudaSuccess;
+    if (e == cudaSuccess && !big.empty()) e = launch_decode_tc8_batch(big.data(), (int)big.size(), s);
+    return e;
 }
 
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s) {

@@ -251,6 +251,7 @@ __device__ __forceinline__ void issue_gemm1(uint32_t tbase, uint32_t s_base, int
     const uint64_t d_hi = desc_sw128(s_base + kOffAHi, 16, 1024);
     const uint64_t d_lo = desc_sw128(s_base + kOffALo, 16, 1024);
     const uint32_t id1 = idesc_f16(128, (uint32_t)m16, BF ? 1u : 0u, 0u, 0u);
+#pragma unroll 1
     for (int j = 0; j < nks; ++j) {
         const uint32_t ks = (uint32_t)(ks0 + j);
         const uint32_t n0 = 16 * ks;
@@ -268,6 +269,7 @@ __device__ __forceinline__ void issue_gemm1(uint32_t tbase, uint32_t s_base, int
 template <bool BF>
 __device__ __forceinline__ void issue_gemm2(uint32_t tbase, uint32_t s_base, int m16, bool split) {
     const uint32_t id2 = idesc_f16(128, kW, BF ? 1u : 0u, 1u, 1u);
+#pragma unroll 1
     for (int ks = 0; ks < m16 / 16; ++ks) {
         const uint64_t dp_hi = desc_sw128(s_base + kOffPHi + 4096u * ks, 1024, 2048);
         const uint64_t dp_lo = desc_sw128(s_base + kOffPLo + 4096u * ks, 1024, 2048);

@@ -54,6 +54,7 @@ struct cs_ctx {
     std::vector<csvc::Ticket*> live;
     uint64_t next_ticket = 1;
     std::vector<cudaStream_t> streams;
+    std::vector<cudaStream_t> fork_streams;   // extra persistent launches of one batched decode
     int next_stream = 0;
 };
 

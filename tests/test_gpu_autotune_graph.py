@@ -66,9 +66,13 @@ def test_autotuned_decode_matches_oracle(B, ctx, h, w, gop, b, m, iters):
 
 
 def test_batched_decode_replays_from_a_cuda_graph(B, ctx):
+    # two tensor-core layouts (M16 <= 96 and M = 128: launches forked onto the
+    # context's streams and joined), the 32 x 32 cluster kernel and the plain kernel
     cases = [_case(B, ctx, 144, 176, 4, 16, 26, 40, 1),
              _case(B, ctx, 96, 112, 5, 16, 64, 30, 2, precision=3, tail=10),
-             _case(B, ctx, 48, 64, 3, 8, 16, 30, 3)]          # plain kernel
+             _case(B, ctx, 80, 96, 3, 16, 128, 30, 6),
+             _case(B, ctx, 64, 96, 3, 32, 51, 20, 7),
+             _case(B, ctx, 48, 64, 3, 8, 16, 30, 3)]
     try:
         plans = [c[1] for c in cases]
         params = [c[2] for c in cases]
