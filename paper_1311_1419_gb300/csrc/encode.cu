@@ -15,35 +15,52 @@ constexpr int kKChunk = 32;
 
 __global__ void __launch_bounds__(256) k_encode(const uint8_t* __restrict__ frames,
                                                 const float* __restrict__ phi,
-                                                float* __restrict__ y, GopShape gs) {
+                                                float* __restrict__ y, GopShape gs, int lb) {
     __shared__ float rs[kKChunk][kRowsPerCta];
     __shared__ float ps[kKChunk][kMPerCta + 4];
+    // per block row of the tile: offsets of its top-left pixel in the CS frame and
+    // in the key frame, and its valid extent (blocks at the right / bottom edge
+    // are cropped; the padding is zero)
+    __shared__ long long row_cur[kRowsPerCta], row_key[kRowsPerCta];
+    __shared__ int row_vr[kRowsPerCta], row_vc[kRowsPerCta];
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
     const int row0 = blockIdx.x * kRowsPerCta;
     const int m0 = blockIdx.y * kMPerCta;
     const long long total_rows = (long long)gs.n_cs * gs.nblk;
     const size_t frame_px = (size_t)gs.h * gs.w;
+    if (tid < kRowsPerCta) {
+        const long long row = row0 + tid;
+        int vr = 0, vc = 0;
+        long long cur = 0, key = 0;
+        if (row < total_rows) {
+            const int c = (int)(row / gs.nblk), blk = (int)(row % gs.nblk);
+            const int g = c / (gs.g - 1), j = c % (gs.g - 1) + 1;
+            const int bi = blk / gs.nbc, bj = blk % gs.nbc;
+            const long long off = (long long)bi * gs.b * gs.w + (long long)bj * gs.b;
+            cur = (long long)(g * gs.g + j) * (long long)frame_px + off;
+            key = (long long)(g * gs.g) * (long long)frame_px + off;
+            vr = min(gs.b, gs.h - bi * gs.b);
+            vc = min(gs.b, gs.w - bj * gs.b);
+        }
+        row_cur[tid] = cur;
+        row_key[tid] = key;
+        row_vr[tid] = vr;
+        row_vc[tid] = vc;
+    }
+    __syncthreads();
 
     float acc[4][4] = {};
     for (int k0 = 0; k0 < gs.n; k0 += kKChunk) {
         // residual chunk: rows row0.., pixels k0..k0+31 of each block
         for (int e = tid; e < kRowsPerCta * kKChunk; e += 256) {
             const int rr = e / kKChunk, kk = e % kKChunk;
-            const long long row = row0 + rr;
             const int k = k0 + kk;
+            const int ky = lb >= 0 ? k >> lb : k / gs.b, kx = lb >= 0 ? k & (gs.b - 1) : k % gs.b;
             float v = 0.f;
-            if (row < total_rows && k < gs.n) {
-                const int c = (int)(row / gs.nblk), blk = (int)(row % gs.nblk);
-                const int g = c / (gs.g - 1), j = c % (gs.g - 1) + 1;
-                const int bi = blk / gs.nbc, bj = blk % gs.nbc;
-                const int py = bi * gs.b + k / gs.b, px = bj * gs.b + k % gs.b;
-                if (py < gs.h && px < gs.w) {
-                    const size_t off = (size_t)py * gs.w + px;
-                    const int cur = frames[(size_t)(g * gs.g + j) * frame_px + off];
-                    const int key = frames[(size_t)(g * gs.g) * frame_px + off];
-                    v = (float)(cur - key);
-                }
+            if (k < gs.n && ky < row_vr[rr] && kx < row_vc[rr]) {
+                const long long o = (long long)ky * gs.w + kx;
+                v = (float)((int)frames[row_cur[rr] + o] - (int)frames[row_key[rr] + o]);
             }
             rs[kk][rr] = v;
         }
@@ -87,7 +104,10 @@ cudaError_t launch_encode(const cs_plan* plan, const GopShape& gs, const uint8_t
     if (rows == 0) return cudaSuccess;
     dim3 grid((unsigned)((rows + kRowsPerCta - 1) / kRowsPerCta),
               (unsigned)((gs.m + kMPerCta - 1) / kMPerCta));
-    k_encode<<<grid, 256, 0, s>>>(frames, plan->phi, y, gs);
+    int lb = -1;   // log2 of the block side when it is a power of two
+    for (int i = 0; i < 7; ++i)
+        if ((1 << i) == gs.b) lb = i;
+    k_encode<<<grid, 256, 0, s>>>(frames, plan->phi, y, gs, lb);
     return cudaGetLastError();
 }
 
