@@ -24,6 +24,13 @@ What each function follows
   2-D DCT basis, min_s 1/2 ||A s - y||^2 + lambda ||s||_1 with A = Phi Psi,
   solved by FISTA (Beck & Teboulle, SIAM J. Imaging Sci. 2009) for a fixed
   number of iterations.
+* The paper's own recovery, TVAL3 (Sec. 4): Eq. (1) with Phi(x) the total
+  variation of the residual block, min TV(r) s.t. Phi r = y, by the augmented
+  Lagrangian / alternating-direction scheme of Li, Yin, Jiang and Zhang
+  (Comput. Optim. Appl. 2013), read as: anisotropic TV with forward differences
+  (zero at the last row and column), one shrinkage step for the splitting
+  variable w, one gradient step of fixed length 1 / (8 beta + mu L) for r and
+  one update of each multiplier per iteration, a fixed number of iterations.
 * Add the recovered residual back to the key frame: Sec. 3.2, Eq. (4).
 * Total compression ratio of a GOP: Sec. 3.1 and Table I (Sec. 4).
 
@@ -36,7 +43,8 @@ round-half-even and clamp.
 
 Pinned by ``tests/test_oracle_*.py`` against numpy's Philox, long-double
 sin/cos/log, scipy's DCT, LAPACK eigenvalues and solves, brute-force LASSO
-enumeration, closed forms and the Table I compression ratios.
+enumeration, a linear-programming solution of the TV problem, closed forms and
+the Table I compression ratios.
 """
 from __future__ import annotations
 
@@ -377,6 +385,63 @@ def decode_blocks(plan: Plan, y_blocks: np.ndarray, iters: int,
     yb = np.atleast_2d(np.asarray(y_blocks, dtype=np.float64))
     lam = block_lambda(plan.a, yb, lambda_rel)
     return fista(plan.a, yb, plan.lipschitz, lam, iters) @ plan.psi.T
+
+
+def tv_difference_matrix(b: int) -> np.ndarray:
+    """D = [Dx; Dy] (2N x N) of a B x B block in row-major vec order: forward
+    differences along rows (Dx) and columns (Dy), zero at the last column / row."""
+    n = b * b
+    d = np.zeros((2 * n, n))
+    for i in range(b):
+        for j in range(b):
+            k = i * b + j
+            if j < b - 1:
+                d[k, k + 1], d[k, k] = 1.0, -1.0
+            if i < b - 1:
+                d[n + k, k + b], d[n + k, k] = 1.0, -1.0
+    return d
+
+
+def tv_adm(phi: np.ndarray, y: np.ndarray, lipschitz: float, iters: int,
+           beta: float = 0.125, mu: float = 1.0) -> np.ndarray:
+    """TV recovery of every block (Eq. 1 with Phi(x) = TV, the TVAL3 choice of
+    Sec. 4): min ||D r||_1 s.t. Phi r = y by the augmented Lagrangian
+    ||w||_1 - nu^T (D r - w) + beta/2 ||D r - w||^2 - lam^T (Phi r - y)
+    + mu/2 ||Phi r - y||^2, minimised alternately in w (shrinkage) and r (one
+    gradient step of length 1 / (8 beta + mu L); 8 bounds ||D||^2, L the plan's
+    Lipschitz constant of Phi Phi^T), then nu -= beta (D r - w) and
+    lam -= mu (Phi r - y); r, nu, lam start at zero.
+
+    phi: [M][N]; y: [blocks][M].  Returns r: [blocks][N] (pixel domain).
+    """
+    n = phi.shape[1]
+    b = int(round(np.sqrt(n)))
+    d = tv_difference_matrix(b)
+    alpha = 1.0 / (8.0 * beta + mu * lipschitz)
+    r = np.zeros((y.shape[0], n))
+    nu = np.zeros((y.shape[0], 2 * n))
+    lam = np.zeros_like(y, dtype=np.float64)
+    for _ in range(iters):
+        dr = r @ d.T
+        w = soft(dr - nu / beta, 1.0 / beta)
+        g = (beta * (dr - w) - nu) @ d + (mu * (r @ phi.T - y) - lam) @ phi
+        r = r - alpha * g
+        nu = nu - beta * (r @ d.T - w)
+        lam = lam - mu * (r @ phi.T - y)
+    return r
+
+
+def decode_tv(plan: Plan, key_frames: np.ndarray, y: np.ndarray, gop: int, n_frames: int,
+              iters: int, beta: float = 0.125, mu: float = 1.0) -> np.ndarray:
+    """Every CS frame by TV recovery of its residual blocks, added back to its
+    GOP's key (Sec. 3.2, Eq. 4).  Returns float64 [n_cs][H][W]."""
+    _, h, w = key_frames.shape
+    cs = cs_frame_indices(n_frames, gop)
+    out = np.empty((len(cs), h, w))
+    for i, t in enumerate(cs):
+        r = tv_adm(plan.phi, y[i], plan.lipschitz, iters, beta, mu)
+        out[i] = key_frames[key_index(t, gop) // gop].astype(np.float64) + unblockify(r, h, w, plan.b)
+    return out
 
 
 def to_uint8(frames: np.ndarray) -> np.ndarray:
