@@ -287,6 +287,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true",
                     help="one decode call per M instead of one batched launch")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-tv", action="store_true", help="skip the TV-recovery measurement")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision decode measurement")
     ap.add_argument("--serving-sweep", action="store_true",
@@ -525,6 +526,29 @@ def main():
                            "vs_fp32_decode": dec_ms / mms}
             mixed_out[name] = {m: mo[i] for i, m in enumerate(wl["ms"])}
 
+    # TV recovery (the paper's TVAL3 regulariser) on the plain per-block kernel:
+    # the clip at the largest M, timed once after a warm-up call
+    tv = None
+    tv_m = max(wl["ms"])
+    if not args.no_tv and args.engine != "tc":
+        tv_out = torch.empty((n_cs, h, w), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            B.cs_decode_gop_tv(plans[tv_m], params[tv_m], keys_dev, y_dev[tv_m], tv_out, None, stream)
+            torch.cuda.synchronize(dev)
+            a0, a1 = ev_pair()
+            a0.record(stream)
+            B.cs_decode_gop_tv(plans[tv_m], params[tv_m], keys_dev, y_dev[tv_m], tv_out, None, stream)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+        B.cs_ctx_status(ctx)
+        tv_ms = a0.elapsed_time(a1)
+        tv_psnr = torch.empty(n_cs, dtype=torch.float64, device=dev)
+        B.cs_psnr(cs_dev, tv_out, n_cs, h, w, tv_psnr, stream)
+        torch.cuda.synchronize(dev)
+        tv = {"workload": "the clip at M=%d, %d iters, beta=1/8, mu=1, plain FP32 kernel" % (tv_m, iters),
+              "decode_ms": tv_ms, "mpixel_per_s": n_cs * h * w / (tv_ms / 1e3) / 1e6,
+              "psnr_db": float(np.mean(tv_psnr.cpu().numpy()))}
+
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         rates = [50, 100, 200, 300, 400, 600] if args.serving_sweep else [100]
@@ -564,6 +588,16 @@ def main():
                     "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
                     "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want))}
             mixed[name]["vs_oracle"] = errs
+        if tv is not None:
+            # the oracle's TV decode of the first CS frame
+            oplan = O.Plan(n, tv_m, wl["seed"])
+            y0 = O.encode(oplan, frames[:gop], gop)[:1]
+            r0 = O.tv_adm(oplan.phi, y0[0], oplan.lipschitz, iters)
+            want = frames[0].astype(np.float64) + O.unblockify(r0, h, w, b)
+            got = tv_out[0].cpu().numpy().astype(np.float64)
+            tv["vs_oracle"] = {"frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                               "dpsnr_db": float(O.psnr(frames[1:2], got[None]) -
+                                                 O.psnr(frames[1:2], want[None]))}
 
     if rank == 0:
         line = {
@@ -595,6 +629,7 @@ def main():
             "parity_vs_oracle": parity,
             "mixed_precision": mixed,
             "hbm_kernels": hbm_kernels,
+            "tv_recovery": tv,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)

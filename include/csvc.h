@@ -162,6 +162,23 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
                     float* const* frames_f32_dev, uint8_t* const* frames_u8_dev,
                     cs_stream_t stream);
 
+/* cs_decode_gop_tv: the same call as cs_decode_gop with the paper's own
+ * regulariser: every residual block r is recovered by total-variation
+ * minimisation, Eq. 1 with Phi(x) = ||D r||_1 (the TVAL3 decoder of Sec. 4),
+ * min ||D r||_1 s.t. Phi r = y, D the forward differences along the block's
+ * rows and columns (zero at its last column / row), by the augmented
+ * Lagrangian / alternating-direction scheme: per iteration one shrinkage step
+ * of the splitting variable w = D r, one gradient step of length
+ * 1 / (8 beta + mu L) for r (L = the plan's Lipschitz constant) and one update
+ * of each multiplier; params->iters iterations from zero.  beta and mu are the
+ * penalties of the splitting and of the measurement constraint (0.125 and 1
+ * suit 8-bit residuals).  FP32, plain per-block kernel (params->precision must
+ * be CS_FP32, params->engine not CS_ENGINE_TC; lambda_rel is not used).
+ * Buffers and errors as cs_decode_gop; CS_EINVAL for beta or mu <= 0. */
+int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float mu,
+                     const uint8_t* key_dev, const float* y_dev, float* frames_f32_dev,
+                     uint8_t* frames_u8_dev, cs_stream_t stream);
+
 /* cs_autotune: pick the decode's launch shape for the plan's (N, M) by timing
  * every candidate on the device: the persistent tensor-core kernel where the
  * shape has one, and the plain per-block kernel at 64, 128, 256, 512 and 1024

@@ -74,6 +74,8 @@ _SIGS = {
     "cs_decode_batch": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(cs_params),
                                        ctypes.POINTER(_vp), ctypes.POINTER(_vp),
                                        ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
+    "cs_decode_gop_tv": (ctypes.c_int, [_vp, ctypes.POINTER(cs_params), ctypes.c_float,
+                                        ctypes.c_float, _vp, _vp, _vp, _vp, _vp]),
     "cs_autotune": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                    ctypes.POINTER(ctypes.c_float)]),
     "cs_psnr": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
@@ -207,6 +209,14 @@ def cs_decode_gop(plan: int, params: cs_params, key_dev, y_dev, frames_f32_dev=N
                   frames_u8_dev=None, stream=None) -> None:
     _check(load().cs_decode_gop(plan, ctypes.byref(params), _ptr(key_dev), _ptr(y_dev),
                                 _ptr(frames_f32_dev), _ptr(frames_u8_dev), _stream(stream)))
+
+
+def cs_decode_gop_tv(plan: int, params: cs_params, key_dev, y_dev, frames_f32_dev=None,
+                     frames_u8_dev=None, stream=None, beta: float = 0.125, mu: float = 1.0) -> None:
+    """TV recovery (the paper's TVAL3 regulariser) of every CS frame of the call."""
+    _check(load().cs_decode_gop_tv(plan, ctypes.byref(params), float(beta), float(mu),
+                                   _ptr(key_dev), _ptr(y_dev), _ptr(frames_f32_dev),
+                                   _ptr(frames_u8_dev), _stream(stream)))
 
 
 def cs_decode_batch(ctx: int, plans, params, key_dev, y_dev, frames_f32_dev=None,
