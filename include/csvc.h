@@ -180,21 +180,22 @@ int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float m
                      uint8_t* frames_u8_dev, cs_stream_t stream);
 
 /* cs_autotune: pick the decode's launch shape for the plan's (N, M) by timing
- * every candidate on the device: the persistent tensor-core kernel where the
- * shape has one, and the plain per-block kernel at 64, 128, 256, 512 and 1024
- * threads per block (those that cover N with at most 16 coefficients per
- * thread).  Each runs a synthetic call (random measurements, zero key, up to
- * 19456 blocks, 8 iterations, FP32); the fastest is recorded in ctx for this
- * (N, M) and used from then on by FP32 decodes whose engine is
- * CS_ENGINE_AUTO (an explicit engine still wins; mixed precision always takes
- * the tensor-core kernel).  Synchronises the device: call it before serving or
- * before capturing decodes into a CUDA graph.  Outputs (each may be NULL): the
- * chosen engine (CS_ENGINE_TC or CS_ENGINE_PLAIN), the plain kernel's threads
- * per block (0 for the tensor-core kernel) and the measured time per block per
- * iteration in ns.  The paper has no counterpart (its decoder is a MATLAB
- * solver). */
+ * every candidate on the device: the tensor-core kernel where the shape has
+ * one (16 x 16 and 32 x 32 blocks, M <= 128), and the plain FP32 kernel at 64,
+ * 128, 256, 512 and 1024 threads per CTA with 1, 2, 4 or 8 measured blocks per
+ * CTA (the blocks of a CTA share each load of A; shapes whose shared memory
+ * exceeds 200 KB are skipped).  Each runs a synthetic call (random
+ * measurements, zero key, up to 19456 blocks, 8 iterations, FP32); the
+ * fastest is recorded in ctx for this (N, M) and used from then on by FP32
+ * decodes whose engine is CS_ENGINE_AUTO (an explicit engine still wins;
+ * mixed precision always takes the tensor-core kernel).  Synchronises the
+ * device: call it before serving or before capturing decodes into a CUDA
+ * graph.  Outputs (each may be NULL): the chosen engine (CS_ENGINE_TC or
+ * CS_ENGINE_PLAIN), the plain kernel's threads and blocks per CTA (0 for the
+ * tensor-core kernel) and the measured time per block per iteration in ns.
+ * The paper has no counterpart (its decoder is a MATLAB solver). */
 int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t* plain_threads,
-                float* ns_per_block_iter);
+                int32_t* plain_blocks_per_cta, float* ns_per_block_iter);
 
 /* ---- quality and compression accounting (Sec. 4, Table I) ----------------
  * cs_psnr: per-frame PSNR 10 log10(255^2 / MSE) of test_dev (float32

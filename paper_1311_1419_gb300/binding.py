@@ -77,7 +77,7 @@ _SIGS = {
     "cs_decode_gop_tv": (ctypes.c_int, [_vp, ctypes.POINTER(cs_params), ctypes.c_float,
                                         ctypes.c_float, _vp, _vp, _vp, _vp, _vp]),
     "cs_autotune": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
-                                   ctypes.POINTER(ctypes.c_float)]),
+                                   ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_float)]),
     "cs_psnr": (ctypes.c_int, [_vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "cs_total_cr": (ctypes.c_double, [_i32, ctypes.c_double, ctypes.c_double]),
     "cs_raw_key_cr": (ctypes.c_double, [_i32, _i32, _i32, _i32, _i32]),
@@ -166,10 +166,11 @@ def cs_ctx_set_debug(ctx: int, flags: int) -> None:
 
 def cs_autotune(ctx: int, plan: int):
     """Time the decode shapes of the plan's (N, M) and record the fastest;
-    returns (engine, plain_threads, ns_per_block_iter)."""
-    eng, thr, ns = _i32(), _i32(), ctypes.c_float()
-    _check(load().cs_autotune(ctx, plan, ctypes.byref(eng), ctypes.byref(thr), ctypes.byref(ns)))
-    return eng.value, thr.value, ns.value
+    returns (engine, plain_threads, plain_blocks_per_cta, ns_per_block_iter)."""
+    eng, thr, blk, ns = _i32(), _i32(), _i32(), ctypes.c_float()
+    _check(load().cs_autotune(ctx, plan, ctypes.byref(eng), ctypes.byref(thr), ctypes.byref(blk),
+                              ctypes.byref(ns)))
+    return eng.value, thr.value, blk.value, ns.value
 
 
 def cs_make_phi(ctx: int, n: int, m: int, seed: int) -> int:

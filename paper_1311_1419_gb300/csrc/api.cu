@@ -89,6 +89,7 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
     d->precision = params->precision;
     d->beta = plan->ctx->beta_dev;
     d->plain_threads = 0;
+    d->plain_blocks = 0;
     int eng = params->engine;
     const bool tc_ok = tc_supported(plan, params->precision);
     if (eng == CS_ENGINE_TC && !tc_ok)
@@ -97,8 +98,9 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
         std::lock_guard<std::mutex> lock(plan->ctx->tune_mu);
         auto it = plan->ctx->tuned.find({plan->n, plan->m});
         if (it != plan->ctx->tuned.end()) {
-            if (eng == CS_ENGINE_AUTO && params->precision == CS_FP32) eng = it->second.first;
-            d->plain_threads = it->second.second;
+            if (eng == CS_ENGINE_AUTO && params->precision == CS_FP32) eng = it->second[0];
+            d->plain_threads = it->second[1];
+            d->plain_blocks = it->second[2];
         }
     }
     if (eng == CS_ENGINE_AUTO) eng = tc_ok ? CS_ENGINE_TC : CS_ENGINE_PLAIN;

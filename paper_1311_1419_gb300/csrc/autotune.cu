@@ -1,8 +1,8 @@
 // Autotuner of the decode's launch shape per (N, M).
 //
 // The recovery of a plan's blocks can run on the persistent tensor-core kernel
-// (128-block tiles, where the shape has one) or on the plain kernel with 64 to
-// 1024 threads per block.  cs_autotune times every candidate the plan's shape
+// (where the shape has one) or on the plain kernel with 64 to 1024 threads
+// and 1, 2, 4 or 8 measured blocks per CTA.  cs_autotune times every candidate the plan's shape
 // admits on a synthetic call of the same N and M (random measurements, a zero
 // key, a few thousand blocks, a short fixed iteration count) and records the
 // fastest in the context; FP32 decodes with engine CS_ENGINE_AUTO then use it.
@@ -19,6 +19,7 @@ namespace {
 struct Candidate {
     int engine;
     int threads;
+    int blocks;
 };
 
 // Uniform values in [-0.5, 0.5) from a 64-bit LCG (Knuth's MMIX constants):
@@ -37,7 +38,7 @@ void fill_uniform(std::vector<float>& v, uint64_t seed) {
 using namespace csvc;
 
 extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t* plain_threads,
-                           float* ns_per_block_iter) {
+                           int32_t* plain_blocks_per_cta, float* ns_per_block_iter) {
     if (!ctx || !plan) return fail(CS_EINVAL, "null argument");
     if (plan->ctx != ctx) return fail(CS_EINVAL, "plan belongs to another context");
     CS_CUDA_TRY(cudaSetDevice(ctx->device));
@@ -59,9 +60,10 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
     gs.n_cs = 1;
 
     std::vector<Candidate> cands;
-    if (tc_supported(plan, CS_FP32)) cands.push_back({CS_ENGINE_TC, 0});
+    if (tc_supported(plan, CS_FP32)) cands.push_back({CS_ENGINE_TC, 0, 0});
     for (int t : {64, 128, 256, 512, 1024})
-        if (plain_threads_valid(t, n)) cands.push_back({CS_ENGINE_PLAIN, t});
+        for (int r : {1, 2, 4, 8})
+            if (plain_shape_valid(t, r, n, m)) cands.push_back({CS_ENGINE_PLAIN, t, r});
 
     std::vector<float> y_host((size_t)rows * m);
     fill_uniform(y_host, plan->seed);
@@ -81,7 +83,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
     if (e == cudaSuccess) e = cudaMemsetAsync(key, 0, px, s);
 
     const int iters = 8;
-    Candidate best{0, 0};
+    Candidate best{0, 0, 0};
     float best_ms = -1.f;
     for (size_t i = 0; e == cudaSuccess && i < cands.size(); ++i) {
         DecodeArgs d;
@@ -97,6 +99,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
         d.precision = CS_FP32;
         d.beta = ctx->beta_dev;
         d.plain_threads = cands[i].threads;
+        d.plain_blocks = cands[i].blocks;
         auto launch = [&]() {
             return cands[i].engine == CS_ENGINE_TC ? launch_decode_tc(d, s) : launch_decode_plain(d, s);
         };
@@ -122,10 +125,11 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
     if (best_ms < 0.f) return fail(CS_EINVAL, "no decode kernel for this (N, M)");
     {
         std::lock_guard<std::mutex> lock(ctx->tune_mu);
-        ctx->tuned[{n, m}] = {best.engine, best.threads};
+        ctx->tuned[{n, m}] = {best.engine, best.threads, best.blocks};
     }
     if (engine) *engine = best.engine;
     if (plain_threads) *plain_threads = best.threads;
+    if (plain_blocks_per_cta) *plain_blocks_per_cta = best.blocks;
     if (ns_per_block_iter) *ns_per_block_iter = (float)(1e6 * best_ms / 2.0 / ((double)rows * iters));
     return CS_OK;
 }

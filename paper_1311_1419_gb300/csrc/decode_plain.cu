@@ -1,116 +1,154 @@
-// K5 + K7: plain FP32 per-block decode.  One CTA recovers one measured block
-// by fixed-count FISTA on 1/2 ||A s - y||^2 + lambda ||s||_1 (Eq. 1 with an
-// l1 regulariser in the DCT basis; Beck & Teboulle 2009), then reconstructs
-// the residual r = Psi s (separable inverse DCT, R = C^T S C) and adds it back
-// to the GOP's key frame (Eq. 4).  A is read from global memory (L1/L2
-// resident) every iteration; the iterates stay in registers and shared memory.
-// This kernel is the simple SIMT baseline of the decode, and the path for the
-// (N, M) shapes the tensor-core kernel does not take.  Its thread count per
-// block (T) is a launch-time choice: the autotuner times the candidates.
+// K5 + K7: plain FP32 decode.  A CTA recovers R measured blocks by
+// fixed-count FISTA on 1/2 ||A s - y||^2 + lambda ||s||_1 (Eq. 1 with an l1
+// regulariser in the DCT basis; Beck & Teboulle 2009), then reconstructs each
+// residual r = Psi s (separable inverse DCT, R = C^T S C) and adds it back to
+// its GOP's key frame (Eq. 4).  A is read from global memory (L2 resident)
+// every iteration, once for all R blocks of the CTA: each loaded element of A
+// feeds R multiply-adds, so R divides the L2 traffic of A, which dominates
+// once A (M x N floats) no longer fits L1.  The iterates of the R blocks live
+// in shared memory.  This kernel is the simple SIMT baseline of the decode
+// and the path of the (N, M) shapes the tensor-core kernels do not take; its
+// launch shape (threads per CTA T, blocks per CTA R) is chosen by the
+// autotuner.
+#include <math.h>
+
 #include "internal.h"
 
 namespace csvc {
 namespace {
 
+
 __device__ __forceinline__ float soft_threshold(float v, float tau) {
     return v - fminf(fmaxf(v, -tau), tau);
 }
 
-template <int T, int PER>
+template <int T, int R>
 __global__ void __launch_bounds__(T) k_fista_plain(
     const float* __restrict__ a, const float* __restrict__ dct, const float* __restrict__ yall,
     const uint8_t* __restrict__ keys, float* __restrict__ out_f32, uint8_t* __restrict__ out_u8,
     GopShape gs, int iters, float lambda_rel, float inv_l, const float* __restrict__ beta) {
+    constexpr int nr = R;
     extern __shared__ float sm[];
     const int n = gs.n, m = gs.m, b = gs.b;
-    float* zs = sm;           // [N] current z (then s^K for recon)
-    float* rho = zs + n;      // [M] A z - y
-    float* ys = rho + m;      // [M]
-    float* cs = ys + m;       // [B][B] DCT matrix
-    float* tmp = cs + b * b;  // [N] recon scratch
-    __shared__ float red[T / 32];
+    float* zs = sm;               // [R][N] current z (then s^K for recon)
+    float* sps = zs + nr * n;     // [R][N] s^{k-1}
+    float* rho = sps + nr * n;    // [R][M] A z - y
+    float* ys = rho + nr * m;     // [R][M]
+    float* cs = ys + nr * m;      // [B][B] DCT matrix
+    float* tmp = zs;              // recon scratch: T = S C over z once s^K is in sps
+    __shared__ float red[R][T / 32];
+    __shared__ float taus[R];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long r = blockIdx.x;
-    const float* y = yall + r * m;
-    for (int i = tid; i < m; i += T) ys[i] = y[i];
-    for (int i = tid; i < b * b; i += T) cs[i] = dct[i];
-    for (int i = tid; i < n; i += T) zs[i] = 0.f;
-    for (int i = tid; i < m; i += T) rho[i] = ys[i];
-    __syncthreads();
-
-    // lambda_b = lambda_rel * ||A^T y||_inf
-    float amax = 0.f;
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int col = tid + j * T;
-        if (col < n) {
-            float g = 0.f;
-            for (int i = 0; i < m; ++i) g = fmaf(a[(size_t)i * n + col], rho[i], g);
-            amax = fmaxf(amax, fabsf(g));
-        }
+    const long long total = (long long)gs.n_cs * gs.nblk;
+    const long long row0 = (long long)blockIdx.x * nr;
+    // blocks beyond the call's last measure nothing (y = 0): their iterates stay 0
+    for (int e = tid; e < nr * m; e += T) {
+        const int q = e / m, i = e % m;
+        const float v = row0 + q < total ? yall[(row0 + q) * m + i] : 0.f;
+        ys[e] = v;
+        rho[e] = v;
     }
-    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-    if (lane == 0) red[warp] = amax;
+    for (int i = tid; i < b * b; i += T) cs[i] = dct[i];
+    for (int e = tid; e < nr * n; e += T) zs[e] = sps[e] = 0.f;
     __syncthreads();
-    amax = 0.f;
-    for (int w = 0; w < T / 32; ++w) amax = fmaxf(amax, red[w]);
-    const float tau = lambda_rel * amax * inv_l;
 
-    float z[PER], sp[PER];
+    // lambda_b = lambda_rel * ||A^T y_b||_inf
+    {
+        float amax[R];
 #pragma unroll
-    for (int j = 0; j < PER; ++j) z[j] = sp[j] = 0.f;
+        for (int q = 0; q < R; ++q) amax[q] = 0.f;
+        for (int col = tid; col < n; col += T) {
+            float g[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) g[q] = 0.f;
+            for (int i = 0; i < m; ++i) {
+                const float av = a[(size_t)i * n + col];
+#pragma unroll
+                for (int q = 0; q < R; ++q) g[q] = fmaf(av, rho[q * m + i], g[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) amax[q] = fmaxf(amax[q], fabsf(g[q]));
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            float v = amax[q];
+            for (int off = 16; off > 0; off >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, off));
+            if (lane == 0) red[q][warp] = v;
+        }
+        __syncthreads();
+        if (tid < nr) {
+            float v = 0.f;
+            for (int w = 0; w < T / 32; ++w) v = fmaxf(v, red[tid][w]);
+            taus[tid] = lambda_rel * v * inv_l;
+        }
+        __syncthreads();
+    }
 
     for (int k = 0; k < iters; ++k) {
-        // rho = A z - y, one warp per measurement row
+        // rho = A z - y, one warp per measurement row, all R blocks per load of A
         for (int i = warp; i < m; i += T / 32) {
             const float* arow = a + (size_t)i * n;
-            float acc = 0.f;
-            for (int col = lane; col < n; col += 32) acc = fmaf(arow[col], zs[col], acc);
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            if (lane == 0) rho[i] = acc - ys[i];
+            float acc[R];
+#pragma unroll
+            for (int q = 0; q < R; ++q) acc[q] = 0.f;
+            for (int col = lane; col < n; col += 32) {
+                const float av = arow[col];
+#pragma unroll
+                for (int q = 0; q < R; ++q) acc[q] = fmaf(av, zs[q * n + col], acc[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                float v = acc[q];
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                if (lane == 0) rho[q * m + i] = v - ys[q * m + i];
+            }
         }
         __syncthreads();
         const float bk = beta[k];
+        for (int col = tid; col < n; col += T) {
+            float g[R];
 #pragma unroll
-        for (int j = 0; j < PER; ++j) {
-            const int col = tid + j * T;
-            if (col < n) {
-                float g = 0.f;
-                for (int i = 0; i < m; ++i) g = fmaf(a[(size_t)i * n + col], rho[i], g);
-                const float s = soft_threshold(z[j] - g * inv_l, tau);
-                z[j] = s + bk * (s - sp[j]);
-                sp[j] = s;
-                zs[col] = z[j];  // every read of zs happened before the barrier above
+            for (int q = 0; q < R; ++q) g[q] = 0.f;
+            for (int i = 0; i < m; ++i) {
+                const float av = a[(size_t)i * n + col];
+#pragma unroll
+                for (int q = 0; q < R; ++q) g[q] = fmaf(av, rho[q * m + i], g[q]);
+            }
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                // every read of zs happened before the barrier above
+                const float s = soft_threshold(zs[q * n + col] - g[q] * inv_l, taus[q]);
+                zs[q * n + col] = s + bk * (s - sps[q * n + col]);
+                sps[q * n + col] = s;
             }
         }
         __syncthreads();
     }
 
-    // recon: S = s^K as B x B, T = S C, R = C^T T
-#pragma unroll
-    for (int j = 0; j < PER; ++j) {
-        const int col = tid + j * T;
-        if (col < n) zs[col] = sp[j];
-    }
-    __syncthreads();
-    for (int idx = tid; idx < n; idx += T) {
-        const int k = idx / b, q = idx % b;
+    // recon: S = s^K as B x B, T = S C (into zs), R = C^T T
+    for (int e = tid; e < nr * n; e += T) {
+        const int q = e / n, idx = e % n;
+        const int kk = idx / b, qq = idx % b;
+        const float* srow = sps + q * n + kk * b;
         float acc = 0.f;
-        for (int l = 0; l < b; ++l) acc = fmaf(zs[k * b + l], cs[l * b + q], acc);
-        tmp[idx] = acc;
+        for (int l = 0; l < b; ++l) acc = fmaf(srow[l], cs[l * b + qq], acc);
+        tmp[e] = acc;
     }
     __syncthreads();
-    const int c = (int)(r / gs.nblk), blk = (int)(r % gs.nblk);
-    const int g = c / (gs.g - 1);
-    const int bi = blk / gs.nbc, bj = blk % gs.nbc;
     const size_t frame_px = (size_t)gs.h * gs.w;
-    for (int idx = tid; idx < n; idx += T) {
-        const int p = idx / b, q = idx % b;
-        const int py = bi * b + p, px = bj * b + q;
+    for (int e = tid; e < nr * n; e += T) {
+        const int q = e / n, idx = e % n;
+        const long long r = row0 + q;
+        if (r >= total) continue;
+        const int c = (int)(r / gs.nblk), blk = (int)(r % gs.nblk);
+        const int g = c / (gs.g - 1);
+        const int bi = blk / gs.nbc, bj = blk % gs.nbc;
+        const int p = idx / b, qq = idx % b;
+        const int py = bi * b + p, px = bj * b + qq;
         if (py >= gs.h || px >= gs.w) continue;
         float acc = 0.f;
-        for (int k = 0; k < b; ++k) acc = fmaf(cs[k * b + p], tmp[k * b + q], acc);
+        for (int kk = 0; kk < b; ++kk) acc = fmaf(cs[kk * b + p], tmp[q * n + kk * b + qq], acc);
         const size_t off = (size_t)py * gs.w + px;
         const float v = (float)keys[(size_t)g * frame_px + off] + acc;
         if (out_f32) out_f32[(size_t)c * frame_px + off] = v;
@@ -118,37 +156,46 @@ __global__ void __launch_bounds__(T) k_fista_plain(
     }
 }
 
-template <int T, int PER>
-cudaError_t launch_per(const DecodeArgs& d, size_t smem, long long rows, cudaStream_t s) {
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_fista_plain<T, PER>,
+template <int T, int R>
+cudaError_t launch_tr(const DecodeArgs& d, size_t smem, long long rows, cudaStream_t s) {
+    // the opt-in covers dynamic + static shared memory (red, taus: under 2 KB)
+    if (smem + 2048 > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_fista_plain<T, R>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     const float inv_l = (float)(1.0 / d.plan->lipschitz);
-    k_fista_plain<T, PER><<<(unsigned)rows, T, smem, s>>>(
-        d.plan->a, d.plan->dct, d.y, d.key, d.out_f32, d.out_u8, d.gs, d.iters, d.lambda_rel,
-        inv_l, d.beta);
+    const long long ctas = (rows + R - 1) / R;
+    k_fista_plain<T, R><<<(unsigned)ctas, T, smem, s>>>(d.plan->a, d.plan->dct, d.y, d.key, d.out_f32,
+                                                        d.out_u8, d.gs, d.iters, d.lambda_rel, inv_l,
+                                                        d.beta);
     return cudaGetLastError();
 }
 
 template <int T>
-cudaError_t launch_threads(const DecodeArgs& d, size_t smem, long long rows, cudaStream_t s) {
-    const int per = (d.gs.n + T - 1) / T;
-    if (per <= 1) return launch_per<T, 1>(d, smem, rows, s);
-    if (per <= 2) return launch_per<T, 2>(d, smem, rows, s);
-    if (per <= 4) return launch_per<T, 4>(d, smem, rows, s);
-    if (per <= 8) return launch_per<T, 8>(d, smem, rows, s);
-    if (per <= 16) return launch_per<T, 16>(d, smem, rows, s);
-    return cudaErrorInvalidValue;
+cudaError_t launch_t(const DecodeArgs& d, int nr, size_t smem, long long rows, cudaStream_t s) {
+    switch (nr) {
+        case 1: return launch_tr<T, 1>(d, smem, rows, s);
+        case 2: return launch_tr<T, 2>(d, smem, rows, s);
+        case 4: return launch_tr<T, 4>(d, smem, rows, s);
+        default: return launch_tr<T, 8>(d, smem, rows, s);
+    }
+}
+
+size_t plain_smem(int n, int m, int b, int nr) {
+    return (size_t)(2 * nr * n + 2 * nr * m + b * b) * sizeof(float);
 }
 
 }  // namespace
 
-bool plain_threads_valid(int threads, int n) {
-    return (threads == 64 || threads == 128 || threads == 256 || threads == 512 ||
-            threads == 1024) && (n + threads - 1) / threads <= 16;
+bool plain_shape_valid(int threads, int blocks_per_cta, int n, int m) {
+    const int b = (int)lround(sqrt((double)n));
+    return (threads == 64 || threads == 128 || threads == 256 || threads == 512 || threads == 1024) &&
+           (blocks_per_cta == 1 || blocks_per_cta == 2 || blocks_per_cta == 4 || blocks_per_cta == 8) &&
+           plain_smem(n, m, b, blocks_per_cta) <= 200 * 1024;
 }
+
+bool plain_threads_valid(int threads, int n) { return plain_shape_valid(threads, 1, n, 1); }
 
 int plain_threads_default(int n) { return n <= 64 ? 64 : n <= 4096 ? 256 : 1024; }
 
@@ -156,15 +203,16 @@ cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s) {
     const GopShape& gs = d.gs;
     const long long rows = (long long)gs.n_cs * gs.nblk;
     if (rows == 0) return cudaSuccess;
-    const size_t smem = (size_t)(2 * gs.n + 2 * gs.m + gs.b * gs.b) * sizeof(float);
     const int t = d.plain_threads ? d.plain_threads : plain_threads_default(gs.n);
-    if (!plain_threads_valid(t, gs.n)) return cudaErrorInvalidValue;
+    const int nr = d.plain_blocks ? d.plain_blocks : 1;
+    if (!plain_shape_valid(t, nr, gs.n, gs.m)) return cudaErrorInvalidValue;
+    const size_t smem = plain_smem(gs.n, gs.m, gs.b, nr);
     switch (t) {
-        case 64: return launch_threads<64>(d, smem, rows, s);
-        case 128: return launch_threads<128>(d, smem, rows, s);
-        case 256: return launch_threads<256>(d, smem, rows, s);
-        case 512: return launch_threads<512>(d, smem, rows, s);
-        default: return launch_threads<1024>(d, smem, rows, s);
+        case 64: return launch_t<64>(d, nr, smem, rows, s);
+        case 128: return launch_t<128>(d, nr, smem, rows, s);
+        case 256: return launch_t<256>(d, nr, smem, rows, s);
+        case 512: return launch_t<512>(d, nr, smem, rows, s);
+        default: return launch_t<1024>(d, nr, smem, rows, s);
     }
 }
 

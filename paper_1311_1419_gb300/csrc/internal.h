@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <array>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -44,9 +45,9 @@ struct cs_ctx {
     float* tc8_scratch = nullptr;       // s^K all-gather of the 32 x 32 cluster decode
     std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
     std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
-    // autotuned decode shape per (N, M): (engine, plain-kernel threads per block)
+    // autotuned decode shape per (N, M): engine, plain-kernel threads and blocks per CTA
     std::mutex tune_mu;
-    std::map<std::pair<int, int>, std::pair<int, int>> tuned;
+    std::map<std::pair<int, int>, std::array<int, 3>> tuned;
     // serving state
     std::mutex mu;
     csvc::Pool* pool = nullptr;         // device pool carved from the HBM budget, on first use
@@ -104,10 +105,12 @@ struct DecodeArgs {
     float lambda_rel;
     int precision;
     const float* beta;
-    int plain_threads;        // threads per block of the plain kernel; 0 = default rule
+    int plain_threads;        // threads per CTA of the plain kernel; 0 = default rule
+    int plain_blocks;         // measured blocks per CTA of the plain kernel; 0 = 1
 };
 cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s);
 bool plain_threads_valid(int threads, int n);
+bool plain_shape_valid(int threads, int blocks_per_cta, int n, int m);
 int plain_threads_default(int n);
 bool tc_supported(const cs_plan* plan, int precision);
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
