@@ -140,8 +140,10 @@ def decode_flops(blocks: int, m: int, n: int, iters: int) -> float:
 
 SERVING = {
     "workload": "256 synthetic cameras, resolution QCIF/CIF/720p/1080p (p = .4/.3/.2/.1), "
-                "GOP uniform 4..32, 16x16 blocks, M/N uniform 5%..25%, Phi seed = camera id, "
-                "FISTA 200 iters; one request = one GOP decode; Poisson arrivals",
+                "GOP uniform 4..32, 16x16 or 32x32 blocks (p = .5/.5), M/N uniform 5%..25%, "
+                "Phi seed = camera id, FISTA 200 iters; one request = one GOP decode; Poisson "
+                "arrivals; mixed-precision runs fall back to FP32 where a shape has no "
+                "tensor-core kernel (32x32 blocks with M > 128)",
     "cameras": 256, "iters": 200, "seed": 7,
 }
 
@@ -161,13 +163,16 @@ def serving_run(B, torch, dev, precision, tail, rates, seconds, hbm_budget=8 << 
         for cid in range(SERVING["cameras"]):
             h, w = res[rng.choice(4, p=[0.4, 0.3, 0.2, 0.1])]
             gop = int(rng.integers(4, 33))
-            m = max(1, int(np.rint(256 * rng.uniform(0.05, 0.25))))
-            plan = B.cs_make_phi(ctx, 256, m, cid)
-            p = B.make_params(h, w, gop, 16, m, iters=SERVING["iters"], precision=precision,
-                              fp32_tail_iters=tail)
+            b = (16, 32)[rng.integers(2)]
+            m = max(1, int(np.rint(b * b * rng.uniform(0.05, 0.25))))
+            plan = B.cs_make_phi(ctx, b * b, m, cid)
+            tc = m <= 128
+            p = B.make_params(h, w, gop, b, m, iters=SERVING["iters"],
+                              precision=precision if tc else B.CS_FP32,
+                              fp32_tail_iters=tail if tc else 0)
             off = cid % (33 - gop)
             clip = base[(h, w)][off:off + gop]
-            nblk = (-(-h // 16)) * (-(-w // 16))
+            nblk = (-(-h // b)) * (-(-w // b))
             y = torch.empty((gop - 1, nblk, m), dtype=torch.float32, device=dev)
             B.cs_encode_gop(plan, p, torch.from_numpy(np.ascontiguousarray(clip)).to(dev), y,
                             stream)

@@ -197,14 +197,22 @@ bool plain_shape_valid(int threads, int blocks_per_cta, int n, int m) {
 
 bool plain_threads_valid(int threads, int n) { return plain_shape_valid(threads, 1, n, 1); }
 
-int plain_threads_default(int n) { return n <= 64 ? 64 : n <= 4096 ? 256 : 1024; }
+int plain_threads_default(int n) { return n >= 1024 ? 1024 : n >= 256 ? 256 : 128; }
+
+// The launch shape of an (N, M) that cs_autotune has not timed: the autotuner's
+// usual winner, as many blocks per CTA (up to 8) as shared memory allows.
+static int plain_blocks_default(int t, int n, int m) {
+    for (int r : {8, 4, 2})
+        if (plain_shape_valid(t, r, n, m)) return r;
+    return 1;
+}
 
 cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s) {
     const GopShape& gs = d.gs;
     const long long rows = (long long)gs.n_cs * gs.nblk;
     if (rows == 0) return cudaSuccess;
     const int t = d.plain_threads ? d.plain_threads : plain_threads_default(gs.n);
-    const int nr = d.plain_blocks ? d.plain_blocks : 1;
+    const int nr = d.plain_blocks ? d.plain_blocks : plain_blocks_default(t, gs.n, gs.m);
     if (!plain_shape_valid(t, nr, gs.n, gs.m)) return cudaErrorInvalidValue;
     const size_t smem = plain_smem(gs.n, gs.m, gs.b, nr);
     switch (t) {
