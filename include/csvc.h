@@ -182,9 +182,9 @@ int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float m
 /* cs_autotune: pick the decode's launch shape for the plan's (N, M) by timing
  * every candidate on the device: the tensor-core kernel where the shape has
  * one (16 x 16 and 32 x 32 blocks, M <= 128), and the plain FP32 kernel at 64,
- * 128, 256, 512 and 1024 threads per CTA with 1, 2, 4 or 8 measured blocks per
- * CTA (the blocks of a CTA share each load of A; shapes whose shared memory
- * exceeds 200 KB are skipped).  Each runs a synthetic call (random
+ * 128, 256, 512 and 1024 threads per CTA with 1, 2, 4, 8 or 16 (up to 512
+ * threads) measured blocks per CTA (the blocks of a CTA share each load of A;
+ * shapes whose shared memory exceeds 200 KB are skipped).  Each runs a synthetic call (random
  * measurements, zero key, up to 19456 blocks, 8 iterations, FP32); the
  * fastest is recorded in ctx for this (N, M) and used from then on by FP32
  * decodes whose engine is CS_ENGINE_AUTO (an explicit engine still wins;

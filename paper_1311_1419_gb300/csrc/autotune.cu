@@ -2,7 +2,7 @@
 //
 // The recovery of a plan's blocks can run on the persistent tensor-core kernel
 // (where the shape has one) or on the plain kernel with 64 to 1024 threads
-// and 1, 2, 4 or 8 measured blocks per CTA.  cs_autotune times every candidate the plan's shape
+// and 1, 2, 4, 8 or 16 measured blocks per CTA.  cs_autotune times every candidate the plan's shape
 // admits on a synthetic call of the same N and M (random measurements, a zero
 // key, a few thousand blocks, a short fixed iteration count) and records the
 // fastest in the context; FP32 decodes with engine CS_ENGINE_AUTO then use it.
@@ -62,7 +62,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
     std::vector<Candidate> cands;
     if (tc_supported(plan, CS_FP32)) cands.push_back({CS_ENGINE_TC, 0, 0});
     for (int t : {64, 128, 256, 512, 1024})
-        for (int r : {1, 2, 4, 8})
+        for (int r : {1, 2, 4, 8, 16})
             if (plain_shape_valid(t, r, n, m)) cands.push_back({CS_ENGINE_PLAIN, t, r});
 
     std::vector<float> y_host((size_t)rows * m);

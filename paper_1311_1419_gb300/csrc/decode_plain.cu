@@ -8,8 +8,8 @@
 // once A (M x N floats) no longer fits L1.  The iterates of the R blocks live
 // in shared memory.  This kernel is the simple SIMT baseline of the decode
 // and the path of the (N, M) shapes the tensor-core kernels do not take; its
-// launch shape (threads per CTA T, blocks per CTA R) is chosen by the
-// autotuner.
+// launch shape (threads per CTA T, blocks per CTA R = 1, 2, 4, 8 or 16) is
+// chosen by the autotuner.
 #include <math.h>
 
 #include "internal.h"
@@ -30,11 +30,12 @@ __global__ void __launch_bounds__(T) k_fista_plain(
     constexpr int nr = R;
     extern __shared__ float sm[];
     const int n = gs.n, m = gs.m, b = gs.b;
+    const int mp = (m + 3) & ~3;  // row stride of rho / ys: 16-byte aligned rows
     float* zs = sm;               // [R][N] current z (then s^K for recon)
     float* sps = zs + nr * n;     // [R][N] s^{k-1}
-    float* rho = sps + nr * n;    // [R][M] A z - y
-    float* ys = rho + nr * m;     // [R][M]
-    float* cs = ys + nr * m;      // [B][B] DCT matrix
+    float* rho = sm + ((2 * nr * n + 3) & ~3);   // [R][mp] A z - y (zero beyond M), 16-byte aligned
+    float* ys = rho + nr * mp;    // [R][mp]
+    float* cs = ys + nr * mp;     // [B][B] DCT matrix
     float* tmp = zs;              // recon scratch: T = S C over z once s^K is in sps
     __shared__ float red[R][T / 32];
     __shared__ float taus[R];
@@ -43,9 +44,9 @@ __global__ void __launch_bounds__(T) k_fista_plain(
     const long long total = (long long)gs.n_cs * gs.nblk;
     const long long row0 = (long long)blockIdx.x * nr;
     // blocks beyond the call's last measure nothing (y = 0): their iterates stay 0
-    for (int e = tid; e < nr * m; e += T) {
-        const int q = e / m, i = e % m;
-        const float v = row0 + q < total ? yall[(row0 + q) * m + i] : 0.f;
+    for (int e = tid; e < nr * mp; e += T) {
+        const int q = e / mp, i = e % mp;
+        const float v = (i < m && row0 + q < total) ? yall[(row0 + q) * m + i] : 0.f;
         ys[e] = v;
         rho[e] = v;
     }
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(T) k_fista_plain(
             for (int i = 0; i < m; ++i) {
                 const float av = a[(size_t)i * n + col];
 #pragma unroll
-                for (int q = 0; q < R; ++q) g[q] = fmaf(av, rho[q * m + i], g[q]);
+                for (int q = 0; q < R; ++q) g[q] = fmaf(av, rho[q * mp + i], g[q]);
             }
 #pragma unroll
             for (int q = 0; q < R; ++q) amax[q] = fmaxf(amax[q], fabsf(g[q]));
@@ -86,22 +87,36 @@ __global__ void __launch_bounds__(T) k_fista_plain(
     }
 
     for (int k = 0; k < iters; ++k) {
-        // rho = A z - y, one warp per measurement row, all R blocks per load of A
-        for (int i = warp; i < m; i += T / 32) {
-            const float* arow = a + (size_t)i * n;
-            float acc[R];
+        // rho = A z - y: a warp takes 4 measurement rows at a time, so each value
+        // of z loaded from shared memory feeds 4 rows x R blocks of multiply-adds
+        for (int i0 = warp * 4; i0 < m; i0 += (T / 32) * 4) {
+            float acc[4][R];
 #pragma unroll
-            for (int q = 0; q < R; ++q) acc[q] = 0.f;
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int q = 0; q < R; ++q) acc[r][q] = 0.f;
+            const int nrow = m - i0 < 4 ? m - i0 : 4;
             for (int col = lane; col < n; col += 32) {
-                const float av = arow[col];
+                float zv[R];
 #pragma unroll
-                for (int q = 0; q < R; ++q) acc[q] = fmaf(av, zs[q * n + col], acc[q]);
+                for (int q = 0; q < R; ++q) zv[q] = zs[q * n + col];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if (r < nrow) {
+                        const float av = a[(size_t)(i0 + r) * n + col];
+#pragma unroll
+                        for (int q = 0; q < R; ++q) acc[r][q] = fmaf(av, zv[q], acc[r][q]);
+                    }
+                }
             }
 #pragma unroll
-            for (int q = 0; q < R; ++q) {
-                float v = acc[q];
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                if (lane == 0) rho[q * m + i] = v - ys[q * m + i];
+            for (int r = 0; r < 4; ++r) {
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    float v = acc[r][q];
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+                    if (lane == 0 && r < nrow) rho[q * mp + i0 + r] = v - ys[q * mp + i0 + r];
+                }
             }
         }
         __syncthreads();
@@ -110,10 +125,20 @@ __global__ void __launch_bounds__(T) k_fista_plain(
             float g[R];
 #pragma unroll
             for (int q = 0; q < R; ++q) g[q] = 0.f;
-            for (int i = 0; i < m; ++i) {
-                const float av = a[(size_t)i * n + col];
+            // 4 rows of rho per 16-byte (broadcast) load; rows m .. mp - 1 of rho are
+            // zero, and A is read only below m
+            for (int i = 0; i < m; i += 4) {
+                float av[4];
 #pragma unroll
-                for (int q = 0; q < R; ++q) g[q] = fmaf(av, rho[q * m + i], g[q]);
+                for (int r = 0; r < 4; ++r) av[r] = i + r < m ? a[(size_t)(i + r) * n + col] : 0.f;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const float4 rv = *reinterpret_cast<const float4*>(rho + q * mp + i);
+                    g[q] = fmaf(av[0], rv.x, g[q]);
+                    g[q] = fmaf(av[1], rv.y, g[q]);
+                    g[q] = fmaf(av[2], rv.z, g[q]);
+                    g[q] = fmaf(av[3], rv.w, g[q]);
+                }
             }
 #pragma unroll
             for (int q = 0; q < R; ++q) {
@@ -178,12 +203,14 @@ cudaError_t launch_t(const DecodeArgs& d, int nr, size_t smem, long long rows, c
         case 1: return launch_tr<T, 1>(d, smem, rows, s);
         case 2: return launch_tr<T, 2>(d, smem, rows, s);
         case 4: return launch_tr<T, 4>(d, smem, rows, s);
-        default: return launch_tr<T, 8>(d, smem, rows, s);
+        case 8: return launch_tr<T, 8>(d, smem, rows, s);
+        default: return launch_tr<T, 16>(d, smem, rows, s);
     }
 }
 
 size_t plain_smem(int n, int m, int b, int nr) {
-    return (size_t)(2 * nr * n + 2 * nr * m + b * b) * sizeof(float);
+    const int mp = (m + 3) & ~3;
+    return (size_t)(((2 * nr * n + 3) & ~3) + 2 * nr * mp + b * b) * sizeof(float);
 }
 
 }  // namespace
@@ -191,7 +218,8 @@ size_t plain_smem(int n, int m, int b, int nr) {
 bool plain_shape_valid(int threads, int blocks_per_cta, int n, int m) {
     const int b = (int)lround(sqrt((double)n));
     return (threads == 64 || threads == 128 || threads == 256 || threads == 512 || threads == 1024) &&
-           (blocks_per_cta == 1 || blocks_per_cta == 2 || blocks_per_cta == 4 || blocks_per_cta == 8) &&
+           (blocks_per_cta == 1 || blocks_per_cta == 2 || blocks_per_cta == 4 || blocks_per_cta == 8 ||
+            (blocks_per_cta == 16 && threads <= 512)) &&
            plain_smem(n, m, b, blocks_per_cta) <= 200 * 1024;
 }
 
@@ -199,9 +227,11 @@ bool plain_threads_valid(int threads, int n) { return plain_shape_valid(threads,
 
 int plain_threads_default(int n) { return n >= 1024 ? 1024 : n >= 256 ? 256 : 128; }
 
-// The launch shape of an (N, M) that cs_autotune has not timed: the autotuner's
-// usual winner, as many blocks per CTA (up to 8) as shared memory allows.
+// The launch shape of an (N, M) that cs_autotune has not timed: as many blocks
+// per CTA as shared memory allows (up to 8, or 16 when A reaches 256 KB and L2
+// bandwidth bounds the kernel).
 static int plain_blocks_default(int t, int n, int m) {
+    if ((long long)n * m >= 65536 && plain_shape_valid(t <= 512 ? t : 512, 16, n, m)) return 16;
     for (int r : {8, 4, 2})
         if (plain_shape_valid(t, r, n, m)) return r;
     return 1;
@@ -211,8 +241,9 @@ cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s) {
     const GopShape& gs = d.gs;
     const long long rows = (long long)gs.n_cs * gs.nblk;
     if (rows == 0) return cudaSuccess;
-    const int t = d.plain_threads ? d.plain_threads : plain_threads_default(gs.n);
+    int t = d.plain_threads ? d.plain_threads : plain_threads_default(gs.n);
     const int nr = d.plain_blocks ? d.plain_blocks : plain_blocks_default(t, gs.n, gs.m);
+    if (!d.plain_threads && nr == 16 && t > 512) t = 512;
     if (!plain_shape_valid(t, nr, gs.n, gs.m)) return cudaErrorInvalidValue;
     const size_t smem = plain_smem(gs.n, gs.m, gs.b, nr);
     switch (t) {

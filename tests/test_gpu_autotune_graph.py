@@ -50,7 +50,7 @@ def test_autotuned_decode_matches_oracle(B, ctx, h, w, gop, b, m, iters):
         eng, thr, blk, ns = B.cs_autotune(ctx, plan)
         assert eng in (B.CS_ENGINE_TC, B.CS_ENGINE_PLAIN) and ns > 0
         if eng == B.CS_ENGINE_PLAIN:
-            assert thr in (64, 128, 256, 512, 1024) and blk in (1, 2, 4, 8)
+            assert thr in (64, 128, 256, 512, 1024) and blk in (1, 2, 4, 8, 16)
         else:
             assert b in (16, 32) and thr == 0 and blk == 0
         print("N=%d M=%d: engine %d threads %d blocks/CTA %d, %.2f ns per block-iteration"
