@@ -216,7 +216,7 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
     double* gram = nullptr;
     double* lam_dev = nullptr;
     float* ranges_dev = nullptr;
-    float ranges[2] = {0.f, 0.f};
+    float ranges[3] = {0.f, 0.f, 0.f};
     cudaStream_t s = nullptr;
     double lam = 0.0;
     const bool tc = tc_plan_supported(n, m);
@@ -227,7 +227,7 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
     if (e == cudaSuccess) e = cudaMalloc(&p->dct, (size_t)b * b * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&gram, (size_t)m * m * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&lam_dev, sizeof(double));
-    if (e == cudaSuccess && tc) e = cudaMalloc(&ranges_dev, 2 * sizeof(float));
+    if (e == cudaSuccess && tc) e = cudaMalloc(&ranges_dev, 3 * sizeof(float));
     if (e == cudaSuccess) e = launch_phi(p->phi, n, m, seed, s);
     if (e == cudaSuccess) e = launch_form_a(p->phi, p->a, p->dct, n, m, b, s);
     if (e == cudaSuccess) e = launch_lambda_max(p->phi, n, m, gram, lam_dev, s);
@@ -247,6 +247,13 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
             e = n == 1024 ? launch_tc8_images(p->a, p->a_tc, m, p->tc_ea, s)
                           : launch_tc_images(p->a, p->a_tc, n, m, p->tc_ea, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && n == 256 && ranges[2] > 0.f) {
+            // the tensor-core encode's Phi images, max |Phi| near 2^14
+            p->tc_ephi = (int)floor(log2(16384.0 / (double)ranges[2]));
+            e = cudaMalloc(&p->phi_tc, tc_operand_bytes(n, m));
+            if (e == cudaSuccess) e = launch_tc_images(p->phi, p->phi_tc, n, m, p->tc_ephi, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
         if (e == cudaSuccess && n == 1024) {
             // the cluster decode's s^K all-gather, one per context
             std::lock_guard<std::mutex> lock(ctx->mu);
@@ -278,6 +285,7 @@ int cs_plan_destroy(cs_plan* p) {
     if (p->a) cudaFree(p->a);
     if (p->dct) cudaFree(p->dct);
     if (p->a_tc) cudaFree(p->a_tc);
+    if (p->phi_tc) cudaFree(p->phi_tc);
     delete p;
     return CS_OK;
 }
@@ -306,7 +314,11 @@ int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_
     int st = make_shape(plan, params, &gs);
     if (st) return st;
     if (gs.n_cs > 0 && (!frames_dev || !y_dev)) return fail(CS_EINVAL, "null buffer");
-    cudaError_t e = launch_encode(plan, gs, frames_dev, y_dev, (cudaStream_t)stream);
+    if (params->engine < CS_ENGINE_AUTO || params->engine > CS_ENGINE_TC) return fail(CS_EINVAL, "bad engine");
+    // the tensor-core encode where the plan has one, unless the plain engine is asked for
+    const bool tc = params->engine != CS_ENGINE_PLAIN && encode_tc_supported(plan);
+    cudaError_t e = tc ? launch_encode_tc(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
+                       : launch_encode(plan, gs, frames_dev, y_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "encode launch");
     return CS_OK;
 }

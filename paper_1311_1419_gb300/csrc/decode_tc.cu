@@ -640,34 +640,41 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
     if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
-// Scales of the fp16 operands: max |A| and max_m sum_n |Phi[m][n]|.
+// Scales of the fp16 operands: max |A|, max_m sum_n |Phi[m][n]| and max |Phi|.
 __global__ void k_tc_ranges(const float* __restrict__ a, const float* __restrict__ phi, int n, int m,
                             float* __restrict__ out) {
-    __shared__ float red_a[32], red_l[32];
-    float amax = 0.f, lmax = 0.f;
+    __shared__ float red_a[32], red_l[32], red_p[32];
+    float amax = 0.f, lmax = 0.f, pmax = 0.f;
     for (int row = threadIdx.x >> 5; row < m; row += blockDim.x >> 5) {
         float l1 = 0.f;
         for (int c = threadIdx.x & 31; c < n; c += 32) {
             amax = fmaxf(amax, fabsf(a[(size_t)row * n + c]));
             l1 += fabsf(phi[(size_t)row * n + c]);
+            pmax = fmaxf(pmax, fabsf(phi[(size_t)row * n + c]));
         }
         for (int off = 16; off > 0; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
         lmax = fmaxf(lmax, l1);
     }
-    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    for (int off = 16; off > 0; off >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        pmax = fmaxf(pmax, __shfl_xor_sync(0xffffffffu, pmax, off));
+    }
     if ((threadIdx.x & 31) == 0) {
         red_a[threadIdx.x >> 5] = amax;
         red_l[threadIdx.x >> 5] = lmax;
+        red_p[threadIdx.x >> 5] = pmax;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        float x = 0.f, y = 0.f;
+        float x = 0.f, y = 0.f, z = 0.f;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
             x = fmaxf(x, red_a[w]);
             y = fmaxf(y, red_l[w]);
+            z = fmaxf(z, red_p[w]);
         }
         out[0] = x;
         out[1] = y;
+        out[2] = z;
     }
 }
 

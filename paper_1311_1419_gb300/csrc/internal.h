@@ -71,6 +71,10 @@ struct cs_plan {
     // lo, bf16 hi, bf16 lo); NULL when the shape has no tensor-core kernel
     uint8_t* a_tc = nullptr;
     int tc_ea = 0;            // log2 scale of A in the 16-bit operands
+    // fp16 hi / lo (then bf16 hi / lo) images of Phi * 2^tc_ephi for the
+    // tensor-core encode (16 x 16 blocks, M <= 128); NULL otherwise
+    uint8_t* phi_tc = nullptr;
+    int tc_ephi = 0;
     int tc_ep = 0;            // log2 scale of the residual operand P
 };
 
@@ -89,6 +93,9 @@ struct GopShape {
     int nbr, nbc, nblk;   // block rows, block cols, blocks per frame
     int n_cs;             // CS frames in the call = n_gops * (g - 1)
 };
+bool encode_tc_supported(const cs_plan* plan);
+cudaError_t launch_encode_tc(const cs_plan* plan, const GopShape& gs, const uint8_t* frames, float* y,
+                             cudaStream_t s);
 cudaError_t launch_encode(const cs_plan* plan, const GopShape& gs, const uint8_t* frames,
                           float* y, cudaStream_t s);
 
