@@ -769,8 +769,10 @@ cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaS
     return cudaGetLastError();
 }
 
+static size_t tc8_slot_floats(int sm_count) { return (size_t)(sm_count / kCl + 1) * kTile * kN; }
+
 size_t tc8_scratch_bytes(int sm_count) {
-    return (size_t)(sm_count / kCl + 1) * kTile * kN * sizeof(float);
+    return (size_t)kScratchSlots * tc8_slot_floats(sm_count) * sizeof(float);
 }
 
 static void fill_job8(const DecodeArgs& d, int tile_begin, Tc8Job* J) {
@@ -802,7 +804,8 @@ static cudaError_t launch_group8(const DecodeArgs* const* jobs, int n_jobs, bool
     Tc8Launch L{};
     L.beta = jobs[0]->beta;
     L.err = ctx->err_dev;
-    L.scratch = ctx->tc8_scratch;
+    L.scratch = ctx->tc8_scratch +
+                (ctx->tc8_next_slot.fetch_add(1) % kScratchSlots) * tc8_slot_floats(ctx->sm_count);
     int tiles = 0;
     for (int i = 0; i < n_jobs; ++i) {
         fill_job8(*jobs[i], tiles, &L.jobs[i]);

@@ -19,6 +19,7 @@ namespace csvc {
 constexpr int kMaxIters = 1 << 17;
 constexpr int kMaxN = 4096;
 constexpr int kTileCounters = 256;   // per-launch tile counters of the persistent decode
+constexpr int kScratchSlots = 16;    // per-launch scratch areas of the 32 x 32 cluster decode
 
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
@@ -42,7 +43,11 @@ struct cs_ctx {
     float* beta_dev = nullptr;          // FISTA momentum (t_k - 1)/t_{k+1}, k = 1..kMaxIters
     int* err_dev = nullptr;             // set to 1 by a kernel whose bounded wait gave up
     int* counters_dev = nullptr;        // csvc::kTileCounters tile counters, used round robin
-    float* tc8_scratch = nullptr;       // s^K all-gather of the 32 x 32 cluster decode
+    // s^K all-gather of the 32 x 32 cluster decode: a ring of kScratchSlots
+    // per-launch areas, so that launches in flight on different streams (serving)
+    // never share one
+    float* tc8_scratch = nullptr;
+    std::atomic<uint64_t> tc8_next_slot{0};
     std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
     std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
     // autotuned decode shape per (N, M): engine, plain-kernel threads and blocks per CTA

@@ -20,20 +20,23 @@ def B():
     return binding
 
 
-CAMERAS = [  # (h, w, gop, m, iters, precision, tail, seed)
-    (144, 176, 4, 26, 80, 0, 0, 11),
-    (288, 352, 6, 64, 60, 0, 0, 12),
-    (96, 128, 8, 13, 100, 3, 20, 13),
-    (144, 176, 5, 51, 40, 0, 0, 14),
+CAMERAS = [  # (h, w, gop, m, iters, precision, tail, seed, block)
+    (144, 176, 4, 26, 80, 0, 0, 11, 16),
+    (288, 352, 6, 64, 60, 0, 0, 12, 16),
+    (96, 128, 8, 13, 100, 3, 20, 13, 16),
+    (144, 176, 5, 51, 40, 0, 0, 14, 16),
+    (288, 352, 4, 102, 40, 0, 0, 15, 32),    # the 8-CTA cluster kernel
+    (160, 192, 3, 200, 30, 0, 0, 16, 32),    # the plain kernel (M > 128)
 ]
 
 
 def _camera(B, ctx, cam):
-    h, w, gop, m, iters, prec, tail, seed = cam
+    h, w, gop, m, iters, prec, tail, seed = cam[:8]
+    b = cam[8] if len(cam) > 8 else 16
     frames = scenes.surveillance_video(gop, h, w, seed=seed)
-    plan = B.cs_make_phi(ctx, 256, m, seed)
-    p = B.make_params(h, w, gop, 16, m, iters=iters, precision=prec, fp32_tail_iters=tail)
-    nblk = (-(-h // 16)) * (-(-w // 16))
+    plan = B.cs_make_phi(ctx, b * b, m, seed)
+    p = B.make_params(h, w, gop, b, m, iters=iters, precision=prec, fp32_tail_iters=tail)
+    nblk = (-(-h // b)) * (-(-w // b))
     y = torch.empty((gop - 1, nblk, m), dtype=torch.float32, device="cuda")
     B.cs_encode_gop(plan, p, torch.from_numpy(frames).cuda(), y, torch.cuda.current_stream())
     torch.cuda.synchronize()
@@ -64,7 +67,7 @@ def test_requests_in_the_mix_equal_each_request_alone(B):
     cams = [_camera(B, ctx, c) for c in CAMERAS]
     try:
         outs, tickets = [], []
-        for rep in range(3):                       # 12 requests in flight at once
+        for rep in range(3):                       # 18 requests in flight at once
             for plan, p, key, y_host, _ in cams:
                 out = torch.zeros(y_host.shape[0:1] + key.shape[1:], dtype=torch.uint8).pin_memory()
                 tickets.append(B.cs_submit(ctx, plan, p, key, y_host, out))
