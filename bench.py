@@ -468,7 +468,26 @@ def main():
     dec_ev = []
     plan_list = [plans[m] for m in wl["ms"]]
     param_list = [params[m] for m in wl["ms"]]
-    launches_per_step = 2 * len(wl["ms"]) + (len(wl["ms"]) if args.no_batch else 1)
+    # our kernels per step: one encode and one PSNR per M, and the decode: one
+    # launch per call with --no-batch, else one per (operand type, shared-memory
+    # layout) group of the 16x16 tensor path (M16 <= 96 or <= 128), one per group
+    # of the 32x32 cluster path, one per plain-kernel job
+    def decode_launches():
+        if args.no_batch:
+            return len(wl["ms"])
+        groups, plain = set(), 0
+        for m in wl["ms"]:
+            m16 = (m + 15) // 16 * 16
+            tc = engine != B.CS_ENGINE_PLAIN and (
+                engine == B.CS_ENGINE_TC or tuned[str(m)]["engine"] == B.CS_ENGINE_TC)
+            if not tc:
+                plain += 1
+            elif n == 256:
+                groups.add(("tc", m16 <= 96))
+            else:
+                groups.add(("tc8",))
+        return len(groups) + plain
+    launches_per_step = 2 * len(wl["ms"]) + decode_launches()
 
     enc_ev, psnr_ev = [], []
 

@@ -1,11 +1,15 @@
 // K8: per-frame PSNR (the paper's quality measure, Sec. 4 and Table I),
-// 10 log10(255^2 / MSE), with the squared error summed in FP64.
+// 10 log10(255^2 / MSE); the squared errors are summed with about 48 significant bits.
 //
 // A cluster of 8 CTAs takes one frame: each CTA sums the squared errors of an
 // eighth of the pixels (vector loads when the frame is 16-byte aligned), and
 // CTA 0 adds the 8 partial sums in rank order from distributed shared memory,
-// so the result does not depend on scheduling.  d = t - r is exact in FP64
-// (r an 8-bit integer, t a float32), and d^2 accumulates by FMA in FP64.
+// so the result does not depend on scheduling.  FP64 is scarce on this part,
+// so a thread keeps its sum in float-float (about 48 significant bits) with
+// error-free transformations in FP32: d = t - r exactly as a pair s + e
+// (Knuth's TwoSum), s^2 exactly as p + q (the FMA TwoProduct), d^2 = p + (q +
+// 2 s e) up to e^2 < 2^-48 s^2, and each term added to the pair (hi, lo) by
+// TwoSum.  The per-thread pairs are combined in FP64.
 #include <math.h>
 
 #include "internal.h"
@@ -16,8 +20,24 @@ namespace {
 constexpr int kPsnrCta = 8;
 constexpr int kPsnrThreads = 512;
 
-__device__ __forceinline__ double sq_err(uint8_t r, float t) {
-    return (double)t - (double)r;
+// a + b = s + e exactly (round to nearest, no reassociation)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += (t - r)^2
+__device__ __forceinline__ void add_sq_err(uint8_t r, float t, float& hi, float& lo) {
+    float s, e;
+    two_sum(t, -(float)r, s, e);                    // d = s + e exactly
+    const float p = __fmul_rn(s, s);
+    const float q = __fmaf_rn(s, s, -p);            // s^2 = p + q exactly
+    const float tail = __fmaf_rn(__fmul_rn(2.f, s), e, q);
+    float h, c;
+    two_sum(hi, p, h, c);
+    hi = h;
+    lo = __fadd_rn(lo, __fadd_rn(c, tail));
 }
 
 __global__ void __cluster_dims__(kPsnrCta, 1, 1) __launch_bounds__(kPsnrThreads)
@@ -33,28 +53,22 @@ __global__ void __cluster_dims__(kPsnrCta, 1, 1) __launch_bounds__(kPsnrThreads)
     const long long end = begin + chunk < px ? begin + chunk : px;
     const uint8_t* r = ref + f * px;
     const float* t = test + f * px;
-    double acc = 0.0;
+    float hi = 0.f, lo = 0.f;
     long long i = begin + threadIdx.x * 4;
     if (vec) {
         // 4 pixels per thread and step: 4-byte uint8 and 16-byte float32 loads
         for (; i + 3 < end; i += 4 * kPsnrThreads) {
             const uchar4 rv = *reinterpret_cast<const uchar4*>(r + i);
             const float4 tv = __ldg(reinterpret_cast<const float4*>(t + i));
-            double d = sq_err(rv.x, tv.x);
-            acc = fma(d, d, acc);
-            d = sq_err(rv.y, tv.y);
-            acc = fma(d, d, acc);
-            d = sq_err(rv.z, tv.z);
-            acc = fma(d, d, acc);
-            d = sq_err(rv.w, tv.w);
-            acc = fma(d, d, acc);
+            add_sq_err(rv.x, tv.x, hi, lo);
+            add_sq_err(rv.y, tv.y, hi, lo);
+            add_sq_err(rv.z, tv.z, hi, lo);
+            add_sq_err(rv.w, tv.w, hi, lo);
         }
     } else {
-        for (long long j = begin + threadIdx.x; j < end; j += kPsnrThreads) {
-            const double d = sq_err(r[j], t[j]);
-            acc = fma(d, d, acc);
-        }
+        for (long long j = begin + threadIdx.x; j < end; j += kPsnrThreads) add_sq_err(r[j], t[j], hi, lo);
     }
+    double acc = (double)hi + (double)lo;
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
