@@ -64,9 +64,13 @@ typedef struct cs_plan cs_plan;
 #define CS_FP16 3          /* FP16 A and iterate (scaled), FP32-grade tail iterations */
 
 /* decode kernel (cs_params.engine) */
-#define CS_ENGINE_AUTO 0   /* persistent tensor-core kernel when the shape allows it */
+#define CS_ENGINE_AUTO 0   /* CS_ENGINE_TC if the shape allows it, else CS_ENGINE_TC_STREAM, else plain */
 #define CS_ENGINE_PLAIN 1  /* one CTA per block, FP32 SIMT: the plain baseline */
-#define CS_ENGINE_TC 2     /* persistent tcgen05 kernel; CS_EINVAL if the shape is unsupported */
+#define CS_ENGINE_TC 2     /* persistent tcgen05 kernel with the iterates on chip: N = 256 or
+                            * 1024 with M <= 128; CS_EINVAL for any other shape */
+#define CS_ENGINE_TC_STREAM 3  /* persistent tcgen05 kernel with A streamed from L2 and the
+                                * iterates in global memory: N = 64, 256 or 1024 with
+                                * M <= 512; CS_EINVAL for any other shape */
 
 /* Codec parameters of one encode/decode call (Sec. 3.1: "GOP size and
  * measurement matrix size" are the encoder's configuration). */
@@ -151,10 +155,10 @@ int cs_decode_gop(cs_plan* plan, const cs_params* params, const uint8_t* key_dev
  * cs_decode_batch: decode n_jobs GOP calls (cs_decode_gop semantics, job i =
  * plans[i], params[i], key_dev[i], y_dev[i], frames_f32_dev[i] and
  * frames_u8_dev[i]; the two output arrays may be NULL, or hold NULL entries)
- * as one persistent tensor-core launch per operand type: plans of different M
- * and calls of different frame size, GOP size, iteration count and precision
- * share the SMs, each CTA taking the next 128-block tile.  All plans belong
- * to ctx.  Jobs the tensor-core kernel does not cover (or that ask for
+ * as one persistent tensor-core launch per kernel and operand type: plans of
+ * different N and M and calls of different frame size, GOP size, iteration
+ * count and precision share the SMs, each CTA taking the next 128-block tile.
+ * All plans belong to ctx.  Jobs no tensor-core kernel covers (or that ask for
  * CS_ENGINE_PLAIN) run on the plain kernel on the same stream.  Results are
  * identical to decoding each job alone.  Host arrays, device buffers. */
 int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs_params* params,
@@ -173,15 +177,18 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
  * of each multiplier; params->iters iterations from zero.  beta and mu are the
  * penalties of the splitting and of the measurement constraint (0.125 and 1
  * suit 8-bit residuals).  FP32, plain per-block kernel (params->precision must
- * be CS_FP32, params->engine not CS_ENGINE_TC; lambda_rel is not used).
+ * be CS_FP32, params->engine CS_ENGINE_AUTO or CS_ENGINE_PLAIN; lambda_rel is
+ * not used).
  * Buffers and errors as cs_decode_gop; CS_EINVAL for beta or mu <= 0. */
 int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float mu,
                      const uint8_t* key_dev, const float* y_dev, float* frames_f32_dev,
                      uint8_t* frames_u8_dev, cs_stream_t stream);
 
 /* cs_autotune: pick the decode's launch shape for the plan's (N, M) by timing
- * every candidate on the device: the tensor-core kernel where the shape has
- * one (16 x 16 and 32 x 32 blocks, M <= 128), and the plain FP32 kernel at 64,
+ * every candidate on the device: the on-chip tensor-core kernel where the
+ * shape has one (16 x 16 and 32 x 32 blocks, M <= 128), the streaming
+ * tensor-core kernel where it has one (8 x 8, 16 x 16 and 32 x 32 blocks,
+ * M <= 512), and the plain FP32 kernel at 64,
  * 128, 256, 512 and 1024 threads per CTA with 1, 2, 4, 8 or 16 (up to 512
  * threads) measured blocks per CTA (the blocks of a CTA share each load of A;
  * shapes whose shared memory exceeds 200 KB are skipped).  Each runs a synthetic call (random
@@ -190,9 +197,10 @@ int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float m
  * decodes whose engine is CS_ENGINE_AUTO (an explicit engine still wins;
  * mixed precision always takes the tensor-core kernel).  Synchronises the
  * device: call it before serving or before capturing decodes into a CUDA
- * graph.  Outputs (each may be NULL): the chosen engine (CS_ENGINE_TC or
- * CS_ENGINE_PLAIN), the plain kernel's threads and blocks per CTA (0 for the
- * tensor-core kernel) and the measured time per block per iteration in ns.
+ * graph.  Outputs (each may be NULL): the chosen engine (CS_ENGINE_TC,
+ * CS_ENGINE_TC_STREAM or CS_ENGINE_PLAIN), the plain kernel's threads and
+ * blocks per CTA (0 for the tensor-core kernels) and the measured time per
+ * block per iteration in ns.
  * The paper has no counterpart (its decoder is a MATLAB solver). */
 int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t* plain_threads,
                 int32_t* plain_blocks_per_cta, float* ns_per_block_iter);

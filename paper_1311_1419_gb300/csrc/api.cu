@@ -62,7 +62,7 @@ int check_decode_params(const cs_params* p) {
     if (!(p->lambda_rel >= 0.f) || !isfinite(p->lambda_rel))
         return fail(CS_EINVAL, "lambda_rel must be finite and >= 0");
     if (p->precision < CS_FP32 || p->precision > CS_FP16) return fail(CS_EINVAL, "bad precision");
-    if (p->engine < CS_ENGINE_AUTO || p->engine > CS_ENGINE_TC) return fail(CS_EINVAL, "bad engine");
+    if (p->engine < CS_ENGINE_AUTO || p->engine > CS_ENGINE_TC_STREAM) return fail(CS_EINVAL, "bad engine");
     return CS_OK;
 }
 
@@ -92,8 +92,11 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
     d->plain_blocks = 0;
     int eng = params->engine;
     const bool tc_ok = tc_supported(plan, params->precision);
+    const bool tcs_ok = tcs_supported(plan);
     if (eng == CS_ENGINE_TC && !tc_ok)
-        return fail(CS_EINVAL, "tensor-core decode does not support this (N, M, precision)");
+        return fail(CS_EINVAL, "on-chip tensor-core decode does not support this (N, M)");
+    if (eng == CS_ENGINE_TC_STREAM && !tcs_ok)
+        return fail(CS_EINVAL, "streaming tensor-core decode does not support this (N, M)");
     {   // the autotuned shape of this (N, M), if cs_autotune has run for it
         std::lock_guard<std::mutex> lock(plan->ctx->tune_mu);
         auto it = plan->ctx->tuned.find({plan->n, plan->m});
@@ -103,7 +106,7 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
             d->plain_blocks = it->second[2];
         }
     }
-    if (eng == CS_ENGINE_AUTO) eng = tc_ok ? CS_ENGINE_TC : CS_ENGINE_PLAIN;
+    if (eng == CS_ENGINE_AUTO) eng = tc_ok ? CS_ENGINE_TC : tcs_ok ? CS_ENGINE_TC_STREAM : CS_ENGINE_PLAIN;
     if (eng == CS_ENGINE_PLAIN && params->precision != CS_FP32)
         return fail(CS_EINVAL, "the plain engine computes in FP32 only");
     *engine = eng;
@@ -118,8 +121,9 @@ int decode_enqueue(cs_plan* plan, const cs_params* params, const uint8_t* key, c
     int engine = 0;
     int st = prepare_decode(plan, params, key, y, out_f32, out_u8, &d, &engine);
     if (st) return st;
-    cudaError_t e = engine == CS_ENGINE_TC ? launch_decode_tc(d, stream)
-                                           : launch_decode_plain(d, stream);
+    cudaError_t e = engine == CS_ENGINE_TC          ? launch_decode_tc(d, stream)
+                    : engine == CS_ENGINE_TC_STREAM ? launch_decode_tcs(d, stream)
+                                                    : launch_decode_plain(d, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     return CS_OK;
 }
@@ -195,6 +199,7 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     if (ctx->err_dev) cudaFree(ctx->err_dev);
     if (ctx->counters_dev) cudaFree(ctx->counters_dev);
     if (ctx->tc8_scratch) cudaFree(ctx->tc8_scratch);
+    if (ctx->tcs_scratch) cudaFree(ctx->tcs_scratch);
     delete ctx;
     return CS_OK;
 }
@@ -219,7 +224,8 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
     float ranges[3] = {0.f, 0.f, 0.f};
     cudaStream_t s = nullptr;
     double lam = 0.0;
-    const bool tc = tc_plan_supported(n, m);
+    const bool tc_chip = tc_plan_supported(n, m), tcs = tcs_plan_supported(n, m);
+    const bool tc = tc_chip || tcs;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     const size_t mn = (size_t)m * n;
     if (e == cudaSuccess) e = cudaMalloc(&p->phi, mn * sizeof(float));
@@ -242,19 +248,31 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
         p->tc_ea = (int)floor(log2(16384.0 / (double)ranges[0]));
         const double pbound = 4.0 * 255.0 * (double)ranges[1];
         p->tc_ep = pbound > 16384.0 ? (int)floor(log2(16384.0 / pbound)) : 0;
-        e = cudaMalloc(&p->a_tc, tc_operand_bytes(n, m));
-        if (e == cudaSuccess)
-            e = n == 1024 ? launch_tc8_images(p->a, p->a_tc, m, p->tc_ea, s)
-                          : launch_tc_images(p->a, p->a_tc, n, m, p->tc_ea, s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        if (e == cudaSuccess && n == 256 && ranges[2] > 0.f) {
+        if (tc_chip) {
+            e = cudaMalloc(&p->a_tc, tc_operand_bytes(n, m));
+            if (e == cudaSuccess)
+                e = n == 1024 ? launch_tc8_images(p->a, p->a_tc, m, p->tc_ea, s)
+                              : launch_tc_images(p->a, p->a_tc, n, m, p->tc_ea, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
+        if (e == cudaSuccess && tcs) {
+            e = cudaMalloc(&p->a_tcs, tcs_operand_bytes(n, m));
+            if (e == cudaSuccess) e = launch_tcs_images(p->a, p->a_tcs, n, m, p->tc_ea, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e == cudaSuccess) {
+                // the streaming decode's per-CTA iterates, one ring per context
+                std::lock_guard<std::mutex> lock(ctx->mu);
+                if (!ctx->tcs_scratch) e = cudaMalloc(&ctx->tcs_scratch, tcs_scratch_bytes(ctx->sm_count));
+            }
+        }
+        if (e == cudaSuccess && tc_chip && n == 256 && ranges[2] > 0.f) {
             // the tensor-core encode's Phi images, max |Phi| near 2^14
             p->tc_ephi = (int)floor(log2(16384.0 / (double)ranges[2]));
             e = cudaMalloc(&p->phi_tc, tc_operand_bytes(n, m));
             if (e == cudaSuccess) e = launch_tc_images(p->phi, p->phi_tc, n, m, p->tc_ephi, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
-        if (e == cudaSuccess && n == 1024) {
+        if (e == cudaSuccess && tc_chip && n == 1024) {
             // the cluster decode's s^K all-gather, one per context
             std::lock_guard<std::mutex> lock(ctx->mu);
             if (!ctx->tc8_scratch) e = cudaMalloc(&ctx->tc8_scratch, tc8_scratch_bytes(ctx->sm_count));
@@ -285,6 +303,7 @@ int cs_plan_destroy(cs_plan* p) {
     if (p->a) cudaFree(p->a);
     if (p->dct) cudaFree(p->dct);
     if (p->a_tc) cudaFree(p->a_tc);
+    if (p->a_tcs) cudaFree(p->a_tcs);
     if (p->phi_tc) cudaFree(p->phi_tc);
     delete p;
     return CS_OK;
@@ -314,7 +333,7 @@ int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_
     int st = make_shape(plan, params, &gs);
     if (st) return st;
     if (gs.n_cs > 0 && (!frames_dev || !y_dev)) return fail(CS_EINVAL, "null buffer");
-    if (params->engine < CS_ENGINE_AUTO || params->engine > CS_ENGINE_TC) return fail(CS_EINVAL, "bad engine");
+    if (params->engine < CS_ENGINE_AUTO || params->engine > CS_ENGINE_TC_STREAM) return fail(CS_EINVAL, "bad engine");
     // the tensor-core encode where the plan has one, unless the plain engine is asked for
     const bool tc = params->engine != CS_ENGINE_PLAIN && encode_tc_supported(plan);
     cudaError_t e = tc ? launch_encode_tc(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
@@ -335,7 +354,7 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
                     cs_stream_t stream) {
     if (!ctx || n_jobs < 0 || (n_jobs > 0 && (!plans || !params || !key_dev || !y_dev)))
         return fail(CS_EINVAL, "null argument");
-    std::vector<DecodeArgs> tc_jobs, plain_jobs;
+    std::vector<DecodeArgs> tc_jobs, tcs_jobs, plain_jobs;
     tc_jobs.reserve(n_jobs);
     for (int i = 0; i < n_jobs; ++i) {
         if (!plans[i] || plans[i]->ctx != ctx) return fail(CS_EINVAL, "plan of another context");
@@ -345,10 +364,12 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
                                 frames_f32_dev ? frames_f32_dev[i] : nullptr,
                                 frames_u8_dev ? frames_u8_dev[i] : nullptr, &d, &engine);
         if (st) return fail(st, std::string("job ") + std::to_string(i) + ": " + cs_last_error());
-        (engine == CS_ENGINE_TC ? tc_jobs : plain_jobs).push_back(d);
+        (engine == CS_ENGINE_TC ? tc_jobs : engine == CS_ENGINE_TC_STREAM ? tcs_jobs : plain_jobs).push_back(d);
     }
     cudaError_t e = cudaSuccess;
     if (!tc_jobs.empty()) e = launch_decode_tc_batch(tc_jobs.data(), (int)tc_jobs.size(), (cudaStream_t)stream);
+    if (e == cudaSuccess && !tcs_jobs.empty())
+        e = launch_decode_tcs_batch(tcs_jobs.data(), (int)tcs_jobs.size(), (cudaStream_t)stream);
     for (size_t i = 0; e == cudaSuccess && i < plain_jobs.size(); ++i)
         e = launch_decode_plain(plain_jobs[i], (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");

@@ -1,7 +1,8 @@
 // Autotuner of the decode's launch shape per (N, M).
 //
 // The recovery of a plan's blocks can run on the persistent tensor-core kernel
-// (where the shape has one) or on the plain kernel with 64 to 1024 threads
+// with the iterates on chip (where the shape has one), on the streaming
+// tensor-core kernel (where the shape has one) or on the plain kernel with 64 to 1024 threads
 // and 1, 2, 4, 8 or 16 measured blocks per CTA.  cs_autotune times every candidate the plan's shape
 // admits on a synthetic call of the same N and M (random measurements, a zero
 // key, a few thousand blocks, a short fixed iteration count) and records the
@@ -61,6 +62,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
 
     std::vector<Candidate> cands;
     if (tc_supported(plan, CS_FP32)) cands.push_back({CS_ENGINE_TC, 0, 0});
+    if (tcs_supported(plan)) cands.push_back({CS_ENGINE_TC_STREAM, 0, 0});
     for (int t : {64, 128, 256, 512, 1024})
         for (int r : {1, 2, 4, 8, 16})
             if (plain_shape_valid(t, r, n, m)) cands.push_back({CS_ENGINE_PLAIN, t, r});
@@ -101,7 +103,9 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
         d.plain_threads = cands[i].threads;
         d.plain_blocks = cands[i].blocks;
         auto launch = [&]() {
-            return cands[i].engine == CS_ENGINE_TC ? launch_decode_tc(d, s) : launch_decode_plain(d, s);
+            return cands[i].engine == CS_ENGINE_TC          ? launch_decode_tc(d, s)
+                   : cands[i].engine == CS_ENGINE_TC_STREAM ? launch_decode_tcs(d, s)
+                                                            : launch_decode_plain(d, s);
         };
         e = launch();   // warm-up (and first-launch attribute set-up)
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);

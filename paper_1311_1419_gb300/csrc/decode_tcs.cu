@@ -1,0 +1,763 @@
+// K6 for the (N, M) shapes whose iterates do not fit on one SM: tensor-core
+// FISTA with streamed operands and the iterates in global memory.
+//
+// The recovery is the same fixed-count FISTA on 1/2 ||A s - y||^2 +
+// lambda ||s||_1 (Eq. 1 with an l1 regulariser in the DCT basis; Beck &
+// Teboulle 2009) followed by r = Psi s and the key add-back of Eq. (4), for
+// 8 x 8, 16 x 16 and 32 x 32 blocks (N = 64, 256, 1024) with up to 512
+// measurements.  A tile of 128 blocks is one CTA's work (the MMA's M
+// dimension).  Per FISTA iteration of a tile, two GEMMs run on the tensor cores:
+//
+//   GEMM1  U [128 x M16] = Z [128 x N] . A^T   in one or two column chunks of <= 256
+//   GEMM2  G [128 x N]   = P [128 x M16] . A   in column chunks of min(N, 256)
+//
+// Neither A (up to 2 MB as fp16 hi + lo at N = 1024, M = 512) nor the tile's
+// iterates (Z and s^{k-1}: 1 MB) fit on chip, so the operands stream: a copy
+// warp feeds a two-stage ring of 64-wide K slices through the bulk-copy engine
+// (the tile operand Z or P from this CTA's global scratch, the A slice from the
+// plan's swizzled image, which stays in L2), one thread issues the MMAs, and
+// two 256-column accumulators in tensor memory let the epilogue of one chunk
+// run while the next chunk is computed.  The epilogue (16 warps, TMEM lane
+// quarter = warp % 4, column group = warp / 4) forms P = U - y into the
+// scratch's P image and runs the gradient / soft-threshold / momentum step,
+// reading and writing s^{k-1} (fp32) and Z (fp16 hi + lo, the next GEMM1's
+// operand image) in the scratch.  lambda_b needs max |A^T y_b| over all N
+// coefficients before the first step, so GEMM2 runs once more at k = 0 for it.
+// Mixed precision: a split product uses three MMAs (hi.hi + lo.hi + hi.lo),
+// a bulk one hi.hi only.  Every mbarrier wait is bounded and reports through
+// the context's error word; a CTA that gives up drains its copies and MMAs.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "internal.h"
+#include "tc_ptx.h"
+
+namespace csvc {
+namespace {
+
+using namespace tc;
+
+constexpr int kTile = 128;                 // blocks per tile = TMEM lanes = MMA M
+constexpr int kMaxNs = 1024, kMaxM16s = 512;
+constexpr int kEpiWarps = 16;
+constexpr int kEpiThreads = kEpiWarps * 32;
+constexpr int kThreads = 64 + kEpiThreads;  // warp 0 MMA, warp 1 copies, warps 2 .. 17 epilogue
+constexpr int kChunk = 256;                 // accumulator columns per chunk
+constexpr uint32_t kTBytes = kTile * 128;   // one 64-wide K slice of the tile operand (16 KB)
+constexpr uint32_t kBBytes = kChunk * 128;  // one K slice of up to 256 rows of A (32 KB)
+constexpr int kStages = 2;
+constexpr uint32_t kStageBytes = 2 * (kTBytes + kBBytes);   // hi and lo of both: 96 KB
+constexpr uint32_t kOffC = kStages * kStageBytes;           // DCT matrix, <= 32 x 32 floats
+constexpr uint32_t kOffMisc = kOffC + 4096;
+constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024;     // + alignment slack
+// per-CTA global scratch: Z image (hi, lo), P image (hi, lo), s^{k-1}
+constexpr size_t kScrZ = 0, kScrP = 512 * 1024, kScrS = 768 * 1024, kScrBytes = 1280 * 1024;
+constexpr uint64_t kWaitNs = 1000000000ull;                 // 1 s per wait
+constexpr uint32_t kBarEpi = 1;                             // named barrier of the epilogue
+
+struct MiscS {
+    uint64_t full[kStages], empty[kStages];
+    uint64_t acc_full[2], acc_empty[2];
+    uint64_t p_ready, z_ready, drain;
+    uint32_t tmem_base;
+    int abort;
+    int next_tile;
+    uint32_t colmax[kTile];
+};
+static_assert(sizeof(MiscS) <= 1024, "barrier block");
+
+}  // namespace
+
+// One job of a launch: the blocks of one cs_decode_gop call.
+struct TcsJob {
+    const uint8_t* a_img;   // A * 2^ea, hi image then lo image, m16 x n x 2 bytes each
+    const float* y;
+    const uint8_t* keys;
+    float* out_f32;
+    uint8_t* out_u8;
+    const float* dct;       // [B][B]
+    GopShape gs;
+    long long rows;         // measured blocks
+    int tile_begin;
+    int n, m16;
+    int iters;
+    int split_from;         // iterations k >= split_from use the 3-MMA split
+    int y_vec;              // rows of y start on 16-byte boundaries
+    float lambda_rel, inv_l;
+    float su, sg, sp;       // U = acc su, G = acc sg, P operand = P sp
+};
+
+constexpr int kMaxJobsS = 48;
+struct TcsLaunch {
+    const float* beta;
+    int* err;
+    int* tile_counter;
+    uint8_t* scratch;       // this launch's area: gridDim.x x kScrBytes
+    int n_jobs;
+    int n_tiles;
+    TcsJob jobs[kMaxJobsS];
+};
+
+namespace {
+
+template <bool BF>
+__device__ __forceinline__ uint32_t pack2s(float2 v) {
+    if constexpr (BF) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
+        return *reinterpret_cast<uint32_t*>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(v.x, v.y);
+        return *reinterpret_cast<uint32_t*>(&h);
+    }
+}
+template <bool BF>
+__device__ __forceinline__ float2 unpack2s(uint32_t v) {
+    if constexpr (BF) {
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+        return __bfloat1622float2(h);
+    } else {
+        __half2 h = *reinterpret_cast<__half2*>(&v);
+        return __half22float2(h);
+    }
+}
+
+__device__ __forceinline__ bool wait_s(MiscS* ms, uint64_t* bar, uint32_t parity, int* err) {
+    if (*(volatile int*)&ms->abort) return false;
+    if (mbar_wait(bar, parity, kWaitNs)) return true;
+    *(volatile int*)&ms->abort = 1;
+    atomicExch(err, 1);
+    return false;
+}
+
+__device__ __forceinline__ int job_of_s(const TcsLaunch& L, int tile) {
+    int j = 0;
+    while (j + 1 < L.n_jobs && L.jobs[j + 1].tile_begin <= tile) ++j;
+    return j;
+}
+
+__device__ __forceinline__ int fetch_tile_s(const TcsLaunch& L, MiscS* ms) {
+    if (threadIdx.x == 0) ms->next_tile = atomicAdd(L.tile_counter, 1);
+    __syncthreads();
+    return ms->next_tile;
+}
+__device__ __forceinline__ void cta_sync_s() {
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+}
+
+// Chunk geometry.  GEMM1: U in one chunk of m16 columns, or two of about m16 / 2
+// (multiples of 16).  GEMM2: G in n / nc chunks of nc = min(n, 256) columns.
+__device__ __forceinline__ int g1_chunks(int m16) { return m16 > kChunk ? 2 : 1; }
+__device__ __forceinline__ int g1_width(int m16, int c) {
+    if (m16 <= kChunk) return m16;
+    const int w0 = (m16 / 2 + 15) / 16 * 16;
+    return c == 0 ? w0 : m16 - w0;
+}
+__device__ __forceinline__ int g1_base(int m16, int c) { return c == 0 ? 0 : g1_width(m16, 0); }
+__device__ __forceinline__ int g2_width(int n) { return n < kChunk ? n : kChunk; }
+__device__ __forceinline__ int p_atoms(int m16) { return (m16 + 63) / 64; }
+
+// Passes of a tile with K iterations: 0 = GEMM2 for lambda, 1 = GEMM2 of k = 0,
+// then GEMM1 (even) and GEMM2 (odd) of k = pass / 2.
+__device__ __forceinline__ bool pass_is_g2(int pass) { return pass < 2 || (pass & 1); }
+__device__ __forceinline__ int pass_iter(int pass) { return pass < 2 ? 0 : pass / 2; }
+
+// Index (in float4) of s^{k-1} values 4 v .. 4 v + 3 of the column group cg of
+// GEMM2 chunk jc for tile row r: each epilogue warp reads 512 contiguous bytes.
+__device__ __forceinline__ size_t s_index4(int jc, int cg, int v, int r, int nc) {
+    return ((size_t)(jc * 4 + cg) * (nc / 16) + v) * kTile + r;
+}
+
+// ---------------------------------------------------------------------------
+// Warp 1: streams the operands of every pass into the stage ring.
+template <bool BF>
+__device__ __forceinline__ void copy_role(const TcsLaunch& L, MiscS* ms, uint8_t* sm, int lane) {
+    uint8_t* scr = L.scratch + (size_t)blockIdx.x * kScrBytes;
+    uint32_t st = 0, pc = 0, zc = 0;
+    uint32_t last_par[kStages] = {0u, 0u};
+    bool issued[kStages] = {false, false};
+    bool ok = true;
+    for (;;) {
+        const int tile = fetch_tile_s(L, ms);
+        if (tile >= L.n_tiles) break;
+        const TcsJob& J = L.jobs[job_of_s(L, tile)];
+        cta_sync_s();   // B
+        const int n = J.n, m16 = J.m16;
+        const size_t img = (size_t)m16 * n * 2;
+        const uint8_t* z_hi = scr + kScrZ;
+        const uint8_t* z_lo = z_hi + (size_t)n * 256;
+        const uint8_t* p_hi = scr + kScrP;
+        const uint8_t* p_lo = p_hi + (size_t)p_atoms(m16) * kTBytes;
+        for (int pass = 0; pass < 2 * J.iters; ++pass) {
+            const bool g2 = pass_is_g2(pass);
+            const int k = pass_iter(pass);
+            const bool split = k >= J.split_from;
+            if (pass != 1) {   // P (GEMM2) or Z (GEMM1) written by the epilogue
+                if (g2) {
+                    ok = wait_s(ms, &ms->p_ready, pc & 1, L.err) && ok;
+                    ++pc;
+                } else {
+                    ok = wait_s(ms, &ms->z_ready, zc & 1, L.err) && ok;
+                    ++zc;
+                }
+            }
+            const int nch = g2 ? n / g2_width(n) : g1_chunks(m16);
+            const int nst = g2 ? p_atoms(m16) : n / 64;
+            for (int c = 0; c < nch; ++c) {
+                for (int ks = 0; ks < nst; ++ks) {
+                    const uint32_t s = st % kStages, par = (st / kStages) & 1;
+                    ok = wait_s(ms, &ms->empty[s], par ^ 1, L.err) && ok;
+                    if (ok && lane == 0) {
+                        uint8_t* stg = sm + s * kStageBytes;
+                        const int reps = split ? 2 : 1;
+                        uint32_t bbytes;
+                        if (g2) {
+                            const int nc = g2_width(n);
+                            const int ng = min(8, m16 / 8 - 8 * ks);
+                            bbytes = (uint32_t)(nc / 64) * (uint32_t)ng * 1024u;
+                        } else {
+                            bbytes = (uint32_t)g1_width(m16, c) * 128u;
+                        }
+                        mbar_arrive_expect_tx(&ms->full[s], (uint32_t)reps * (kTBytes + bbytes));
+                        for (int h = 0; h < reps; ++h) {
+                            const uint8_t* aimg = J.a_img + (h ? img : 0);
+                            uint8_t* t_dst = stg + h * kTBytes;
+                            uint8_t* b_dst = stg + 2 * kTBytes + h * kBBytes;
+                            if (g2) {
+                                bulk_g2s(t_dst, (h ? p_lo : p_hi) + (size_t)ks * kTBytes, kTBytes, &ms->full[s]);
+                                const int nc = g2_width(n);
+                                const int ng = min(8, m16 / 8 - 8 * ks);
+                                for (int t = 0; t < nc / 64; ++t) {
+                                    const int a = c * (nc / 64) + t;   // j atom
+                                    bulk_g2s(b_dst + t * 8192,
+                                             aimg + ((size_t)a * (m16 / 8) + 8 * ks) * 1024,
+                                             (uint32_t)ng * 1024u, &ms->full[s]);
+                                }
+                            } else {
+                                bulk_g2s(t_dst, (h ? z_lo : z_hi) + (size_t)ks * kTBytes, kTBytes, &ms->full[s]);
+                                const int i0 = g1_base(m16, c);
+                                bulk_g2s(b_dst, aimg + ((size_t)ks * (m16 / 8) + i0 / 8) * 1024,
+                                         (uint32_t)g1_width(m16, c) * 128u, &ms->full[s]);
+                            }
+                        }
+                        last_par[s] = par;
+                        issued[s] = true;
+                    }
+                    __syncwarp();
+                    ++st;
+                }
+            }
+        }
+        cta_sync_s();   // C
+    }
+    if (lane == 0) {
+        // copies whose consumer gave up may still be in flight (bounded)
+        for (int s = 0; s < kStages; ++s)
+            if (issued[s]) mbar_wait(&ms->full[s], last_par[s], kWaitNs);
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Warp 0: issues every MMA (lane 0), chunk by chunk into the two accumulators.
+template <bool BF>
+__device__ __forceinline__ void mma_role_s(const TcsLaunch& L, MiscS* ms, uint8_t* sm, uint32_t tbase,
+                                           int lane) {
+    const uint32_t s_base = smem_u32(sm);
+    uint32_t st = 0, acc = 0;
+    bool ok = true;
+    for (;;) {
+        const int tile = fetch_tile_s(L, ms);
+        if (tile >= L.n_tiles) break;
+        const TcsJob& J = L.jobs[job_of_s(L, tile)];
+        cta_sync_s();   // B
+        const int n = J.n, m16 = J.m16;
+        for (int pass = 0; pass < 2 * J.iters; ++pass) {
+            const bool g2 = pass_is_g2(pass);
+            const bool split = pass_iter(pass) >= J.split_from;
+            const int nch = g2 ? n / g2_width(n) : g1_chunks(m16);
+            const int nst = g2 ? p_atoms(m16) : n / 64;
+            for (int c = 0; c < nch; ++c) {
+                const uint32_t b = acc & 1, apar = (acc >> 1) & 1;
+                ok = wait_s(ms, &ms->acc_empty[b], apar ^ 1, L.err) && ok;
+                fence_after_sync();
+                const uint32_t d = tbase + b * kChunk;
+                const int width = g2 ? g2_width(n) : g1_width(m16, c);
+                const uint32_t id = idesc_f16(128, (uint32_t)width, BF ? 1u : 0u, 0u, g2 ? 1u : 0u);
+#pragma unroll 1
+                for (int ks = 0; ks < nst; ++ks) {
+                    const uint32_t s = st % kStages, par = (st / kStages) & 1;
+                    ok = wait_s(ms, &ms->full[s], par, L.err) && ok;
+                    fence_after_sync();
+                    if (ok && lane == 0) {
+                        const uint32_t stg = s_base + s * kStageBytes;
+                        const uint64_t t_hi = desc_sw128(stg, 16, 1024);
+                        const uint64_t t_lo = desc_sw128(stg + kTBytes, 16, 1024);
+                        const uint64_t b_hi = g2 ? desc_sw128(stg + 2 * kTBytes, 8192, 1024)
+                                                 : desc_sw128(stg + 2 * kTBytes, 16, 1024);
+                        const uint64_t b_lo = g2 ? desc_sw128(stg + 2 * kTBytes + kBBytes, 8192, 1024)
+                                                 : desc_sw128(stg + 2 * kTBytes + kBBytes, 16, 1024);
+                        // K steps of 16 in this slice: 32 bytes along a K-major row; two
+                        // 8-row K groups (2 KB) in GEMM2's MN-major A slice
+                        const int nk = g2 ? min(4, m16 / 16 - 4 * ks) : 4;
+                        for (int kk = 0; kk < nk; ++kk) {
+                            const uint32_t to = (uint32_t)kk * 2u;
+                            const uint32_t bo = g2 ? (uint32_t)kk * 128u : (uint32_t)kk * 2u;
+                            const uint32_t accum = (ks > 0 || kk > 0) ? 1u : 0u;
+                            mma_f16(d, t_hi + to, b_hi + bo, id, accum);
+                            if (split) {
+                                mma_f16(d, t_lo + to, b_hi + bo, id, 1u);
+                                mma_f16(d, t_hi + to, b_lo + bo, id, 1u);
+                            }
+                        }
+                        mma_commit(&ms->empty[s]);
+                    }
+                    __syncwarp();
+                    ++st;
+                }
+                if (ok && lane == 0) mma_commit(&ms->acc_full[b]);
+                __syncwarp();
+                ++acc;
+            }
+        }
+        cta_sync_s();   // C
+    }
+    if (lane == 0) {
+        // every MMA issued so far has completed before tensor memory is freed
+        mma_commit(&ms->drain);
+        mbar_wait(&ms->drain, 0, kWaitNs);
+    }
+    __syncwarp();
+}
+
+// ---------------------------------------------------------------------------
+// Epilogue pieces.  Thread: TMEM lane / tile row r = 32 q + lane, column
+// group cg of the chunk.
+
+// P = (U su - y) sp for the thread's columns of GEMM1 chunk c (U = 0 at k = 0),
+// written as fp16/bf16 hi (and lo) into the scratch's P image.
+template <bool BF>
+__device__ __forceinline__ void epi_residual(const TcsJob& J, uint8_t* p_hi, uint8_t* p_lo, uint32_t lane_addr,
+                                             uint32_t col, int c, int cg, int r, const float* yrow,
+                                             bool use_u, bool split) {
+    const int m16 = J.m16, m = J.gs.m;
+    const int w4 = g1_width(m16, c) / 4;
+    const int i0 = g1_base(m16, c) + cg * w4;
+    for (int c0 = 0; c0 < w4; c0 += 16) {
+        uint32_t u[4][4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) u[t][e] = 0u;
+            if (use_u && c0 + 4 * t < w4) tmem_ld4(lane_addr + col + (uint32_t)(cg * w4 + c0 + 4 * t), u[t]);
+        }
+        if (use_u) tmem_wait_ld();
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            if (c0 + 4 * t >= w4) break;
+            const int i = i0 + c0 + 4 * t;
+            float yv[4] = {0.f, 0.f, 0.f, 0.f};
+            if (yrow) {
+                if (J.y_vec && i + 3 < m) {
+                    const float4 v4 = __ldg(reinterpret_cast<const float4*>(yrow + i));
+                    yv[0] = v4.x; yv[1] = v4.y; yv[2] = v4.z; yv[3] = v4.w;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+                        if (i + e < m) yv[e] = __ldg(yrow + i + e);
+                }
+            }
+            float p[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) p[e] = (__uint_as_float(u[t][e]) * J.su - yv[e]) * J.sp;
+            const uint32_t h0 = pack2s<BF>(make_float2(p[0], p[1])), h1 = pack2s<BF>(make_float2(p[2], p[3]));
+            const uint32_t off = sw128_offset((uint32_t)r, (uint32_t)i, kTile / 8);
+            *reinterpret_cast<uint2*>(p_hi + off) = make_uint2(h0, h1);
+            if (split) {
+                const float2 d0 = unpack2s<BF>(h0), d1 = unpack2s<BF>(h1);
+                const uint32_t l0 = pack2s<BF>(make_float2(p[0] - d0.x, p[1] - d0.y));
+                const uint32_t l1 = pack2s<BF>(make_float2(p[2] - d1.x, p[3] - d1.y));
+                *reinterpret_cast<uint2*>(p_lo + off) = make_uint2(l0, l1);
+            }
+        }
+    }
+}
+
+// lambda pass: max |G| over the thread's columns of GEMM2 chunk jc.
+__device__ __forceinline__ float epi_gmax(uint32_t lane_addr, uint32_t col, int w, int cg, float mx) {
+    for (int c0 = 0; c0 < w; c0 += 16) {
+        uint32_t g0[8], g1[8];
+        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0), g0);
+        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0 + 8), g1);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            mx = fmaxf(mx, fabsf(__uint_as_float(g0[e])));
+            mx = fmaxf(mx, fabsf(__uint_as_float(g1[e])));
+        }
+    }
+    return mx;
+}
+
+// Gradient step, soft threshold and momentum for the thread's columns of GEMM2
+// chunk jc: s^k = soft(z^k - g / L, tau), z^{k+1} = s^k + beta_k (s^k - s^{k-1}).
+template <bool BF>
+__device__ __forceinline__ void epi_update(const TcsJob& J, uint8_t* scr, uint32_t lane_addr, uint32_t col,
+                                           int jc, int cg, int r, int k, float tau, float bk, bool want_z) {
+    const int n = J.n, nc = g2_width(n), w = nc / 4;
+    uint8_t* z_hi = scr + kScrZ;
+    uint8_t* z_lo = z_hi + (size_t)n * 256;
+    float4* s4 = reinterpret_cast<float4*>(scr + kScrS);
+    const float2 ginv2 = make_float2(-J.sg * J.inv_l, -J.sg * J.inv_l);
+    const float2 b2 = make_float2(bk, bk);
+    for (int c0 = 0; c0 < w; c0 += 16) {
+        uint32_t g[2][8];
+        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0), g[0]);
+        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0 + 8), g[1]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int j = jc * nc + cg * w + c0 + 8 * h;               // first coefficient
+            const uint32_t zoff = sw128_offset((uint32_t)r, (uint32_t)j, kTile / 8);
+            const size_t si = s_index4(jc, cg, (c0 + 8 * h) / 4, r, nc);
+            uint4 zh = make_uint4(0u, 0u, 0u, 0u), zl = zh;
+            float4 sp0 = make_float4(0.f, 0.f, 0.f, 0.f), sp1 = sp0;
+            if (k > 0) {
+                zh = *reinterpret_cast<const uint4*>(z_hi + zoff);
+                zl = *reinterpret_cast<const uint4*>(z_lo + zoff);
+                sp0 = s4[si];
+                sp1 = s4[si + kTile];
+            }
+            const uint32_t zhw[4] = {zh.x, zh.y, zh.z, zh.w}, zlw[4] = {zl.x, zl.y, zl.z, zl.w};
+            const float spv[8] = {sp0.x, sp0.y, sp0.z, sp0.w, sp1.x, sp1.y, sp1.z, sp1.w};
+            float sv[8];
+            uint32_t nh[4], nl[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 zhf = unpack2s<BF>(zhw[e]), zlf = unpack2s<BF>(zlw[e]);
+                const float2 z2 = make_float2(zhf.x + zlf.x, zhf.y + zlf.y);
+                const float2 v = fma2(make_float2(__uint_as_float(g[h][2 * e]), __uint_as_float(g[h][2 * e + 1])),
+                                      ginv2, z2);
+                const float2 cl = make_float2(fminf(fmaxf(v.x, -tau), tau), fminf(fmaxf(v.y, -tau), tau));
+                const float2 s2 = sub2(v, cl);
+                const float2 zn = fma2(b2, sub2(s2, make_float2(spv[2 * e], spv[2 * e + 1])), s2);
+                sv[2 * e] = s2.x;
+                sv[2 * e + 1] = s2.y;
+                nh[e] = pack2s<BF>(zn);
+                nl[e] = pack2s<BF>(sub2(zn, unpack2s<BF>(nh[e])));
+            }
+            s4[si] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+            s4[si + kTile] = make_float4(sv[4], sv[5], sv[6], sv[7]);
+            if (want_z) {
+                *reinterpret_cast<uint4*>(z_hi + zoff) = make_uint4(nh[0], nh[1], nh[2], nh[3]);
+                *reinterpret_cast<uint4*>(z_lo + zoff) = make_uint4(nl[0], nl[1], nl[2], nl[3]);
+            }
+        }
+    }
+}
+
+// Wait for accumulator chunk `acc`, then (after the caller has read it) give
+// it back to the MMA warp.
+__device__ __forceinline__ void acc_wait(const TcsLaunch& L, MiscS* ms, uint32_t acc) {
+    wait_s(ms, &ms->acc_full[acc & 1], (acc >> 1) & 1, L.err);
+    fence_after_sync();
+}
+__device__ __forceinline__ void acc_release(MiscS* ms, uint32_t acc, int lane) {
+    fence_before_sync();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&ms->acc_empty[acc & 1]);
+}
+// The epilogue's global writes of an operand image are complete: let the copy warp read it.
+__device__ __forceinline__ void signal_copy(uint64_t* bar, int lane) {
+    fence_proxy_async_global();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(bar);
+}
+
+// Warps 2 .. 17.
+template <bool BF>
+__device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_t* sm, uint32_t tbase, int warp,
+                                           int lane) {
+    const int ew = warp - 2, q = warp & 3, cg = ew >> 2;
+    const int r = 32 * q + lane;                      // TMEM lane = tile row
+    const int et = threadIdx.x - 64;                  // 0 .. 511
+    const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
+    uint8_t* scr = L.scratch + (size_t)blockIdx.x * kScrBytes;
+    float* c_s = reinterpret_cast<float*>(sm + kOffC);
+    uint32_t acc = 0;
+    for (;;) {
+        const int tile = fetch_tile_s(L, ms);
+        if (tile >= L.n_tiles) break;
+        const TcsJob& J = L.jobs[job_of_s(L, tile)];
+        const GopShape& gs = J.gs;
+        const int n = J.n, m16 = J.m16, K = J.iters;
+        const int bsz = gs.b;
+        if (cg == 0) ms->colmax[r] = 0u;
+        for (int i = et; i < bsz * bsz; i += kEpiThreads) c_s[i] = J.dct[i];
+        cta_sync_s();   // B
+        const long long tile_row0 = (long long)(tile - J.tile_begin) * kTile;
+        const long long row = tile_row0 + r;
+        const float* yrow = row < J.rows ? J.y + row * gs.m : nullptr;
+        uint8_t* p_hi = scr + kScrP;
+        uint8_t* p_lo = p_hi + (size_t)p_atoms(m16) * kTBytes;
+        const int nch2 = n / g2_width(n), w2 = g2_width(n) / 4;
+        if (K > 0) {
+            const bool split0 = 0 >= J.split_from;
+            // P = -y for GEMM2 of k = 0 (z = 0, so U = 0)
+            for (int c = 0; c < g1_chunks(m16); ++c)
+                epi_residual<BF>(J, p_hi, p_lo, lane_addr, 0u, c, cg, r, yrow, false, split0);
+            signal_copy(&ms->p_ready, lane);
+            // lambda_b = lambda_rel ||A^T y_b||_inf from G = -A^T y
+            float mx = 0.f;
+            for (int jc = 0; jc < nch2; ++jc, ++acc) {
+                acc_wait(L, ms, acc);
+                mx = epi_gmax(lane_addr, (acc & 1) * kChunk, w2, cg, mx);
+                acc_release(ms, acc, lane);
+            }
+            atomicMax(&ms->colmax[r], __float_as_uint(mx * J.sg));
+            named_sync(kBarEpi, kEpiThreads);
+            const float tau = J.lambda_rel * __uint_as_float(ms->colmax[r]) * J.inv_l;
+            for (int k = 0; k < K; ++k) {
+                const bool want_z = k + 1 < K;
+                if (k > 0) {
+                    const bool split = k >= J.split_from;
+                    for (int c = 0; c < g1_chunks(m16); ++c, ++acc) {
+                        acc_wait(L, ms, acc);
+                        epi_residual<BF>(J, p_hi, p_lo, lane_addr, (acc & 1) * kChunk, c, cg, r, yrow, true,
+                                         split);
+                        acc_release(ms, acc, lane);
+                    }
+                    signal_copy(&ms->p_ready, lane);
+                }
+                const float bk = L.beta[k];
+                for (int jc = 0; jc < nch2; ++jc, ++acc) {
+                    acc_wait(L, ms, acc);
+                    epi_update<BF>(J, scr, lane_addr, (acc & 1) * kChunk, jc, cg, r, k, tau, bk, want_z);
+                    acc_release(ms, acc, lane);
+                }
+                if (want_z) signal_copy(&ms->z_ready, lane);
+            }
+        }
+        // --- reconstruct: R = C^T S C per block, S = s^K; 1024 / n blocks at a time ---
+        __threadfence_block();
+        named_sync(kBarEpi, kEpiThreads);
+        float* s_s = reinterpret_cast<float*>(sm);   // stage 0 is idle now
+        float* t_s = s_s + 1024;
+        const float4* s4 = reinterpret_cast<const float4*>(scr + kScrS);
+        const int nc = g2_width(n), w = nc / 4, gb = 1024 / n;
+        const size_t frame_px = (size_t)gs.h * gs.w;
+        for (int b0 = 0; b0 < kTile; b0 += gb) {
+            for (int e = et; e < gb * n; e += kEpiThreads) {
+                const int bl = e / n, j = e % n;
+                float v = 0.f;
+                if (K > 0) {
+                    const int jc = j / nc, rem = j % nc, cgj = rem / w, cc = rem % w;
+                    const float* f = reinterpret_cast<const float*>(s4 + s_index4(jc, cgj, cc / 4, b0 + bl, nc));
+                    v = f[cc % 4];
+                }
+                s_s[e] = v;
+            }
+            named_sync(kBarEpi, kEpiThreads);
+            for (int e = et; e < gb * n; e += kEpiThreads) {
+                const int bl = e / n, idx = e % n, kk = idx / bsz, qq = idx % bsz;
+                const float* srow = s_s + bl * n + kk * bsz;
+                float a = 0.f;
+                for (int l = 0; l < bsz; ++l) a = fmaf(srow[l], c_s[l * bsz + qq], a);
+                t_s[e] = a;
+            }
+            named_sync(kBarEpi, kEpiThreads);
+            for (int e = et; e < gb * n; e += kEpiThreads) {
+                const int bl = e / n, idx = e % n, p = idx / bsz, qq = idx % bsz;
+                const long long grow = tile_row0 + b0 + bl;
+                if (grow >= J.rows) continue;
+                const int c_idx = (int)(grow / gs.nblk), blk = (int)(grow % gs.nblk);
+                const int g_key = c_idx / (gs.g - 1);
+                const int py = (blk / gs.nbc) * bsz + p, px = (blk % gs.nbc) * bsz + qq;
+                if (py >= gs.h || px >= gs.w) continue;
+                float a = 0.f;
+                for (int kk = 0; kk < bsz; ++kk) a = fmaf(c_s[kk * bsz + p], t_s[bl * n + kk * bsz + qq], a);
+                const size_t off = (size_t)py * gs.w + px;
+                const float v = (float)J.keys[(size_t)g_key * frame_px + off] + a;
+                if (J.out_f32) J.out_f32[(size_t)c_idx * frame_px + off] = v;
+                if (J.out_u8) J.out_u8[(size_t)c_idx * frame_px + off] = (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
+            }
+            named_sync(kBarEpi, kEpiThreads);
+        }
+        cta_sync_s();   // C
+    }
+}
+
+template <bool BF>
+__global__ void __launch_bounds__(kThreads, 1) k_fista_tcs(const __grid_constant__ TcsLaunch L) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+    MiscS* ms = reinterpret_cast<MiscS*>(sm + kOffMisc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int s = 0; s < kStages; ++s) {
+                mbar_init(&ms->full[s], 1);
+                mbar_init(&ms->empty[s], 1);
+            }
+            for (int b = 0; b < 2; ++b) {
+                mbar_init(&ms->acc_full[b], 1);
+                mbar_init(&ms->acc_empty[b], kEpiWarps);
+            }
+            mbar_init(&ms->p_ready, kEpiWarps);
+            mbar_init(&ms->z_ready, kEpiWarps);
+            mbar_init(&ms->drain, 1);
+            ms->abort = 0;
+            fence_mbar_init();
+        }
+        __syncwarp();
+        tmem_alloc(&ms->tmem_base, 2 * kChunk);
+        tmem_relinquish();
+    }
+    cta_sync_s();
+    const uint32_t tbase = ms->tmem_base;
+    if (warp == 0)
+        mma_role_s<BF>(L, ms, sm, tbase, lane);
+    else if (warp == 1)
+        copy_role<BF>(L, ms, sm, lane);
+    else
+        epi_role_s<BF>(L, ms, sm, tbase, warp, lane);
+    cta_sync_s();
+    if (warp == 0) tmem_dealloc(tbase, 2 * kChunk);
+}
+
+int m16_of_s(int m) { return (m + 15) / 16 * 16; }
+
+// The fp16 hi / lo and bf16 hi / lo images of A * 2^ea for this kernel: m16
+// rows x n, rows >= M zero, 128-byte-swizzled atoms of 8 rows x 64 columns,
+// atom (col / 64, row / 8) at ((col / 64) * m16 / 8 + row / 8) * 1024.
+__global__ void k_tcs_images(const float* __restrict__ a, uint8_t* __restrict__ img, int n, int m, int m16,
+                             float scale) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m16 * n) return;
+    const int row = idx / n, col = idx % n;
+    const float v = row < m ? a[(size_t)row * n + col] * scale : 0.f;
+    const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)col, (uint32_t)m16 / 8);
+    const size_t img_bytes = (size_t)m16 * n * 2;
+    const __half hh = __float2half_rn(v);
+    const __half hl = __float2half_rn(v - __half2float(hh));
+    const __nv_bfloat16 bh = __float2bfloat16_rn(v);
+    const __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(bh));
+    *reinterpret_cast<__half*>(img + off) = hh;
+    *reinterpret_cast<__half*>(img + img_bytes + off) = hl;
+    *reinterpret_cast<__nv_bfloat16*>(img + 2 * img_bytes + off) = bh;
+    *reinterpret_cast<__nv_bfloat16*>(img + 3 * img_bytes + off) = bl;
+}
+
+}  // namespace
+
+bool tcs_plan_supported(int n, int m) {
+    return (n == 64 || n == 256 || n == kMaxNs) && m >= 1 && m16_of_s(m) <= kMaxM16s;
+}
+size_t tcs_operand_bytes(int n, int m) { return 4ull * (size_t)m16_of_s(m) * (size_t)n * 2; }
+size_t tcs_scratch_bytes(int sm_count) { return (size_t)kScratchSlots * (size_t)sm_count * kScrBytes; }
+
+cudaError_t launch_tcs_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s) {
+    const int m16 = m16_of_s(m);
+    const int total = m16 * n;
+    k_tcs_images<<<(total + 255) / 256, 256, 0, s>>>(a, img, n, m, m16, ldexpf(1.f, ea));
+    return cudaGetLastError();
+}
+
+bool tcs_supported(const cs_plan* plan) {
+    return plan->a_tcs != nullptr && plan->ctx->tcs_scratch != nullptr && tcs_plan_supported(plan->n, plan->m);
+}
+
+static void fill_job_s(const DecodeArgs& d, int tile_begin, TcsJob* J) {
+    const cs_plan* p = d.plan;
+    const bool bf = d.precision == CS_BF16 || d.precision == CS_BF16X2;
+    const int m16 = m16_of_s(p->m);
+    const size_t img = (size_t)m16 * p->n * 2;
+    J->a_img = p->a_tcs + (bf ? 2 * img : 0);
+    J->y = d.y;
+    J->keys = d.key;
+    J->out_f32 = d.out_f32;
+    J->out_u8 = d.out_u8;
+    J->dct = p->dct;
+    J->gs = d.gs;
+    J->rows = (long long)d.gs.n_cs * d.gs.nblk;
+    J->tile_begin = tile_begin;
+    J->n = p->n;
+    J->m16 = m16;
+    J->iters = d.iters;
+    const bool mixed = d.precision == CS_BF16 || d.precision == CS_FP16;
+    J->split_from = mixed ? (d.iters > d.tail_iters ? d.iters - d.tail_iters : 0) : 0;
+    J->y_vec = p->m % 4 == 0 && (reinterpret_cast<uintptr_t>(d.y) & 15) == 0;
+    J->lambda_rel = d.lambda_rel;
+    J->inv_l = (float)(1.0 / p->lipschitz);
+    J->su = ldexpf(1.f, -p->tc_ea);
+    J->sg = ldexpf(1.f, -(p->tc_ea + p->tc_ep));
+    J->sp = ldexpf(1.f, p->tc_ep);
+}
+
+static double job_cost_s(const DecodeArgs& d) {
+    const double m16 = (double)m16_of_s(d.plan->m), n = (double)d.plan->n;
+    const double blocks = (double)((long long)d.gs.n_cs * d.gs.nblk);
+    return blocks * (double)d.iters * (m16 > kChunk ? 2.0 * kChunk : m16) * n;
+}
+
+// One launch for up to kMaxJobsS jobs of one operand type (fp16 or bf16), any
+// (N, M) this kernel supports; jobs heaviest first.
+static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, bool bf, cudaStream_t s) {
+    cs_ctx* ctx = jobs[0]->plan->ctx;
+    if (!ctx->tcs_scratch) return cudaErrorInvalidValue;
+    TcsLaunch L{};
+    L.beta = jobs[0]->beta;
+    L.err = ctx->err_dev;
+    L.tile_counter = ctx->counters_dev + (ctx->next_counter.fetch_add(1) % kTileCounters);
+    L.scratch = ctx->tcs_scratch +
+                (ctx->tcs_next_slot.fetch_add(1) % kScratchSlots) * (size_t)ctx->sm_count * kScrBytes;
+    cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    int tiles = 0;
+    for (int i = 0; i < n_jobs; ++i) {
+        fill_job_s(*jobs[i], tiles, &L.jobs[i]);
+        tiles += (int)((L.jobs[i].rows + kTile - 1) / kTile);
+    }
+    L.n_jobs = n_jobs;
+    L.n_tiles = tiles;
+    const int grid = std::min(tiles, ctx->sm_count);
+    const void* fn = bf ? (const void*)k_fista_tcs<true> : (const void*)k_fista_tcs<false>;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    if (bf)
+        k_fista_tcs<true><<<grid, kThreads, kSmemBytes, s>>>(L);
+    else
+        k_fista_tcs<false><<<grid, kThreads, kSmemBytes, s>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
+    std::vector<const DecodeArgs*> groups[2];
+    for (int i = 0; i < n_jobs; ++i) {
+        if ((long long)jobs[i].gs.n_cs * jobs[i].gs.nblk == 0) continue;
+        const bool bf = jobs[i].precision == CS_BF16 || jobs[i].precision == CS_BF16X2;
+        groups[bf ? 1 : 0].push_back(&jobs[i]);
+    }
+    for (int bf = 0; bf < 2; ++bf) {
+        std::vector<const DecodeArgs*>& g = groups[bf];
+        std::stable_sort(g.begin(), g.end(), [](const DecodeArgs* a, const DecodeArgs* b) {
+            return job_cost_s(*a) > job_cost_s(*b);
+        });
+        for (size_t i = 0; i < g.size(); i += kMaxJobsS) {
+            const int nj = (int)std::min(g.size() - i, (size_t)kMaxJobsS);
+            cudaError_t e = launch_group_s(g.data() + i, nj, bf == 1, s);
+            if (e != cudaSuccess) return e;
+        }
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_decode_tcs(const DecodeArgs& d, cudaStream_t s) { return launch_decode_tcs_batch(&d, 1, s); }
+
+}  // namespace csvc

@@ -128,7 +128,8 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
         return fail(CS_EINVAL, "beta and mu must be finite and > 0");
     if (params->iters < 0 || params->iters > kMaxIters) return fail(CS_EINVAL, "iters out of range");
     if (params->precision != CS_FP32) return fail(CS_EINVAL, "TV recovery computes in FP32 only");
-    if (params->engine == CS_ENGINE_TC) return fail(CS_EINVAL, "TV recovery has no tensor-core kernel");
+    if (params->engine == CS_ENGINE_TC || params->engine == CS_ENGINE_TC_STREAM)
+        return fail(CS_EINVAL, "TV recovery has no tensor-core kernel");
     GopShape gs;
     int st = make_shape(plan, params, &gs);
     if (st) return st;

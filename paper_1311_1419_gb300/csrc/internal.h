@@ -48,6 +48,10 @@ struct cs_ctx {
     // never share one
     float* tc8_scratch = nullptr;
     std::atomic<uint64_t> tc8_next_slot{0};
+    // iterates of the streaming tensor-core decode: kScratchSlots per-launch
+    // areas of sm_count per-CTA scratches
+    uint8_t* tcs_scratch = nullptr;
+    std::atomic<uint64_t> tcs_next_slot{0};
     std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
     std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
     // autotuned decode shape per (N, M): engine, plain-kernel threads and blocks per CTA
@@ -81,6 +85,9 @@ struct cs_plan {
     uint8_t* phi_tc = nullptr;
     int tc_ephi = 0;
     int tc_ep = 0;            // log2 scale of the residual operand P
+    // images of A * 2^tc_ea (same four types, m16 x N, 128-byte-swizzled atoms)
+    // for the streaming tensor-core decode; NULL when it does not take the shape
+    uint8_t* a_tcs = nullptr;
 };
 
 namespace csvc {
@@ -131,6 +138,14 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
 cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaStream_t s);
 size_t tc8_scratch_bytes(int sm_count);
+// any N in {64, 256, 1024}, M <= 512, iterates in global memory (decode_tcs.cu)
+bool tcs_plan_supported(int n, int m);
+size_t tcs_operand_bytes(int n, int m);
+size_t tcs_scratch_bytes(int sm_count);
+cudaError_t launch_tcs_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s);
+bool tcs_supported(const cs_plan* plan);
+cudaError_t launch_decode_tcs(const DecodeArgs& d, cudaStream_t s);
+cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
 
 // serving (serving.cu)
 void serving_destroy(cs_ctx* ctx);

@@ -117,6 +117,11 @@ __device__ __forceinline__ void fence_after_sync() {
 __device__ __forceinline__ void fence_proxy_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
+// The same for global memory: generic writes that a later bulk copy (async
+// proxy) reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
 
 // ---- tensor memory ------------------------------------------------------------
 // Executed by one whole warp.  The allocated base address is written to *dst.

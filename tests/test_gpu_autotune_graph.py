@@ -42,17 +42,19 @@ def _case(B, ctx, h, w, gop, b, m, iters, seed, precision=0, tail=0):
 
 @pytest.mark.parametrize("h,w,gop,b,m,iters", [(48, 64, 3, 8, 16, 60),      # N = 64
                                                (64, 96, 2, 32, 102, 40),    # N = 1024
-                                               (64, 96, 2, 32, 300, 30),    # N = 1024, M > 128: plain
+                                               (64, 96, 2, 32, 300, 30),    # N = 1024, M > 128: streaming
                                                (48, 80, 3, 16, 40, 50)])    # N = 256
 def test_autotuned_decode_matches_oracle(B, ctx, h, w, gop, b, m, iters):
     frames, plan, p, key, y = _case(B, ctx, h, w, gop, b, m, iters, seed=5)
     try:
         eng, thr, blk, ns = B.cs_autotune(ctx, plan)
-        assert eng in (B.CS_ENGINE_TC, B.CS_ENGINE_PLAIN) and ns > 0
+        assert eng in (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM, B.CS_ENGINE_PLAIN) and ns > 0
         if eng == B.CS_ENGINE_PLAIN:
             assert thr in (64, 128, 256, 512, 1024) and blk in (1, 2, 4, 8, 16)
         else:
-            assert b in (16, 32) and thr == 0 and blk == 0
+            assert thr == 0 and blk == 0
+            if eng == B.CS_ENGINE_TC:
+                assert b in (16, 32) and m <= 128
         print("N=%d M=%d: engine %d threads %d blocks/CTA %d, %.2f ns per block-iteration"
               % (b * b, m, eng, thr, blk, ns))
         out = torch.full((gop - 1, h, w), float("nan"), dtype=torch.float32, device="cuda")
