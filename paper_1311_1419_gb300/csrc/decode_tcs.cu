@@ -13,13 +13,17 @@
 //
 // Neither A (up to 2 MB as fp16 hi + lo at N = 1024, M = 512) nor the tile's
 // iterates (Z and s^{k-1}: 1 MB) fit on chip, so the operands stream: a copy
-// warp feeds a two-stage ring of 64-wide K slices through the bulk-copy engine
-// (the tile operand Z or P from this CTA's global scratch, the A slice from the
-// plan's swizzled image, which stays in L2), one thread issues the MMAs, and
-// two 256-column accumulators in tensor memory let the epilogue of one chunk
-// run while the next chunk is computed.  The epilogue (16 warps, TMEM lane
-// quarter = warp % 4, column group = warp / 4) forms P = U - y into the
-// scratch's P image and runs the gradient / soft-threshold / momentum step,
+// warp feeds a four-slot ring of 32-wide K slices (64-byte-swizzled operands,
+// 48 KB per slot, so that three slices are in flight while one is consumed)
+// through the bulk-copy engine (the tile operand Z or P from this CTA's global
+// scratch, the A slice from one of the plan's two swizzled images of A, which
+// stay in L2 and make every slice one contiguous copy), one thread issues the MMAs, and
+// two CTAs share an SM (half its shared and tensor memory each), so that one
+// tile's epilogue, bound by the iterates' global-memory traffic, overlaps the
+// other tile's MMAs.  The epilogue (8 warps, TMEM lane quarter = warp % 4,
+// column group = warp / 4) forms P = U - y (y staged once per tile in the
+// scratch, laid out for coalesced reads) into the scratch's P image and runs
+// the gradient / soft-threshold / momentum step,
 // reading and writing s^{k-1} (fp32) and Z (fp16 hi + lo, the next GEMM1's
 // operand image) in the scratch.  lambda_b needs max |A^T y_b| over all N
 // coefficients before the first step, so GEMM2 runs once more at k = 0 for it.
@@ -43,25 +47,29 @@ using namespace tc;
 
 constexpr int kTile = 128;                 // blocks per tile = TMEM lanes = MMA M
 constexpr int kMaxNs = 1024, kMaxM16s = 512;
-constexpr int kEpiWarps = 16;
+constexpr int kEpiWarps = 8;                // 4 TMEM lane quarters x 2 column groups
+constexpr int kColGroups = kEpiWarps / 4;
 constexpr int kEpiThreads = kEpiWarps * 32;
-constexpr int kThreads = 64 + kEpiThreads;  // warp 0 MMA, warp 1 copies, warps 2 .. 17 epilogue
-constexpr int kChunk = 256;                 // accumulator columns per chunk
-constexpr uint32_t kTBytes = kTile * 128;   // one 64-wide K slice of the tile operand (16 KB)
-constexpr uint32_t kBBytes = kChunk * 128;  // one K slice of up to 256 rows of A (32 KB)
+constexpr int kThreads = 64 + kEpiThreads;  // warp 0 MMA, warp 1 copies, warps 2 .. 9 epilogue
+constexpr int kCtasPerSm = 2;               // two tiles per SM: one's epilogue overlaps the other's MMAs
+constexpr int kChunk = 256;                 // accumulator columns per chunk (the CTA's TMEM)
+constexpr int kSliceK = 32;                 // K per ring slot: one 64-byte swizzle atom
+constexpr uint32_t kTBytes = kTile * 64;    // one K slice of the tile operand (8 KB)
+constexpr uint32_t kBBytes = kChunk * 64;   // one K slice of up to 256 rows of A (16 KB)
 constexpr int kStages = 2;
-constexpr uint32_t kStageBytes = 2 * (kTBytes + kBBytes);   // hi and lo of both: 96 KB
+constexpr uint32_t kStageBytes = 2 * (kTBytes + kBBytes);   // hi and lo of both: 48 KB
 constexpr uint32_t kOffC = kStages * kStageBytes;           // DCT matrix, <= 32 x 32 floats
 constexpr uint32_t kOffMisc = kOffC + 4096;
 constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024;     // + alignment slack
-// per-CTA global scratch: Z image (hi, lo), P image (hi, lo), s^{k-1}
-constexpr size_t kScrZ = 0, kScrP = 512 * 1024, kScrS = 768 * 1024, kScrBytes = 1280 * 1024;
+// per-CTA global scratch: Z image (hi, lo), P image (hi, lo), s^{k-1}, the tile's y
+constexpr size_t kScrZ = 0, kScrP = 512 * 1024, kScrS = 768 * 1024, kScrY = 1280 * 1024,
+                 kScrBytes = 1536 * 1024;
 constexpr uint64_t kWaitNs = 1000000000ull;                 // 1 s per wait
 constexpr uint32_t kBarEpi = 1;                             // named barrier of the epilogue
 
 struct MiscS {
     uint64_t full[kStages], empty[kStages];
-    uint64_t acc_full[2], acc_empty[2];
+    uint64_t acc_full, acc_empty;
     uint64_t p_ready, z_ready, drain;
     uint32_t tmem_base;
     int abort;
@@ -74,7 +82,8 @@ static_assert(sizeof(MiscS) <= 1024, "barrier block");
 
 // One job of a launch: the blocks of one cs_decode_gop call.
 struct TcsJob {
-    const uint8_t* a_img;   // A * 2^ea, hi image then lo image, m16 x n x 2 bytes each
+    const uint8_t* a1_img;  // GEMM1's image of A * 2^ea: hi then lo, m16 x n x 2 bytes each
+    const uint8_t* a2_img;  // GEMM2's image: hi then lo, m32 x n x 2 bytes each
     const float* y;
     const uint8_t* keys;
     float* out_f32;
@@ -160,7 +169,7 @@ __device__ __forceinline__ int g1_width(int m16, int c) {
 }
 __device__ __forceinline__ int g1_base(int m16, int c) { return c == 0 ? 0 : g1_width(m16, 0); }
 __device__ __forceinline__ int g2_width(int n) { return n < kChunk ? n : kChunk; }
-__device__ __forceinline__ int p_atoms(int m16) { return (m16 + 63) / 64; }
+__device__ __forceinline__ int p_slices(int m16) { return (m16 + kSliceK - 1) / kSliceK; }
 
 // Passes of a tile with K iterations: 0 = GEMM2 for lambda, 1 = GEMM2 of k = 0,
 // then GEMM1 (even) and GEMM2 (odd) of k = pass / 2.
@@ -170,7 +179,7 @@ __device__ __forceinline__ int pass_iter(int pass) { return pass < 2 ? 0 : pass 
 // Index (in float4) of s^{k-1} values 4 v .. 4 v + 3 of the column group cg of
 // GEMM2 chunk jc for tile row r: each epilogue warp reads 512 contiguous bytes.
 __device__ __forceinline__ size_t s_index4(int jc, int cg, int v, int r, int nc) {
-    return ((size_t)(jc * 4 + cg) * (nc / 16) + v) * kTile + r;
+    return ((size_t)(jc * kColGroups + cg) * (nc / (4 * kColGroups)) + v) * kTile + r;
 }
 
 // ---------------------------------------------------------------------------
@@ -179,8 +188,8 @@ template <bool BF>
 __device__ __forceinline__ void copy_role(const TcsLaunch& L, MiscS* ms, uint8_t* sm, int lane) {
     uint8_t* scr = L.scratch + (size_t)blockIdx.x * kScrBytes;
     uint32_t st = 0, pc = 0, zc = 0;
-    uint32_t last_par[kStages] = {0u, 0u};
-    bool issued[kStages] = {false, false};
+    uint32_t last_par[kStages] = {};
+    bool issued[kStages] = {};
     bool ok = true;
     for (;;) {
         const int tile = fetch_tile_s(L, ms);
@@ -188,11 +197,11 @@ __device__ __forceinline__ void copy_role(const TcsLaunch& L, MiscS* ms, uint8_t
         const TcsJob& J = L.jobs[job_of_s(L, tile)];
         cta_sync_s();   // B
         const int n = J.n, m16 = J.m16;
-        const size_t img = (size_t)m16 * n * 2;
+        const size_t img1 = (size_t)m16 * n * 2, img2 = (size_t)((m16 + 31) / 32 * 32) * n * 2;
         const uint8_t* z_hi = scr + kScrZ;
         const uint8_t* z_lo = z_hi + (size_t)n * 256;
         const uint8_t* p_hi = scr + kScrP;
-        const uint8_t* p_lo = p_hi + (size_t)p_atoms(m16) * kTBytes;
+        const uint8_t* p_lo = p_hi + (size_t)p_slices(m16) * kTBytes;
         for (int pass = 0; pass < 2 * J.iters; ++pass) {
             const bool g2 = pass_is_g2(pass);
             const int k = pass_iter(pass);
@@ -207,7 +216,7 @@ __device__ __forceinline__ void copy_role(const TcsLaunch& L, MiscS* ms, uint8_t
                 }
             }
             const int nch = g2 ? n / g2_width(n) : g1_chunks(m16);
-            const int nst = g2 ? p_atoms(m16) : n / 64;
+            const int nst = g2 ? p_slices(m16) : n / kSliceK;
             for (int c = 0; c < nch; ++c) {
                 for (int ks = 0; ks < nst; ++ks) {
                     const uint32_t s = st % kStages, par = (st / kStages) & 1;
@@ -215,34 +224,25 @@ __device__ __forceinline__ void copy_role(const TcsLaunch& L, MiscS* ms, uint8_t
                     if (ok && lane == 0) {
                         uint8_t* stg = sm + s * kStageBytes;
                         const int reps = split ? 2 : 1;
-                        uint32_t bbytes;
-                        if (g2) {
-                            const int nc = g2_width(n);
-                            const int ng = min(8, m16 / 8 - 8 * ks);
-                            bbytes = (uint32_t)(nc / 64) * (uint32_t)ng * 1024u;
-                        } else {
-                            bbytes = (uint32_t)g1_width(m16, c) * 128u;
-                        }
+                        // GEMM2: slice ks of P and of A's rows 32 ks .., columns of chunk c
+                        // (contiguous in the GEMM2 image); GEMM1: slice ks of Z and of A's
+                        // columns 32 ks .., rows of chunk c (contiguous in the GEMM1 image)
+                        const uint32_t bbytes = g2 ? (uint32_t)g2_width(n) * 64u
+                                                   : (uint32_t)g1_width(m16, c) * 64u;
                         mbar_arrive_expect_tx(&ms->full[s], (uint32_t)reps * (kTBytes + bbytes));
                         for (int h = 0; h < reps; ++h) {
-                            const uint8_t* aimg = J.a_img + (h ? img : 0);
                             uint8_t* t_dst = stg + h * kTBytes;
                             uint8_t* b_dst = stg + 2 * kTBytes + h * kBBytes;
                             if (g2) {
+                                const uint8_t* aimg = J.a2_img + (h ? img2 : 0);
                                 bulk_g2s(t_dst, (h ? p_lo : p_hi) + (size_t)ks * kTBytes, kTBytes, &ms->full[s]);
-                                const int nc = g2_width(n);
-                                const int ng = min(8, m16 / 8 - 8 * ks);
-                                for (int t = 0; t < nc / 64; ++t) {
-                                    const int a = c * (nc / 64) + t;   // j atom
-                                    bulk_g2s(b_dst + t * 8192,
-                                             aimg + ((size_t)a * (m16 / 8) + 8 * ks) * 1024,
-                                             (uint32_t)ng * 1024u, &ms->full[s]);
-                                }
+                                bulk_g2s(b_dst, aimg + ((size_t)ks * (n / 32) + (size_t)c * (g2_width(n) / 32)) * 2048,
+                                         bbytes, &ms->full[s]);
                             } else {
+                                const uint8_t* aimg = J.a1_img + (h ? img1 : 0);
                                 bulk_g2s(t_dst, (h ? z_lo : z_hi) + (size_t)ks * kTBytes, kTBytes, &ms->full[s]);
-                                const int i0 = g1_base(m16, c);
-                                bulk_g2s(b_dst, aimg + ((size_t)ks * (m16 / 8) + i0 / 8) * 1024,
-                                         (uint32_t)g1_width(m16, c) * 128u, &ms->full[s]);
+                                bulk_g2s(b_dst, aimg + ((size_t)ks * (m16 / 8) + g1_base(m16, c) / 8) * 512,
+                                         bbytes, &ms->full[s]);
                             }
                         }
                         last_par[s] = par;
@@ -281,12 +281,11 @@ __device__ __forceinline__ void mma_role_s(const TcsLaunch& L, MiscS* ms, uint8_
             const bool g2 = pass_is_g2(pass);
             const bool split = pass_iter(pass) >= J.split_from;
             const int nch = g2 ? n / g2_width(n) : g1_chunks(m16);
-            const int nst = g2 ? p_atoms(m16) : n / 64;
+            const int nst = g2 ? p_slices(m16) : n / kSliceK;
             for (int c = 0; c < nch; ++c) {
-                const uint32_t b = acc & 1, apar = (acc >> 1) & 1;
-                ok = wait_s(ms, &ms->acc_empty[b], apar ^ 1, L.err) && ok;
+                ok = wait_s(ms, &ms->acc_empty, (acc & 1) ^ 1, L.err) && ok;
                 fence_after_sync();
-                const uint32_t d = tbase + b * kChunk;
+                const uint32_t d = tbase;
                 const int width = g2 ? g2_width(n) : g1_width(m16, c);
                 const uint32_t id = idesc_f16(128, (uint32_t)width, BF ? 1u : 0u, 0u, g2 ? 1u : 0u);
 #pragma unroll 1
@@ -296,18 +295,20 @@ __device__ __forceinline__ void mma_role_s(const TcsLaunch& L, MiscS* ms, uint8_
                     fence_after_sync();
                     if (ok && lane == 0) {
                         const uint32_t stg = s_base + s * kStageBytes;
-                        const uint64_t t_hi = desc_sw128(stg, 16, 1024);
-                        const uint64_t t_lo = desc_sw128(stg + kTBytes, 16, 1024);
-                        const uint64_t b_hi = g2 ? desc_sw128(stg + 2 * kTBytes, 8192, 1024)
-                                                 : desc_sw128(stg + 2 * kTBytes, 16, 1024);
-                        const uint64_t b_lo = g2 ? desc_sw128(stg + 2 * kTBytes + kBBytes, 8192, 1024)
-                                                 : desc_sw128(stg + 2 * kTBytes + kBBytes, 16, 1024);
+                        // K-major operands: 8-row groups 512 bytes apart; GEMM2's A slice
+                        // is MN-major: 32-column atoms 2 KB apart, 8-row K groups 512 bytes
+                        const uint64_t t_hi = desc_sw64(stg, 16, 512);
+                        const uint64_t t_lo = desc_sw64(stg + kTBytes, 16, 512);
+                        const uint64_t b_hi = g2 ? desc_sw64(stg + 2 * kTBytes, 2048, 512)
+                                                 : desc_sw64(stg + 2 * kTBytes, 16, 512);
+                        const uint64_t b_lo = g2 ? desc_sw64(stg + 2 * kTBytes + kBBytes, 2048, 512)
+                                                 : desc_sw64(stg + 2 * kTBytes + kBBytes, 16, 512);
                         // K steps of 16 in this slice: 32 bytes along a K-major row; two
-                        // 8-row K groups (2 KB) in GEMM2's MN-major A slice
-                        const int nk = g2 ? min(4, m16 / 16 - 4 * ks) : 4;
+                        // 8-row K groups (1 KB) in GEMM2's MN-major A slice
+                        const int nk = g2 ? min(2, m16 / 16 - 2 * ks) : 2;
                         for (int kk = 0; kk < nk; ++kk) {
                             const uint32_t to = (uint32_t)kk * 2u;
-                            const uint32_t bo = g2 ? (uint32_t)kk * 128u : (uint32_t)kk * 2u;
+                            const uint32_t bo = g2 ? (uint32_t)kk * 64u : (uint32_t)kk * 2u;
                             const uint32_t accum = (ks > 0 || kk > 0) ? 1u : 0u;
                             mma_f16(d, t_hi + to, b_hi + bo, id, accum);
                             if (split) {
@@ -320,7 +321,7 @@ __device__ __forceinline__ void mma_role_s(const TcsLaunch& L, MiscS* ms, uint8_
                     __syncwarp();
                     ++st;
                 }
-                if (ok && lane == 0) mma_commit(&ms->acc_full[b]);
+                if (ok && lane == 0) mma_commit(&ms->acc_full);
                 __syncwarp();
                 ++acc;
             }
@@ -340,43 +341,37 @@ __device__ __forceinline__ void mma_role_s(const TcsLaunch& L, MiscS* ms, uint8_
 // group cg of the chunk.
 
 // P = (U su - y) sp for the thread's columns of GEMM1 chunk c (U = 0 at k = 0),
-// written as fp16/bf16 hi (and lo) into the scratch's P image.
+// written as fp16/bf16 hi (and lo) into the scratch's P image.  Columns go in
+// groups of 16: the group's y values (from the staged copy: 4 measurements of
+// 128 rows per 2 KB, so a warp reads 512 contiguous bytes) and accumulator
+// columns are requested together.
 template <bool BF>
-__device__ __forceinline__ void epi_residual(const TcsJob& J, uint8_t* p_hi, uint8_t* p_lo, uint32_t lane_addr,
-                                             uint32_t col, int c, int cg, int r, const float* yrow,
-                                             bool use_u, bool split) {
-    const int m16 = J.m16, m = J.gs.m;
-    const int w4 = g1_width(m16, c) / 4;
-    const int i0 = g1_base(m16, c) + cg * w4;
+__device__ __forceinline__ void epi_residual(const TcsJob& J, uint8_t* __restrict__ p_hi, uint8_t* __restrict__ p_lo,
+                                             uint32_t lane_addr, int c, int cg, int r,
+                                             const float4* __restrict__ y4, bool use_u, bool split) {
+    const int w4 = g1_width(J.m16, c) / kColGroups;
+    const int i0 = g1_base(J.m16, c) + cg * w4;
     for (int c0 = 0; c0 < w4; c0 += 16) {
         uint32_t u[4][4];
+        float4 yv[4];
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
 #pragma unroll
             for (int e = 0; e < 4; ++e) u[t][e] = 0u;
-            if (use_u && c0 + 4 * t < w4) tmem_ld4(lane_addr + col + (uint32_t)(cg * w4 + c0 + 4 * t), u[t]);
+            if (use_u && c0 + 4 * t < w4) tmem_ld4(lane_addr + (uint32_t)(cg * w4 + c0 + 4 * t), u[t]);
+            yv[t] = c0 + 4 * t < w4 ? y4[(size_t)((i0 + c0) / 4 + t) * kTile + r] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
         if (use_u) tmem_wait_ld();
 #pragma unroll
         for (int t = 0; t < 4; ++t) {
             if (c0 + 4 * t >= w4) break;
             const int i = i0 + c0 + 4 * t;
-            float yv[4] = {0.f, 0.f, 0.f, 0.f};
-            if (yrow) {
-                if (J.y_vec && i + 3 < m) {
-                    const float4 v4 = __ldg(reinterpret_cast<const float4*>(yrow + i));
-                    yv[0] = v4.x; yv[1] = v4.y; yv[2] = v4.z; yv[3] = v4.w;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; ++e)
-                        if (i + e < m) yv[e] = __ldg(yrow + i + e);
-                }
-            }
+            const float yy[4] = {yv[t].x, yv[t].y, yv[t].z, yv[t].w};
             float p[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) p[e] = (__uint_as_float(u[t][e]) * J.su - yv[e]) * J.sp;
+            for (int e = 0; e < 4; ++e) p[e] = (__uint_as_float(u[t][e]) * J.su - yy[e]) * J.sp;
             const uint32_t h0 = pack2s<BF>(make_float2(p[0], p[1])), h1 = pack2s<BF>(make_float2(p[2], p[3]));
-            const uint32_t off = sw128_offset((uint32_t)r, (uint32_t)i, kTile / 8);
+            const uint32_t off = sw64_offset((uint32_t)r, (uint32_t)i, kTile / 8);
             *reinterpret_cast<uint2*>(p_hi + off) = make_uint2(h0, h1);
             if (split) {
                 const float2 d0 = unpack2s<BF>(h0), d1 = unpack2s<BF>(h1);
@@ -389,11 +384,11 @@ __device__ __forceinline__ void epi_residual(const TcsJob& J, uint8_t* p_hi, uin
 }
 
 // lambda pass: max |G| over the thread's columns of GEMM2 chunk jc.
-__device__ __forceinline__ float epi_gmax(uint32_t lane_addr, uint32_t col, int w, int cg, float mx) {
+__device__ __forceinline__ float epi_gmax(uint32_t lane_addr, int w, int cg, float mx) {
     for (int c0 = 0; c0 < w; c0 += 16) {
         uint32_t g0[8], g1[8];
-        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0), g0);
-        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0 + 8), g1);
+        tmem_ld8(lane_addr + (uint32_t)(cg * w + c0), g0);
+        tmem_ld8(lane_addr + (uint32_t)(cg * w + c0 + 8), g1);
         tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
@@ -406,35 +401,54 @@ __device__ __forceinline__ float epi_gmax(uint32_t lane_addr, uint32_t col, int 
 
 // Gradient step, soft threshold and momentum for the thread's columns of GEMM2
 // chunk jc: s^k = soft(z^k - g / L, tau), z^{k+1} = s^k + beta_k (s^k - s^{k-1}).
+// 16 coefficients at a time: their z (hi, lo) and s^{k-1} are requested
+// together (eight independent 16-byte loads per round trip).
+struct UpdIn {
+    uint4 zh[2], zl[2];
+    float4 sp[4];
+};
 template <bool BF>
-__device__ __forceinline__ void epi_update(const TcsJob& J, uint8_t* scr, uint32_t lane_addr, uint32_t col,
+__device__ __forceinline__ void epi_update(const TcsJob& J, uint8_t* __restrict__ scr, uint32_t lane_addr,
                                            int jc, int cg, int r, int k, float tau, float bk, bool want_z) {
-    const int n = J.n, nc = g2_width(n), w = nc / 4;
-    uint8_t* z_hi = scr + kScrZ;
-    uint8_t* z_lo = z_hi + (size_t)n * 256;
-    float4* s4 = reinterpret_cast<float4*>(scr + kScrS);
+    const int n = J.n, nc = g2_width(n), w = nc / kColGroups;
+    uint8_t* __restrict__ z_hi = scr + kScrZ;
+    uint8_t* __restrict__ z_lo = z_hi + (size_t)n * 256;
+    float4* __restrict__ s4 = reinterpret_cast<float4*>(scr + kScrS);
     const float2 ginv2 = make_float2(-J.sg * J.inv_l, -J.sg * J.inv_l);
     const float2 b2 = make_float2(bk, bk);
-    for (int c0 = 0; c0 < w; c0 += 16) {
-        uint32_t g[2][8];
-        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0), g[0]);
-        tmem_ld8(lane_addr + col + (uint32_t)(cg * w + c0 + 8), g[1]);
-        tmem_wait_ld();
+    const int jb = jc * nc + cg * w;                                   // the thread's first coefficient
+    auto load_in = [&](int c0, UpdIn& in) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const int j = jc * nc + cg * w + c0 + 8 * h;               // first coefficient
-            const uint32_t zoff = sw128_offset((uint32_t)r, (uint32_t)j, kTile / 8);
-            const size_t si = s_index4(jc, cg, (c0 + 8 * h) / 4, r, nc);
-            uint4 zh = make_uint4(0u, 0u, 0u, 0u), zl = zh;
-            float4 sp0 = make_float4(0.f, 0.f, 0.f, 0.f), sp1 = sp0;
-            if (k > 0) {
-                zh = *reinterpret_cast<const uint4*>(z_hi + zoff);
-                zl = *reinterpret_cast<const uint4*>(z_lo + zoff);
-                sp0 = s4[si];
-                sp1 = s4[si + kTile];
-            }
-            const uint32_t zhw[4] = {zh.x, zh.y, zh.z, zh.w}, zlw[4] = {zl.x, zl.y, zl.z, zl.w};
-            const float spv[8] = {sp0.x, sp0.y, sp0.z, sp0.w, sp1.x, sp1.y, sp1.z, sp1.w};
+            const uint32_t zoff = sw64_offset((uint32_t)r, (uint32_t)(jb + c0 + 8 * h), kTile / 8);
+            in.zh[h] = *reinterpret_cast<const uint4*>(z_hi + zoff);
+            in.zl[h] = *reinterpret_cast<const uint4*>(z_lo + zoff);
+        }
+        const size_t si = s_index4(jc, cg, c0 / 4, r, nc);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) in.sp[v] = s4[si + (size_t)v * kTile];
+    };
+    for (int c0 = 0; c0 < w; c0 += 16) {
+        uint32_t g[2][8];
+        tmem_ld8(lane_addr + (uint32_t)(cg * w + c0), g[0]);
+        tmem_ld8(lane_addr + (uint32_t)(cg * w + c0 + 8), g[1]);
+        UpdIn cur;
+        if (k > 0) {
+            load_in(c0, cur);
+        } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) cur.zh[h] = cur.zl[h] = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) cur.sp[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        tmem_wait_ld();
+        const size_t si = s_index4(jc, cg, c0 / 4, r, nc);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t zhw[4] = {cur.zh[h].x, cur.zh[h].y, cur.zh[h].z, cur.zh[h].w};
+            const uint32_t zlw[4] = {cur.zl[h].x, cur.zl[h].y, cur.zl[h].z, cur.zl[h].w};
+            const float4 sa = cur.sp[2 * h], sb = cur.sp[2 * h + 1];
+            const float spv[8] = {sa.x, sa.y, sa.z, sa.w, sb.x, sb.y, sb.z, sb.w};
             float sv[8];
             uint32_t nh[4], nl[4];
 #pragma unroll
@@ -451,9 +465,10 @@ __device__ __forceinline__ void epi_update(const TcsJob& J, uint8_t* scr, uint32
                 nh[e] = pack2s<BF>(zn);
                 nl[e] = pack2s<BF>(sub2(zn, unpack2s<BF>(nh[e])));
             }
-            s4[si] = make_float4(sv[0], sv[1], sv[2], sv[3]);
-            s4[si + kTile] = make_float4(sv[4], sv[5], sv[6], sv[7]);
+            s4[si + (size_t)(2 * h) * kTile] = make_float4(sv[0], sv[1], sv[2], sv[3]);
+            s4[si + (size_t)(2 * h + 1) * kTile] = make_float4(sv[4], sv[5], sv[6], sv[7]);
             if (want_z) {
+                const uint32_t zoff = sw64_offset((uint32_t)r, (uint32_t)(jb + c0 + 8 * h), kTile / 8);
                 *reinterpret_cast<uint4*>(z_hi + zoff) = make_uint4(nh[0], nh[1], nh[2], nh[3]);
                 *reinterpret_cast<uint4*>(z_lo + zoff) = make_uint4(nl[0], nl[1], nl[2], nl[3]);
             }
@@ -464,13 +479,13 @@ __device__ __forceinline__ void epi_update(const TcsJob& J, uint8_t* scr, uint32
 // Wait for accumulator chunk `acc`, then (after the caller has read it) give
 // it back to the MMA warp.
 __device__ __forceinline__ void acc_wait(const TcsLaunch& L, MiscS* ms, uint32_t acc) {
-    wait_s(ms, &ms->acc_full[acc & 1], (acc >> 1) & 1, L.err);
+    wait_s(ms, &ms->acc_full, acc & 1, L.err);
     fence_after_sync();
 }
 __device__ __forceinline__ void acc_release(MiscS* ms, uint32_t acc, int lane) {
     fence_before_sync();
     __syncwarp();
-    if (lane == 0) mbar_arrive(&ms->acc_empty[acc & 1]);
+    if (lane == 0) mbar_arrive(&ms->acc_empty);
 }
 // The epilogue's global writes of an operand image are complete: let the copy warp read it.
 __device__ __forceinline__ void signal_copy(uint64_t* bar, int lane) {
@@ -485,7 +500,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
                                            int lane) {
     const int ew = warp - 2, q = warp & 3, cg = ew >> 2;
     const int r = 32 * q + lane;                      // TMEM lane = tile row
-    const int et = threadIdx.x - 64;                  // 0 .. 511
+    const int et = threadIdx.x - 64;                  // 0 .. kEpiThreads - 1
     const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
     uint8_t* scr = L.scratch + (size_t)blockIdx.x * kScrBytes;
     float* c_s = reinterpret_cast<float*>(sm + kOffC);
@@ -501,22 +516,36 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
         for (int i = et; i < bsz * bsz; i += kEpiThreads) c_s[i] = J.dct[i];
         cta_sync_s();   // B
         const long long tile_row0 = (long long)(tile - J.tile_begin) * kTile;
-        const long long row = tile_row0 + r;
-        const float* yrow = row < J.rows ? J.y + row * gs.m : nullptr;
         uint8_t* p_hi = scr + kScrP;
-        uint8_t* p_lo = p_hi + (size_t)p_atoms(m16) * kTBytes;
-        const int nch2 = n / g2_width(n), w2 = g2_width(n) / 4;
+        uint8_t* p_lo = p_hi + (size_t)p_slices(m16) * kTBytes;
+        float4* y4 = reinterpret_cast<float4*>(scr + kScrY);
+        const int nch2 = n / g2_width(n), w2 = g2_width(n) / kColGroups;
         if (K > 0) {
+            // the tile's y, read once (coalesced) and stored as [m16 / 4][128 rows] float4,
+            // zero beyond M and beyond the call's last block
+            {
+                const int m = gs.m;
+                const long long rows_left = J.rows - tile_row0;
+                float* yf = reinterpret_cast<float*>(y4);
+                const float* src = J.y + tile_row0 * m;
+                for (int q = et; q < kTile * m16; q += kEpiThreads) {
+                    const int rr = q / m16, i = q % m16;
+                    const float v = (i < m && rr < rows_left) ? src[(size_t)rr * m + i] : 0.f;
+                    yf[((size_t)(i / 4) * kTile + rr) * 4 + (i & 3)] = v;
+                }
+                __threadfence_block();
+                named_sync(kBarEpi, kEpiThreads);
+            }
             const bool split0 = 0 >= J.split_from;
             // P = -y for GEMM2 of k = 0 (z = 0, so U = 0)
             for (int c = 0; c < g1_chunks(m16); ++c)
-                epi_residual<BF>(J, p_hi, p_lo, lane_addr, 0u, c, cg, r, yrow, false, split0);
+                epi_residual<BF>(J, p_hi, p_lo, lane_addr, c, cg, r, y4, false, split0);
             signal_copy(&ms->p_ready, lane);
             // lambda_b = lambda_rel ||A^T y_b||_inf from G = -A^T y
             float mx = 0.f;
             for (int jc = 0; jc < nch2; ++jc, ++acc) {
                 acc_wait(L, ms, acc);
-                mx = epi_gmax(lane_addr, (acc & 1) * kChunk, w2, cg, mx);
+                mx = epi_gmax(lane_addr, w2, cg, mx);
                 acc_release(ms, acc, lane);
             }
             atomicMax(&ms->colmax[r], __float_as_uint(mx * J.sg));
@@ -528,8 +557,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
                     const bool split = k >= J.split_from;
                     for (int c = 0; c < g1_chunks(m16); ++c, ++acc) {
                         acc_wait(L, ms, acc);
-                        epi_residual<BF>(J, p_hi, p_lo, lane_addr, (acc & 1) * kChunk, c, cg, r, yrow, true,
-                                         split);
+                        epi_residual<BF>(J, p_hi, p_lo, lane_addr, c, cg, r, y4, true, split);
                         acc_release(ms, acc, lane);
                     }
                     signal_copy(&ms->p_ready, lane);
@@ -537,7 +565,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
                 const float bk = L.beta[k];
                 for (int jc = 0; jc < nch2; ++jc, ++acc) {
                     acc_wait(L, ms, acc);
-                    epi_update<BF>(J, scr, lane_addr, (acc & 1) * kChunk, jc, cg, r, k, tau, bk, want_z);
+                    epi_update<BF>(J, scr, lane_addr, jc, cg, r, k, tau, bk, want_z);
                     acc_release(ms, acc, lane);
                 }
                 if (want_z) signal_copy(&ms->z_ready, lane);
@@ -549,7 +577,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
         float* s_s = reinterpret_cast<float*>(sm);   // stage 0 is idle now
         float* t_s = s_s + 1024;
         const float4* s4 = reinterpret_cast<const float4*>(scr + kScrS);
-        const int nc = g2_width(n), w = nc / 4, gb = 1024 / n;
+        const int nc = g2_width(n), w = nc / kColGroups, gb = 1024 / n;
         const size_t frame_px = (size_t)gs.h * gs.w;
         for (int b0 = 0; b0 < kTile; b0 += gb) {
             for (int e = et; e < gb * n; e += kEpiThreads) {
@@ -593,7 +621,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
 }
 
 template <bool BF>
-__global__ void __launch_bounds__(kThreads, 1) k_fista_tcs(const __grid_constant__ TcsLaunch L) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_fista_tcs(const __grid_constant__ TcsLaunch L) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -605,10 +633,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tcs(const __grid_constant
                 mbar_init(&ms->full[s], 1);
                 mbar_init(&ms->empty[s], 1);
             }
-            for (int b = 0; b < 2; ++b) {
-                mbar_init(&ms->acc_full[b], 1);
-                mbar_init(&ms->acc_empty[b], kEpiWarps);
-            }
+            mbar_init(&ms->acc_full, 1);
+            mbar_init(&ms->acc_empty, kEpiWarps);
             mbar_init(&ms->p_ready, kEpiWarps);
             mbar_init(&ms->z_ready, kEpiWarps);
             mbar_init(&ms->drain, 1);
@@ -616,7 +642,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tcs(const __grid_constant
             fence_mbar_init();
         }
         __syncwarp();
-        tmem_alloc(&ms->tmem_base, 2 * kChunk);
+        tmem_alloc(&ms->tmem_base, kChunk);
         tmem_relinquish();
     }
     cta_sync_s();
@@ -628,30 +654,45 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tcs(const __grid_constant
     else
         epi_role_s<BF>(L, ms, sm, tbase, warp, lane);
     cta_sync_s();
-    if (warp == 0) tmem_dealloc(tbase, 2 * kChunk);
+    if (warp == 0) tmem_dealloc(tbase, kChunk);
 }
 
 int m16_of_s(int m) { return (m + 15) / 16 * 16; }
+int m32_of_s(int m) { return (m + 31) / 32 * 32; }
 
-// The fp16 hi / lo and bf16 hi / lo images of A * 2^ea for this kernel: m16
-// rows x n, rows >= M zero, 128-byte-swizzled atoms of 8 rows x 64 columns,
-// atom (col / 64, row / 8) at ((col / 64) * m16 / 8 + row / 8) * 1024.
+// The plan's operand images of A * 2^ea for this kernel, in four types each
+// (fp16 hi, fp16 lo, bf16 hi, bf16 lo), rows i >= M zero, 64-byte-swizzled atoms
+// of 8 rows x 32 columns:
+//   GEMM1 image, m16 x n: atom (i / 8, j / 32) at ((j / 32) * m16 / 8 + i / 8) * 512,
+//     so a K slice (32 columns j) of any run of rows is contiguous;
+//   GEMM2 image, m32 x n: atom (i / 8, j / 32) at (((i / 32) * n / 32 + j / 32) * 4 +
+//     (i % 32) / 8) * 512, so a K slice (32 rows i) of any run of 32-column atoms
+//     is contiguous (read MN-major: j along the 64-byte rows).
 __global__ void k_tcs_images(const float* __restrict__ a, uint8_t* __restrict__ img, int n, int m, int m16,
-                             float scale) {
+                             int m32, float scale) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= m16 * n) return;
+    if (idx >= m32 * n) return;
     const int row = idx / n, col = idx % n;
     const float v = row < m ? a[(size_t)row * n + col] * scale : 0.f;
-    const uint32_t off = sw128_offset((uint32_t)row, (uint32_t)col, (uint32_t)m16 / 8);
-    const size_t img_bytes = (size_t)m16 * n * 2;
     const __half hh = __float2half_rn(v);
     const __half hl = __float2half_rn(v - __half2float(hh));
     const __nv_bfloat16 bh = __float2bfloat16_rn(v);
     const __nv_bfloat16 bl = __float2bfloat16_rn(v - __bfloat162float(bh));
-    *reinterpret_cast<__half*>(img + off) = hh;
-    *reinterpret_cast<__half*>(img + img_bytes + off) = hl;
-    *reinterpret_cast<__nv_bfloat16*>(img + 2 * img_bytes + off) = bh;
-    *reinterpret_cast<__nv_bfloat16*>(img + 3 * img_bytes + off) = bl;
+    const size_t img1 = (size_t)m16 * n * 2, img2 = (size_t)m32 * n * 2;
+    if (row < m16) {
+        const uint32_t off = sw64_offset((uint32_t)row, (uint32_t)col, (uint32_t)m16 / 8);
+        *reinterpret_cast<__half*>(img + off) = hh;
+        *reinterpret_cast<__half*>(img + img1 + off) = hl;
+        *reinterpret_cast<__nv_bfloat16*>(img + 2 * img1 + off) = bh;
+        *reinterpret_cast<__nv_bfloat16*>(img + 3 * img1 + off) = bl;
+    }
+    const uint32_t r8 = (uint32_t)row & 7, chunk = ((uint32_t)col & 31) >> 3;
+    const size_t atom = ((size_t)(row / 32) * (n / 32) + col / 32) * 4 + (row % 32) / 8;
+    const size_t off2 = 4 * img1 + atom * 512 + r8 * 64 + ((chunk ^ (r8 >> 1)) << 4) + ((col & 7) << 1);
+    *reinterpret_cast<__half*>(img + off2) = hh;
+    *reinterpret_cast<__half*>(img + img2 + off2) = hl;
+    *reinterpret_cast<__nv_bfloat16*>(img + 2 * img2 + off2) = bh;
+    *reinterpret_cast<__nv_bfloat16*>(img + 3 * img2 + off2) = bl;
 }
 
 }  // namespace
@@ -659,13 +700,17 @@ __global__ void k_tcs_images(const float* __restrict__ a, uint8_t* __restrict__ 
 bool tcs_plan_supported(int n, int m) {
     return (n == 64 || n == 256 || n == kMaxNs) && m >= 1 && m16_of_s(m) <= kMaxM16s;
 }
-size_t tcs_operand_bytes(int n, int m) { return 4ull * (size_t)m16_of_s(m) * (size_t)n * 2; }
-size_t tcs_scratch_bytes(int sm_count) { return (size_t)kScratchSlots * (size_t)sm_count * kScrBytes; }
+size_t tcs_operand_bytes(int n, int m) {
+    return 4ull * (size_t)(m16_of_s(m) + m32_of_s(m)) * (size_t)n * 2;
+}
+size_t tcs_scratch_bytes(int sm_count) {
+    return (size_t)kScratchSlots * (size_t)(kCtasPerSm * sm_count) * kScrBytes;
+}
 
 cudaError_t launch_tcs_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s) {
-    const int m16 = m16_of_s(m);
-    const int total = m16 * n;
-    k_tcs_images<<<(total + 255) / 256, 256, 0, s>>>(a, img, n, m, m16, ldexpf(1.f, ea));
+    const int m16 = m16_of_s(m), m32 = m32_of_s(m);
+    const int total = m32 * n;
+    k_tcs_images<<<(total + 255) / 256, 256, 0, s>>>(a, img, n, m, m16, m32, ldexpf(1.f, ea));
     return cudaGetLastError();
 }
 
@@ -677,8 +722,9 @@ static void fill_job_s(const DecodeArgs& d, int tile_begin, TcsJob* J) {
     const cs_plan* p = d.plan;
     const bool bf = d.precision == CS_BF16 || d.precision == CS_BF16X2;
     const int m16 = m16_of_s(p->m);
-    const size_t img = (size_t)m16 * p->n * 2;
-    J->a_img = p->a_tcs + (bf ? 2 * img : 0);
+    const size_t img1 = (size_t)m16 * p->n * 2, img2 = (size_t)m32_of_s(p->m) * p->n * 2;
+    J->a1_img = p->a_tcs + (bf ? 2 * img1 : 0);
+    J->a2_img = p->a_tcs + 4 * img1 + (bf ? 2 * img2 : 0);
     J->y = d.y;
     J->keys = d.key;
     J->out_f32 = d.out_f32;
@@ -715,8 +761,8 @@ static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, boo
     L.beta = jobs[0]->beta;
     L.err = ctx->err_dev;
     L.tile_counter = ctx->counters_dev + (ctx->next_counter.fetch_add(1) % kTileCounters);
-    L.scratch = ctx->tcs_scratch +
-                (ctx->tcs_next_slot.fetch_add(1) % kScratchSlots) * (size_t)ctx->sm_count * kScrBytes;
+    L.scratch = ctx->tcs_scratch + (ctx->tcs_next_slot.fetch_add(1) % kScratchSlots) *
+                                       (size_t)(kCtasPerSm * ctx->sm_count) * kScrBytes;
     cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     int tiles = 0;
@@ -726,7 +772,7 @@ static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, boo
     }
     L.n_jobs = n_jobs;
     L.n_tiles = tiles;
-    const int grid = std::min(tiles, ctx->sm_count);
+    const int grid = std::min(tiles, kCtasPerSm * ctx->sm_count);
     const void* fn = bf ? (const void*)k_fista_tcs<true> : (const void*)k_fista_tcs<false>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;

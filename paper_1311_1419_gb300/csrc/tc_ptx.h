@@ -281,6 +281,29 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr, uint32_t lbo, uin
     return d;
 }
 
+// The same with a 64-byte swizzle: atoms of 8 rows of 64 bytes (512 bytes,
+// on 512-byte boundaries); within an atom the 16-byte chunk index is XORed
+// with (row / 2) % 4.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= 1ull << 46;  // descriptor version for tcgen05
+    d |= 4ull << 61;  // SWIZZLE_64B
+    return d;
+}
+
+// Byte offset of element (row, col) of a 16-bit matrix stored as 64-byte-
+// swizzled atoms of 8 rows x 32 columns; atom (row/8, col/32) starts at
+// ((col/32) * row_groups + row/8) * 512.
+__host__ __device__ __forceinline__ uint32_t sw64_offset(uint32_t row, uint32_t col,
+                                                         uint32_t row_groups) {
+    const uint32_t atom = (col >> 5) * row_groups + (row >> 3);
+    const uint32_t r = row & 7, chunk = (col & 31) >> 3;
+    return atom * 512u + r * 64u + ((chunk ^ (r >> 1)) << 4) + ((col & 7) << 1);
+}
+
 // Instruction descriptor of kind::f16 with f32 accumulation.
 // ab_bf16: 0 = f16 inputs, 1 = bf16 inputs; a_mn / b_mn: operand is MN-major.
 __host__ __device__ constexpr uint32_t idesc_f16(uint32_t m, uint32_t n, uint32_t ab_bf16,
