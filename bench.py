@@ -142,8 +142,8 @@ SERVING = {
     "workload": "256 synthetic cameras, resolution QCIF/CIF/720p/1080p (p = .4/.3/.2/.1), "
                 "GOP uniform 4..32, 16x16 or 32x32 blocks (p = .5/.5), M/N uniform 5%..25%, "
                 "Phi seed = camera id, FISTA 200 iters; one request = one GOP decode; Poisson "
-                "arrivals; mixed-precision runs fall back to FP32 where a shape has no "
-                "tensor-core kernel (32x32 blocks with M > 128)",
+                "arrivals; every shape of the mix has a tensor-core kernel (on chip for M <= 128, "
+                "streaming above)",
     "cameras": 256, "iters": 200, "seed": 7,
 }
 
@@ -166,7 +166,7 @@ def serving_run(B, torch, dev, precision, tail, rates, seconds, hbm_budget=8 << 
             b = (16, 32)[rng.integers(2)]
             m = max(1, int(np.rint(b * b * rng.uniform(0.05, 0.25))))
             plan = B.cs_make_phi(ctx, b * b, m, cid)
-            tc = m <= 128
+            tc = (m + 15) // 16 * 16 <= 512       # on-chip or streaming tensor-core kernel
             p = B.make_params(h, w, gop, b, m, iters=SERVING["iters"],
                               precision=precision if tc else B.CS_FP32,
                               fp32_tail_iters=tail if tc else 0)
@@ -284,6 +284,26 @@ def run_reference(args, wl, frames):
     print(json.dumps(line), flush=True)
 
 
+def mixed_launches(jobs) -> int:
+    """Kernels one cs_decode_batch of the mix launches: one per group of up to 48
+    jobs of each tensor-core kernel (16x16 on chip by shared-memory layout, 32x32
+    cluster, streaming; one operand type here) and one per plain-kernel job."""
+    groups = {}
+    for j in jobs:
+        b, m = j["p"].block, j["p"].m
+        m16 = (m + 15) // 16 * 16
+        if not j["tc"]:
+            key = ("plain", len(groups))
+        elif b == 16 and m <= 128:
+            key = ("tc", m16 <= 96)
+        elif b == 32 and m <= 128:
+            key = ("tc8",)
+        else:
+            key = ("tcs",)
+        groups[key] = groups.get(key, 0) + 1
+    return sum(-(-c // 48) for c in groups.values())
+
+
 def run_mixed64(args, wl):
     """The heterogeneous batch: every GOP a job of its own plan, one batched call
     captured in a CUDA graph and replayed; value = CS pixels per second."""
@@ -364,7 +384,7 @@ def run_mixed64(args, wl):
             "jobs": len(jobs), "tensor_core_jobs": sum(j["tc"] for j in jobs),
             "pixels_per_step": pixels, "tensor_core_pixel_share": tc_pix / pixels,
             "gflop_per_step": sum(j["flops"] for j in jobs) / 1e9,
-            "gpu_launches": None, "clocks": clocks.summary(), "setup_s": setup_s,
+            "gpu_launches": mixed_launches(jobs), "clocks": clocks.summary(), "setup_s": setup_s,
             "autotuned_shapes": len(tuned),
         }
         print(json.dumps(line), flush=True)
@@ -380,7 +400,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--engine", choices=["auto", "plain", "tc"], default="auto")
+    ap.add_argument("--engine", choices=["auto", "plain", "tc", "tcs"], default="auto")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cif",
                     help="cif: the CIF M-sweep (default); 720p: 32x32 blocks, M = 102")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -439,7 +459,8 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
-    engine = {"auto": B.CS_ENGINE_AUTO, "plain": B.CS_ENGINE_PLAIN, "tc": B.CS_ENGINE_TC}[args.engine]
+    engine = {"auto": B.CS_ENGINE_AUTO, "plain": B.CS_ENGINE_PLAIN, "tc": B.CS_ENGINE_TC,
+              "tcs": B.CS_ENGINE_TC_STREAM}[args.engine]
     h, w, gop, b, iters = wl["height"], wl["width"], wl["gop"], wl["block"], wl["iters"]
     n = b * b
     n_gops = wl["frames"] // gop
@@ -473,17 +494,19 @@ def main():
     # our kernels per step: one encode and one PSNR per M, and the decode: one
     # launch per call with --no-batch, else one per (operand type, shared-memory
     # layout) group of the 16x16 tensor path (M16 <= 96 or <= 128), one per group
-    # of the 32x32 cluster path, one per plain-kernel job
+    # of the 32x32 cluster path, one per group of the streaming path, one per
+    # plain-kernel job (FP32: one operand type)
     def decode_launches():
         if args.no_batch:
             return len(wl["ms"])
         groups, plain = set(), 0
         for m in wl["ms"]:
             m16 = (m + 15) // 16 * 16
-            tc = engine != B.CS_ENGINE_PLAIN and (
-                engine == B.CS_ENGINE_TC or tuned[str(m)]["engine"] == B.CS_ENGINE_TC)
-            if not tc:
+            eng = engine if engine != B.CS_ENGINE_AUTO else tuned[str(m)]["engine"]
+            if eng == B.CS_ENGINE_PLAIN:
                 plain += 1
+            elif eng == B.CS_ENGINE_TC_STREAM:
+                groups.add(("tcs",))
             elif n == 256:
                 groups.add(("tc", m16 <= 96))
             else:

@@ -171,7 +171,7 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) ctx->streams.push_back(s);
     }
-    for (int i = 0; e == cudaSuccess && i < 3; ++i) {
+    for (int i = 0; e == cudaSuccess && i < 4; ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) ctx->fork_streams.push_back(s);
@@ -367,11 +367,29 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
         (engine == CS_ENGINE_TC ? tc_jobs : engine == CS_ENGINE_TC_STREAM ? tcs_jobs : plain_jobs).push_back(d);
     }
     cudaError_t e = cudaSuccess;
-    if (!tc_jobs.empty()) e = launch_decode_tc_batch(tc_jobs.data(), (int)tc_jobs.size(), (cudaStream_t)stream);
-    if (e == cudaSuccess && !tcs_jobs.empty())
-        e = launch_decode_tcs_batch(tcs_jobs.data(), (int)tcs_jobs.size(), (cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!tcs_jobs.empty() && !tc_jobs.empty()) {
+        // the streaming kernel's launch on the context's last fork stream, joined
+        // back on s: its CTAs take SMs as the on-chip launches' tails drain
+        cudaStream_t fs = ctx->fork_streams.back();
+        cudaEvent_t fork = nullptr, join = nullptr;
+        e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, fork, 0);
+        if (e == cudaSuccess) e = launch_decode_tcs_batch(tcs_jobs.data(), (int)tcs_jobs.size(), fs);
+        if (e == cudaSuccess) e = cudaEventRecord(join, fs);
+        if (e == cudaSuccess) e = launch_decode_tc_batch(tc_jobs.data(), (int)tc_jobs.size(), s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join, 0);
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+    } else if (!tc_jobs.empty()) {
+        e = launch_decode_tc_batch(tc_jobs.data(), (int)tc_jobs.size(), s);
+    } else if (!tcs_jobs.empty()) {
+        e = launch_decode_tcs_batch(tcs_jobs.data(), (int)tcs_jobs.size(), s);
+    }
     for (size_t i = 0; e == cudaSuccess && i < plain_jobs.size(); ++i)
-        e = launch_decode_plain(plain_jobs[i], (cudaStream_t)stream);
+        e = launch_decode_plain(plain_jobs[i], s);
     if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");
     return CS_OK;
 }

@@ -106,6 +106,7 @@ struct TcsLaunch {
     int* err;
     int* tile_counter;
     uint8_t* scratch;       // this launch's area: gridDim.x x kScrBytes
+    int drop_arrival;       // test hook: CTA 0 withholds one epilogue warp's first P-ready arrival
     int n_jobs;
     int n_tiles;
     TcsJob jobs[kMaxJobsS];
@@ -488,10 +489,10 @@ __device__ __forceinline__ void acc_release(MiscS* ms, uint32_t acc, int lane) {
     if (lane == 0) mbar_arrive(&ms->acc_empty);
 }
 // The epilogue's global writes of an operand image are complete: let the copy warp read it.
-__device__ __forceinline__ void signal_copy(uint64_t* bar, int lane) {
+__device__ __forceinline__ void signal_copy(uint64_t* bar, int lane, bool withhold = false) {
     fence_proxy_async_global();
     __syncwarp();
-    if (lane == 0) mbar_arrive(bar);
+    if (lane == 0 && !withhold) mbar_arrive(bar);
 }
 
 // Warps 2 .. 17.
@@ -505,6 +506,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
     uint8_t* scr = L.scratch + (size_t)blockIdx.x * kScrBytes;
     float* c_s = reinterpret_cast<float*>(sm + kOffC);
     uint32_t acc = 0;
+    bool first_tile = true;
     for (;;) {
         const int tile = fetch_tile_s(L, ms);
         if (tile >= L.n_tiles) break;
@@ -540,7 +542,9 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
             // P = -y for GEMM2 of k = 0 (z = 0, so U = 0)
             for (int c = 0; c < g1_chunks(m16); ++c)
                 epi_residual<BF>(J, p_hi, p_lo, lane_addr, c, cg, r, y4, false, split0);
-            signal_copy(&ms->p_ready, lane);
+            // (the test hook withholds one warp's arrival in CTA 0: the copy warp's
+            // bounded wait then gives up and the CTA drains)
+            signal_copy(&ms->p_ready, lane, L.drop_arrival && blockIdx.x == 0 && ew == 1 && first_tile);
             // lambda_b = lambda_rel ||A^T y_b||_inf from G = -A^T y
             float mx = 0.f;
             for (int jc = 0; jc < nch2; ++jc, ++acc) {
@@ -617,6 +621,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
             named_sync(kBarEpi, kEpiThreads);
         }
         cta_sync_s();   // C
+        first_tile = false;
     }
 }
 
@@ -761,6 +766,7 @@ static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, boo
     L.beta = jobs[0]->beta;
     L.err = ctx->err_dev;
     L.tile_counter = ctx->counters_dev + (ctx->next_counter.fetch_add(1) % kTileCounters);
+    L.drop_arrival = ctx->debug_flags.exchange(0) & CS_DEBUG_DROP_ARRIVAL;
     L.scratch = ctx->tcs_scratch + (ctx->tcs_next_slot.fetch_add(1) % kScratchSlots) *
                                        (size_t)(kCtasPerSm * ctx->sm_count) * kScrBytes;
     cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);

@@ -21,22 +21,27 @@ def B():
     return binding
 
 
-def test_withheld_arrival_times_out_and_the_context_recovers(B):
+@pytest.mark.parametrize("b,m,engine", [(16, 32, "TC"), (32, 200, "TC_STREAM")])
+def test_withheld_arrival_times_out_and_the_context_recovers(B, b, m, engine):
+    # the on-chip kernel (16 x 16 blocks) and the streaming kernel (32 x 32, M > 128)
+    eng = getattr(B, "CS_ENGINE_" + engine)
     ctx = B.cs_ctx_create(0)
-    plan = B.cs_make_phi(ctx, 256, 32, 3)
+    plan = B.cs_make_phi(ctx, b * b, m, 3)
     try:
-        frames = scenes.surveillance_video(2, 64, 128, seed=5)      # 32 blocks: one tile
-        p = B.make_params(64, 128, 2, 16, 32, iters=20, engine=B.CS_ENGINE_TC)
+        h, w = 64, 128
+        nblk = (h // b) * (w // b)                                    # one tile
+        frames = scenes.surveillance_video(2, h, w, seed=5)
+        p = B.make_params(h, w, 2, b, m, iters=20, engine=eng)
         s = torch.cuda.current_stream()
         f = torch.from_numpy(frames).cuda()
-        y = torch.empty((1, 32, 32), dtype=torch.float32, device="cuda")
+        y = torch.empty((1, nblk, m), dtype=torch.float32, device="cuda")
         B.cs_encode_gop(plan, p, f, y, s)
-        ref = torch.empty((1, 64, 128), dtype=torch.float32, device="cuda")
+        ref = torch.empty((1, h, w), dtype=torch.float32, device="cuda")
         B.cs_decode_gop(plan, p, f[:1], y, ref, None, s)
         B.cs_ctx_status(ctx)                                          # healthy
 
         B.cs_ctx_set_debug(ctx, B.CS_DEBUG_DROP_ARRIVAL)
-        out = torch.full((1, 64, 128), -1.0, dtype=torch.float32, device="cuda")
+        out = torch.full((1, h, w), -1.0, dtype=torch.float32, device="cuda")
         t0 = time.time()
         B.cs_decode_gop(plan, p, f[:1], y, out, None, s)
         with pytest.raises(B.CsError) as ei:
@@ -45,7 +50,7 @@ def test_withheld_arrival_times_out_and_the_context_recovers(B):
         assert time.time() - t0 < 30
         B.cs_ctx_status(ctx)                                          # reported once
 
-        again = torch.empty((1, 64, 128), dtype=torch.float32, device="cuda")
+        again = torch.empty((1, h, w), dtype=torch.float32, device="cuda")
         B.cs_decode_gop(plan, p, f[:1], y, again, None, s)
         B.cs_ctx_status(ctx)
         assert np.array_equal(again.cpu().numpy(), ref.cpu().numpy())
