@@ -147,3 +147,46 @@ def test_tcs_in_a_batch_equals_alone(B, ctx):
     finally:
         for x in prepared:
             B.cs_plan_destroy(x[0])
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-4), (2, 2e-3)])   # FP32, split-BF16 (BF16X2)
+def test_tcs_full_720p_sampled(B, ctx, precision, tol):
+    """A 720p GOP (1280 x 720, G = 16: 13800 blocks of 32 x 32, the last block row
+    cropped) at M = 512 and K = 300, in the precision and launch path the mixed
+    bench times; 96 sampled blocks recovered by the oracle one by one, with y
+    measured by the oracle."""
+    h, w, gop, b, m, iters, seed = 720, 1280, 16, 32, 512, 300, 21
+    frames = scenes.surveillance_video(gop, h, w, seed=seed)
+    plan = B.cs_make_phi(ctx, b * b, m, seed)
+    try:
+        p = B.make_params(h, w, gop, b, m, iters=iters, precision=precision)
+        nbr, nbc = -(-h // b), -(-w // b)
+        nblk = nbr * nbc
+        y = torch.empty((gop - 1, nblk, m), dtype=torch.float32, device="cuda")
+        B.cs_encode_gop(plan, p, torch.from_numpy(frames).cuda(), y, torch.cuda.current_stream())
+        key = torch.from_numpy(np.ascontiguousarray(frames[:1])).cuda()
+        out = torch.full((gop - 1, h, w), float("nan"), dtype=torch.float32, device="cuda")
+        B.cs_decode_gop(plan, p, key, y, out, None, torch.cuda.current_stream())
+        B.cs_ctx_status(ctx)
+        out_f = out.cpu().numpy().astype(np.float64)
+    finally:
+        B.cs_plan_destroy(plan)
+    oplan = O.Plan(b * b, m, seed)
+    yo = O.encode(oplan, frames, gop)
+    rng = np.random.default_rng(seed)
+    rows = np.sort(rng.choice(yo.shape[0] * nblk, size=96, replace=False))
+    rows[-1] = yo.shape[0] * nblk - 1          # the last block: the cropped bottom-right corner
+    r_hat = O.decode_blocks(oplan, yo.reshape(-1, m)[rows], iters)
+    key64 = frames[0].astype(np.float64)
+    got, want = [], []
+    for i, r in enumerate(rows):
+        c, blk = divmod(int(r), nblk)
+        bi, bj = divmod(blk, nbc)
+        hh, ww = min(b, h - bi * b), min(b, w - bj * b)
+        sl = (slice(bi * b, bi * b + hh), slice(bj * b, bj * b + ww))
+        want.append((key64[sl] + r_hat[i].reshape(b, b)[:hh, :ww]).ravel())
+        got.append(out_f[c][sl].ravel())
+    got, want = np.concatenate(got), np.concatenate(want)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    print("720p M=512 precision %d: sampled blocks rel-l2 %.3g" % (precision, err))
+    assert err <= tol
