@@ -57,6 +57,10 @@ WORKLOADS["mixed64"] = {
 WORKLOAD = WORKLOADS["cif"]
 METRIC = WORKLOAD["metric"]
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the CIF step's decode, its
+# two tensor-core launches together, from one ncu capture of that exact configuration;
+# reported as roofline.traffic for it only (null for any other configuration or kernel)
+CIF_DECODE_DRAM_BYTES = 62_840_000
 FP32_LANES_PER_SM = 128
 
 
@@ -624,6 +628,10 @@ def main():
     tc_used = engine == B.CS_ENGINE_TC or (
         engine == B.CS_ENGINE_AUTO and all(t["engine"] == B.CS_ENGINE_TC for t in tuned.values()))
     achieved = flops / (dec_ms / 1e3) / 1e12
+    # the captured traffic belongs to the CIF sweep's batched FP32 tensor-core decode only
+    traffic = CIF_DECODE_DRAM_BYTES if (tc_used and args.workload == "cif" and not args.no_batch
+                                        and not args.only_m and
+                                        all(p.precision == B.CS_FP32 for p in params.values())) else None
     if tc_used:
         # kind::f16 MMAs (fp16 operands): the measured bf16 peak x the nominal
         # fp16:bf16 ratio of 1; sustained, as the decode runs inside a long step
@@ -765,7 +773,7 @@ def main():
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "replicas x%d" % world},
             "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": "decode",
                          "peak_source": ("%s bf16 dense, sustained" % peak_kind) if bound == "tensor"
                          else "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"},
