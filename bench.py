@@ -69,6 +69,25 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(x: float, world: int, device="cpu") -> float:
+    """The slowest rank's time: every rank times its own replica of the work, and
+    the job takes as long as its slowest rank (all_reduce MAX over the process
+    group; nccl with a CUDA device, gloo with the CPU)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, units_per_rank_step: float, steps: int, max_ms: float) -> float:
+    """Whole-job throughput in units per second: the units all ranks processed
+    over the slowest rank's time (weak scaling: each rank a fixed share)."""
+    return world * units_per_rank_step * steps / (max_ms / 1e3)
+
+
 def read_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -605,19 +624,11 @@ def main():
             if it >= args.warmup:
                 e2e_ms.append(e0.elapsed_time(e1))
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    total_ms = max_over_ranks(sum(step_ms))
-    e2e_total = max_over_ranks(sum(e2e_ms)) if e2e_ms else float("nan")
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
+    e2e_total = max_over_ranks(sum(e2e_ms), world, dev) if e2e_ms else float("nan")
     pixels_step = len(wl["ms"]) * n_cs * h * w
-    value = world * pixels_step * args.steps / (total_ms / 1e3) / 1e6
-    e2e_value = world * pixels_step * args.steps / (e2e_total / 1e3) / 1e6
+    value = job_throughput(world, pixels_step, args.steps, total_ms) / 1e6
+    e2e_value = job_throughput(world, pixels_step, args.steps, e2e_total) / 1e6
 
     # roofline of the dominant kernel (the decode), from its own launch events
     dec_ms = sum(a.elapsed_time(b_) for a, b_ in dec_ev) / len(dec_ev)

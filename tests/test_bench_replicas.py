@@ -1,0 +1,54 @@
+"""The bench's multi-rank aggregation on CPU: two gloo ranks, each timing its
+own replica of the work, agree on the slowest rank's time, and the whole-job
+throughput counts both ranks' units over that time (weak scaling)."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port() -> int:
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, times, out):
+    import torch.distributed as dist
+
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        t = bench.max_over_ranks(times[rank], world, "cpu")
+        out[rank] = (t, bench.job_throughput(world, 1000.0, 4, t))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_take_the_slowest_time():
+    ctx = torch.multiprocessing.get_context("spawn")
+    manager = ctx.Manager()
+    out = manager.dict()
+    times = [12.5, 20.0]                      # ms of the two replicas
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, times, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        t, v = out[r]
+        assert t == 20.0
+        # 2 ranks x 1000 units x 4 steps in the slowest rank's 20 ms
+        assert v == pytest.approx(2 * 1000 * 4 / 0.020)
+
+
+def test_one_rank_needs_no_process_group():
+    import bench
+    assert bench.max_over_ranks(7.0, 1) == 7.0
+    assert bench.job_throughput(1, 10.0, 2, 5.0) == pytest.approx(4000.0)
