@@ -1,7 +1,6 @@
 // Plan construction on the device: the Gaussian measurement matrix Phi
-// (Sec. 3.1 and Sec. 4: "a Gaussian random matrix"), A = Phi Psi with Psi the
-// orthonormal 2-D DCT of a block, and the FISTA step constant
-// L = 1.0001 * lambda_max(Phi Phi^T) by FP64 power iteration.
+// (Sec. 3.1 and Sec. 4: "a Gaussian random matrix") and A = Phi Psi with Psi
+// the orthonormal 2-D DCT of a block (the step constant L is in lipschitz.cu).
 //
 // Phi must be identical bit for bit wherever it is generated, so every double
 // operation on its path is an explicit round-to-nearest intrinsic (never
@@ -165,63 +164,6 @@ __global__ void k_form_a(const float* __restrict__ phi, float* __restrict__ a,
     }
 }
 
-// K3a: Gram matrix G = Phi Phi^T in FP64, one CTA per row.
-__global__ void k_gram(const float* __restrict__ phi, double* __restrict__ g, int n, int m) {
-    extern __shared__ double rowi[];
-    const int i = blockIdx.x;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) rowi[k] = (double)phi[(size_t)i * n + k];
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-    for (int j = warp; j < m; j += nwarps) {
-        double acc = 0.0;
-        for (int k = lane; k < n; k += 32) acc += rowi[k] * (double)phi[(size_t)j * n + k];
-        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-        if (lane == 0) g[(size_t)i * m + j] = acc;
-    }
-}
-
-__device__ double block_sum(double v, double* red) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    __syncthreads();
-    if (lane == 0) red[warp] = v;
-    __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < nwarps; ++w) tot += red[w];
-    return tot;
-}
-
-// K3b: power iteration on G in one CTA: v0 = 1/sqrt(M); v <- G v / ||G v||,
-// 1000 times; lambda = v^T G v.
-__global__ void k_power(const double* __restrict__ g, int m, int iters, double* result) {
-    extern __shared__ double sh[];
-    double* v = sh;          // [M]
-    double* w = v + m;       // [M]
-    double* red = w + m;     // [32]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = 1.0 / sqrt((double)m);
-    __syncthreads();
-    for (int it = 0; it <= iters; ++it) {
-        for (int i = warp; i < m; i += nwarps) {
-            double acc = 0.0;
-            for (int j = lane; j < m; j += 32) acc += g[(size_t)i * m + j] * v[j];
-            for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-            if (lane == 0) w[i] = acc;
-        }
-        __syncthreads();
-        if (it == iters) break;  // w = G v for the Rayleigh quotient
-        double part = 0.0;
-        for (int i = threadIdx.x; i < m; i += blockDim.x) part += w[i] * w[i];
-        const double inv = 1.0 / sqrt(block_sum(part, red));
-        for (int i = threadIdx.x; i < m; i += blockDim.x) v[i] = w[i] * inv;
-        __syncthreads();
-    }
-    double part = 0.0;
-    for (int i = threadIdx.x; i < m; i += blockDim.x) part += v[i] * w[i];
-    const double lam = block_sum(part, red);
-    if (threadIdx.x == 0) *result = lam;
-}
-
 }  // namespace
 
 cudaError_t launch_phi(float* phi, int n, int m, uint64_t seed, cudaStream_t s) {
@@ -243,26 +185,6 @@ cudaError_t launch_form_a(const float* phi, float* a, float* dct, int n, int m, 
         if (e != cudaSuccess) return e;
     }
     k_form_a<<<m, 256, smem, s>>>(phi, a, dct, n, b);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_lambda_max(const float* phi, int n, int m, double* gram, double* result,
-                              cudaStream_t s) {
-    size_t smem = (size_t)n * sizeof(double);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_gram, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_gram<<<m, 256, smem, s>>>(phi, gram, n, m);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    smem = (2 * (size_t)m + 32) * sizeof(double);
-    if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_power, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    k_power<<<1, 1024, smem, s>>>(gram, m, 1000, result);
     return cudaGetLastError();
 }
 
