@@ -186,17 +186,19 @@ int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float m
                      uint8_t* frames_u8_dev, cs_stream_t stream);
 
 /* cs_autotune: pick the decode's launch shape for the plan's (N, M) by timing
- * every candidate on the device: the on-chip tensor-core kernel where the
+ * the candidates on the device: the on-chip tensor-core kernel where the
  * shape has one (16 x 16 and 32 x 32 blocks, M <= 128), the streaming
  * tensor-core kernel where it has one (8 x 8, 16 x 16 and 32 x 32 blocks,
  * M <= 512), and the plain FP32 kernel at 64,
  * 128, 256, 512 and 1024 threads per CTA with 1, 2, 4, 8 or 16 (up to 512
  * threads) measured blocks per CTA (the blocks of a CTA share each load of A;
- * shapes whose shared memory exceeds 200 KB are skipped).  Each runs a synthetic call (random
+ * shapes whose shared memory exceeds 200 KB are skipped; after its default shape
+ * the plain sweep stops when that is more than 4x slower than a tensor-core
+ * kernel of the shape).  Each runs a synthetic call (random
  * measurements, zero key, up to 19456 blocks, 8 iterations, FP32); the
  * fastest is recorded in ctx for this (N, M) and used from then on by FP32
  * decodes whose engine is CS_ENGINE_AUTO (an explicit engine still wins;
- * mixed precision always takes the tensor-core kernel).  Synchronises the
+ * mixed precision always takes a tensor-core kernel).  Synchronises the
  * device: call it before serving or before capturing decodes into a CUDA
  * graph.  Outputs (each may be NULL): the chosen engine (CS_ENGINE_TC,
  * CS_ENGINE_TC_STREAM or CS_ENGINE_PLAIN), the plain kernel's threads and

@@ -3,10 +3,12 @@
 // The recovery of a plan's blocks can run on the persistent tensor-core kernel
 // with the iterates on chip (where the shape has one), on the streaming
 // tensor-core kernel (where the shape has one) or on the plain kernel with 64 to 1024 threads
-// and 1, 2, 4, 8 or 16 measured blocks per CTA.  cs_autotune times every candidate the plan's shape
-// admits on a synthetic call of the same N and M (random measurements, a zero
-// key, a few thousand blocks, a short fixed iteration count) and records the
-// fastest in the context; FP32 decodes with engine CS_ENGINE_AUTO then use it.
+// and 1, 2, 4, 8 or 16 measured blocks per CTA.  cs_autotune times the candidates the plan's
+// shape admits on a synthetic call of the same N and M (random measurements, a
+// zero key, a few thousand blocks, a short fixed iteration count) and records
+// the fastest in the context; FP32 decodes with engine CS_ENGINE_AUTO then use
+// it.  The plain kernel's sweep stops after its default shape when that is more
+// than 4x slower than a tensor-core kernel of the shape.
 // Timing synchronises the device, so it runs once per (N, M), before serving
 // or before a decode is captured into a CUDA graph.
 #include <algorithm>
@@ -60,12 +62,20 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
     gs.n_gops = 1;
     gs.n_cs = 1;
 
+    // tensor-core kernels first, then the plain kernel's default shape, then the rest
+    // of its sweep; the rest is skipped when the default is over 4x slower than a
+    // tensor-core kernel, a wider margin than the spread between the plain shapes
     std::vector<Candidate> cands;
     if (tc_supported(plan, CS_FP32)) cands.push_back({CS_ENGINE_TC, 0, 0});
     if (tcs_supported(plan)) cands.push_back({CS_ENGINE_TC_STREAM, 0, 0});
+    const size_t n_tc = cands.size();
+    int t_def = 0, r_def = 0;
+    plain_default_shape(n, m, &t_def, &r_def);
+    cands.push_back({CS_ENGINE_PLAIN, t_def, r_def});
     for (int t : {64, 128, 256, 512, 1024})
         for (int r : {1, 2, 4, 8, 16})
-            if (plain_shape_valid(t, r, n, m)) cands.push_back({CS_ENGINE_PLAIN, t, r});
+            if (plain_shape_valid(t, r, n, m) && !(t == t_def && r == r_def))
+                cands.push_back({CS_ENGINE_PLAIN, t, r});
 
     std::vector<float> y_host((size_t)rows * m);
     fill_uniform(y_host, plan->seed);
@@ -86,8 +96,10 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
 
     const int iters = 8;
     Candidate best{0, 0, 0};
-    float best_ms = -1.f;
+    float best_ms = -1.f, plain_default_ms = 0.f;
     for (size_t i = 0; e == cudaSuccess && i < cands.size(); ++i) {
+        if (i == n_tc + 1 && n_tc > 0 && best.engine != CS_ENGINE_PLAIN && plain_default_ms > 4.f * best_ms)
+            break;
         DecodeArgs d;
         d.plan = plan;
         d.gs = gs;
@@ -114,6 +126,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
         if (e == cudaSuccess) e = cudaEventSynchronize(e1);
         float ms = 0.f;
         if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e == cudaSuccess && i == n_tc) plain_default_ms = ms;
         if (e == cudaSuccess && (best_ms < 0.f || ms < best_ms)) {
             best_ms = ms;
             best = cands[i];

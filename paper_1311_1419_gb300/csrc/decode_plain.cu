@@ -237,6 +237,14 @@ static int plain_blocks_default(int t, int n, int m) {
     return 1;
 }
 
+void plain_default_shape(int n, int m, int* threads, int* blocks_per_cta) {
+    int t = plain_threads_default(n);
+    const int nr = plain_blocks_default(t, n, m);
+    if (nr == 16 && t > 512) t = 512;
+    *threads = t;
+    *blocks_per_cta = nr;
+}
+
 cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s) {
     const GopShape& gs = d.gs;
     const long long rows = (long long)gs.n_cs * gs.nblk;

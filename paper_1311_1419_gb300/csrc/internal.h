@@ -131,6 +131,8 @@ cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s);
 bool plain_threads_valid(int threads, int n);
 bool plain_shape_valid(int threads, int blocks_per_cta, int n, int m);
 int plain_threads_default(int n);
+// the plain kernel's launch shape for an (N, M) the autotuner has not timed
+void plain_default_shape(int n, int m, int* threads, int* blocks_per_cta);
 bool tc_supported(const cs_plan* plan, int precision);
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
 cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
