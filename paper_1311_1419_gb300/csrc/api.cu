@@ -171,9 +171,12 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) ctx->streams.push_back(s);
     }
-    for (int i = 0; e == cudaSuccess && i < 4; ++i) {
+    int prio_least = 0, prio_greatest = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+    for (int i = 0; e == cudaSuccess && i < kForkStreams; ++i) {
         cudaStream_t s;
-        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking,
+                                         i == kForkTc8Head ? prio_greatest : prio_least);
         if (e == cudaSuccess) ctx->fork_streams.push_back(s);
     }
     if (e != cudaSuccess) {
@@ -369,9 +372,9 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
     cudaError_t e = cudaSuccess;
     cudaStream_t s = (cudaStream_t)stream;
     if (!tcs_jobs.empty() && !tc_jobs.empty()) {
-        // the streaming kernel's launch on the context's last fork stream, joined
-        // back on s: its CTAs take SMs as the on-chip launches' tails drain
-        cudaStream_t fs = ctx->fork_streams.back();
+        // the streaming kernel's launch on its own fork stream, joined back on s:
+        // its CTAs take SMs as the on-chip launches' tails drain
+        cudaStream_t fs = ctx->fork_streams[kForkTcs];
         cudaEvent_t fork = nullptr, join = nullptr;
         e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);

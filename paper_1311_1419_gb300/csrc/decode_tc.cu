@@ -854,8 +854,7 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
         if (e == cudaSuccess) e = cudaEventRecord(fork, s);
         std::vector<cudaEvent_t> joins;
         for (size_t i = 0; e == cudaSuccess && i < launches.size(); ++i) {
-            // (the context's last fork stream is kept for the streaming kernel's launch)
-            cudaStream_t fs = i == 0 ? s : ctx->fork_streams[(i - 1) % (ctx->fork_streams.size() - 1)];
+            cudaStream_t fs = i == 0 ? s : ctx->fork_streams[(i - 1) % kForkTcGroups];
             if (i > 0) e = cudaStreamWaitEvent(fs, fork, 0);
             if (e == cudaSuccess) e = launch_group(launches[i].jobs, launches[i].n, launches[i].bf,
                                                    launches[i].mx, fs);

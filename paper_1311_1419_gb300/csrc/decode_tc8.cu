@@ -784,7 +784,8 @@ static void fill_job8(const DecodeArgs& d, int tile_begin, Tc8Job* J) {
     J->out_u8 = d.out_u8;
     J->dct = p->dct;
     J->gs = d.gs;
-    J->rows = (long long)d.gs.n_cs * d.gs.nblk;
+    // this launch recovers blocks [0, rows) of the call (a tail may go to the streaming kernel)
+    J->rows = d.row_end < 0 ? (long long)d.gs.n_cs * d.gs.nblk : d.row_end;
     J->tile_begin = tile_begin;
     J->m16 = m16_of8(p->m);
     J->iters = d.iters;
@@ -795,6 +796,26 @@ static void fill_job8(const DecodeArgs& d, int tile_begin, Tc8Job* J) {
     J->su = ldexpf(1.f, -p->tc_ea);
     J->sg = ldexpf(1.f, -(p->tc_ea + p->tc_ep));
     J->sp = ldexpf(1.f, p->tc_ep);
+}
+
+// Clusters of the kernel that fit the device at once (each tile's 8 CTAs wait
+// on one another, so only co-resident clusters may run).
+static cudaError_t co_resident_clusters(bool bf, int* clusters) {
+    const void* fn = bf ? (const void*)k_fista_tc8<true> : (const void*)k_fista_tc8<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCl, 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = kSmemBytes;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = kCl;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, fn, &cfg);
 }
 
 // One cluster launch for up to kMaxJobs8 jobs of one operand type.
@@ -821,21 +842,9 @@ static cudaError_t launch_group8(const DecodeArgs* const* jobs, int n_jobs, bool
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return e;
     if (fa.numRegs < kLaunchRegs || fa.maxThreadsPerBlock < kThreads) return cudaErrorInvalidConfiguration;
-    // as many clusters as are co-resident (each tile's 8 CTAs wait on one another),
-    // and no more than the scratch holds
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(kCl, 1, 1);
-    cfg.blockDim = dim3(kThreads, 1, 1);
-    cfg.dynamicSmemBytes = kSmemBytes;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = kCl;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
+    // as many clusters as are co-resident, and no more than the scratch holds
     int max_clusters = 0;
-    e = cudaOccupancyMaxActiveClusters(&max_clusters, fn, &cfg);
+    e = co_resident_clusters(bf, &max_clusters);
     if (e != cudaSuccess) return e;
     if (max_clusters < 1) return cudaErrorInvalidConfiguration;
     int clusters = std::min(max_clusters, ctx->sm_count / kCl + 1);
@@ -851,23 +860,84 @@ static double job_cost8(const DecodeArgs& d) {
     return (double)((long long)d.gs.n_cs * d.gs.nblk) * (double)d.iters * (double)m16_of8(d.plan->m);
 }
 
+// The SMs that whole clusters leave idle (GPCs whose SM count is not a multiple
+// of 8) take a tail of each large job on the streaming kernel, two CTAs each.
+// A tile there lasts about kTcsTileRatio times a cluster's tile, so the tail is
+// r rounds of 2 x idle tiles with r (2 x idle) + clusters x r x kTcsTileRatio <=
+// the job's tiles: both kernels then finish at about the same time.  The split
+// depends on the job alone, so a job decodes to the same bits in any batch.
+constexpr int kTcsTileRatio = 30;
+
+static long long tail_rows(const DecodeArgs& d, int clusters, int idle_ctas) {
+    if (idle_ctas <= 0 || !tcs_supported(d.plan)) return 0;
+    const long long total = (long long)d.gs.n_cs * d.gs.nblk;
+    const long long tiles = (total + kTile - 1) / kTile;
+    const long long rounds = tiles / ((long long)clusters * kTcsTileRatio + idle_ctas);
+    if (rounds <= 0) return 0;
+    const long long tail_tiles = rounds * idle_ctas;
+    return total - (tiles - tail_tiles) * kTile;
+}
+
 cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
-    std::vector<const DecodeArgs*> groups[2];
+    std::vector<DecodeArgs> head[2], tail[2];
     for (int i = 0; i < n_jobs; ++i) {
         if ((long long)jobs[i].gs.n_cs * jobs[i].gs.nblk == 0) continue;
         const bool bf = jobs[i].precision == CS_BF16 || jobs[i].precision == CS_BF16X2;
-        groups[bf ? 1 : 0].push_back(&jobs[i]);
+        head[bf ? 1 : 0].push_back(jobs[i]);
     }
+    cs_ctx* ctx = n_jobs > 0 ? jobs[0].plan->ctx : nullptr;
     for (int bf = 0; bf < 2; ++bf) {
-        std::vector<const DecodeArgs*>& g = groups[bf];
+        if (head[bf].empty()) continue;
+        int clusters = 0;
+        cudaError_t e = co_resident_clusters(bf == 1, &clusters);
+        if (e != cudaSuccess) return e;
+        const int idle_ctas = tcs_ctas_per_sm() * (ctx->sm_count - clusters * kCl);
+        for (DecodeArgs& d : head[bf]) {
+            const long long t = tail_rows(d, clusters, idle_ctas);
+            if (t <= 0) continue;
+            const long long total = (long long)d.gs.n_cs * d.gs.nblk;
+            DecodeArgs dt = d;
+            dt.row_begin = total - t;
+            dt.row_end = total;
+            d.row_end = total - t;
+            tail[bf].push_back(dt);
+        }
+        std::vector<const DecodeArgs*> g;
+        for (DecodeArgs& d : head[bf]) g.push_back(&d);
         std::stable_sort(g.begin(), g.end(), [](const DecodeArgs* a, const DecodeArgs* b) {
             return job_cost8(*a) > job_cost8(*b);
         });
-        for (size_t i = 0; i < g.size(); i += kMaxJobs8) {
-            const int n = (int)std::min(g.size() - i, (size_t)kMaxJobs8);
-            cudaError_t e = launch_group8(g.data() + i, n, bf == 1, s);
-            if (e != cudaSuccess) return e;
+        // with tails: the clusters on the context's highest-priority stream, so that
+        // the dispatcher places them before the tails' CTAs, and the tails beside
+        // them; both forked from s and joined back on it
+        cudaStream_t hs = s, fs = nullptr;
+        cudaEvent_t fork = nullptr, join_h = nullptr, join_t = nullptr;
+        if (!tail[bf].empty()) {
+            hs = ctx->fork_streams[kForkTc8Head];
+            fs = ctx->fork_streams[kForkTc8Tail];
+            e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_h, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_t, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventRecord(fork, s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(hs, fork, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(fs, fork, 0);
         }
+        for (size_t i = 0; e == cudaSuccess && i < g.size(); i += kMaxJobs8) {
+            const int n = (int)std::min(g.size() - i, (size_t)kMaxJobs8);
+            e = launch_group8(g.data() + i, n, bf == 1, hs);
+        }
+        if (fork) {
+            if (e == cudaSuccess)
+                e = launch_decode_tcs_batch(tail[bf].data(), (int)tail[bf].size(), fs, idle_ctas);
+            if (e == cudaSuccess) e = cudaEventRecord(join_h, hs);
+            if (e == cudaSuccess) e = cudaEventRecord(join_t, fs);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_h, 0);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(s, join_t, 0);
+            cudaEventDestroy(fork);
+            if (join_h) cudaEventDestroy(join_h);
+            if (join_t) cudaEventDestroy(join_t);
+        }
+        if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }

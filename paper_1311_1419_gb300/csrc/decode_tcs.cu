@@ -90,7 +90,8 @@ struct TcsJob {
     uint8_t* out_u8;
     const float* dct;       // [B][B]
     GopShape gs;
-    long long rows;         // measured blocks
+    long long row0;         // first measured block of this launch's share of the call
+    long long rows;         // end (exclusive) of that share
     int tile_begin;
     int n, m16;
     int iters;
@@ -517,7 +518,7 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
         if (cg == 0) ms->colmax[r] = 0u;
         for (int i = et; i < bsz * bsz; i += kEpiThreads) c_s[i] = J.dct[i];
         cta_sync_s();   // B
-        const long long tile_row0 = (long long)(tile - J.tile_begin) * kTile;
+        const long long tile_row0 = J.row0 + (long long)(tile - J.tile_begin) * kTile;
         uint8_t* p_hi = scr + kScrP;
         uint8_t* p_lo = p_hi + (size_t)p_slices(m16) * kTBytes;
         float4* y4 = reinterpret_cast<float4*>(scr + kScrY);
@@ -736,7 +737,9 @@ static void fill_job_s(const DecodeArgs& d, int tile_begin, TcsJob* J) {
     J->out_u8 = d.out_u8;
     J->dct = p->dct;
     J->gs = d.gs;
-    J->rows = (long long)d.gs.n_cs * d.gs.nblk;
+    const long long total = (long long)d.gs.n_cs * d.gs.nblk;
+    J->row0 = d.row_begin;
+    J->rows = d.row_end < 0 ? total : d.row_end;
     J->tile_begin = tile_begin;
     J->n = p->n;
     J->m16 = m16;
@@ -751,15 +754,21 @@ static void fill_job_s(const DecodeArgs& d, int tile_begin, TcsJob* J) {
     J->sp = ldexpf(1.f, p->tc_ep);
 }
 
+static long long job_rows_s(const DecodeArgs& d) {
+    const long long total = (long long)d.gs.n_cs * d.gs.nblk;
+    return (d.row_end < 0 ? total : d.row_end) - d.row_begin;
+}
+
 static double job_cost_s(const DecodeArgs& d) {
     const double m16 = (double)m16_of_s(d.plan->m), n = (double)d.plan->n;
-    const double blocks = (double)((long long)d.gs.n_cs * d.gs.nblk);
+    const double blocks = (double)job_rows_s(d);
     return blocks * (double)d.iters * (m16 > kChunk ? 2.0 * kChunk : m16) * n;
 }
 
 // One launch for up to kMaxJobsS jobs of one operand type (fp16 or bf16), any
 // (N, M) this kernel supports; jobs heaviest first.
-static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, bool bf, cudaStream_t s) {
+static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, bool bf, cudaStream_t s,
+                                  int max_ctas) {
     cs_ctx* ctx = jobs[0]->plan->ctx;
     if (!ctx->tcs_scratch) return cudaErrorInvalidValue;
     TcsLaunch L{};
@@ -774,11 +783,12 @@ static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, boo
     int tiles = 0;
     for (int i = 0; i < n_jobs; ++i) {
         fill_job_s(*jobs[i], tiles, &L.jobs[i]);
-        tiles += (int)((L.jobs[i].rows + kTile - 1) / kTile);
+        tiles += (int)((L.jobs[i].rows - L.jobs[i].row0 + kTile - 1) / kTile);
     }
     L.n_jobs = n_jobs;
     L.n_tiles = tiles;
-    const int grid = std::min(tiles, kCtasPerSm * ctx->sm_count);
+    int grid = std::min(tiles, kCtasPerSm * ctx->sm_count);
+    if (max_ctas > 0) grid = std::min(grid, max_ctas);
     const void* fn = bf ? (const void*)k_fista_tcs<true> : (const void*)k_fista_tcs<false>;
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
@@ -789,10 +799,12 @@ static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, boo
     return cudaGetLastError();
 }
 
-cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
+int tcs_ctas_per_sm() { return kCtasPerSm; }
+
+cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s, int max_ctas) {
     std::vector<const DecodeArgs*> groups[2];
     for (int i = 0; i < n_jobs; ++i) {
-        if ((long long)jobs[i].gs.n_cs * jobs[i].gs.nblk == 0) continue;
+        if (job_rows_s(jobs[i]) <= 0) continue;
         const bool bf = jobs[i].precision == CS_BF16 || jobs[i].precision == CS_BF16X2;
         groups[bf ? 1 : 0].push_back(&jobs[i]);
     }
@@ -803,7 +815,7 @@ cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStre
         });
         for (size_t i = 0; i < g.size(); i += kMaxJobsS) {
             const int nj = (int)std::min(g.size() - i, (size_t)kMaxJobsS);
-            cudaError_t e = launch_group_s(g.data() + i, nj, bf == 1, s);
+            cudaError_t e = launch_group_s(g.data() + i, nj, bf == 1, s, max_ctas);
             if (e != cudaSuccess) return e;
         }
     }

@@ -126,6 +126,10 @@ struct DecodeArgs {
     const float* beta;
     int plain_threads;        // threads per CTA of the plain kernel; 0 = default rule
     int plain_blocks;         // measured blocks per CTA of the plain kernel; 0 = 1
+    // measured blocks [row_begin, row_end) of the call this launch recovers (row_end
+    // < 0: to the last); the cluster kernel hands a tail range to the streaming one
+    long long row_begin = 0;
+    long long row_end = -1;
 };
 cudaError_t launch_decode_plain(const DecodeArgs& d, cudaStream_t s);
 bool plain_threads_valid(int threads, int n);
@@ -147,7 +151,14 @@ size_t tcs_scratch_bytes(int sm_count);
 cudaError_t launch_tcs_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s);
 bool tcs_supported(const cs_plan* plan);
 cudaError_t launch_decode_tcs(const DecodeArgs& d, cudaStream_t s);
-cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
+// max_ctas > 0 caps the launch's grid (the SMs the cluster kernel leaves idle)
+cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s,
+                                    int max_ctas = 0);
+int tcs_ctas_per_sm();
+// fork streams of a context: 0 .. 2 the on-chip kernel's extra groups, 3 the batched
+// streaming launch, 4 the streaming tail of cluster-kernel jobs, 5 (the device's
+// highest stream priority) the cluster kernel when it has tails beside it
+constexpr int kForkTcGroups = 3, kForkTcs = 3, kForkTc8Tail = 4, kForkTc8Head = 5, kForkStreams = 6;
 
 // serving (serving.cu)
 void serving_destroy(cs_ctx* ctx);

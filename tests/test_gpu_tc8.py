@@ -112,3 +112,64 @@ def test_tc8_in_a_batch_equals_alone(B, ctx):
     finally:
         for x in prepared:
             B.cs_plan_destroy(x[0])
+
+
+def test_tc8_large_job_tail_on_idle_sms(B, ctx):
+    """The 720p workload (96 frames, G = 16: 82800 blocks, 647 tiles; M = 102, K = 300):
+    whole clusters leave SMs idle, so a tail of the job runs on the streaming kernel
+    there.  Sampled blocks of the head and of the tail match the oracle, and the
+    tail is bit for bit the streaming kernel's own decode of those blocks."""
+    h, w, gop, n_gops, m, iters, seed = 720, 1280, 16, 6, 102, 300, 31
+    b = 32
+    frames = scenes.surveillance_video(gop * n_gops, h, w, seed=seed)
+    plan = B.cs_make_phi(ctx, b * b, m, seed)
+    nbr, nbc = -(-h // b), -(-w // b)
+    nblk = nbr * nbc
+    n_cs = n_gops * (gop - 1)
+    try:
+        outs = {}
+        for name, eng in (("tc", B.CS_ENGINE_TC), ("tcs", B.CS_ENGINE_TC_STREAM)):
+            p = B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops, engine=eng)
+            y = torch.empty((n_cs, nblk, m), dtype=torch.float32, device="cuda")
+            B.cs_encode_gop(plan, p, torch.from_numpy(frames).cuda(), y, torch.cuda.current_stream())
+            keys = torch.from_numpy(np.ascontiguousarray(frames[::gop])).cuda()
+            out = torch.full((n_cs, h, w), float("nan"), dtype=torch.float32, device="cuda")
+            B.cs_decode_gop(plan, p, keys, y, out, None, torch.cuda.current_stream())
+            B.cs_ctx_status(ctx)
+            outs[name] = out.cpu().numpy()
+    finally:
+        B.cs_plan_destroy(plan)
+    total = n_cs * nblk
+    tiles = -(-total // 128)
+    # the tail is a whole number of rounds of two CTAs per idle SM: with 15 of 19
+    # possible clusters resident that is 64 tiles; the last 32 tiles are in it on
+    # any part that leaves at least 16 SMs idle
+    first_tail = total - (32 * 128 - (tiles * 128 - total))
+
+    def block(o, r):
+        c, blk = divmod(int(r), nblk)
+        bi, bj = divmod(blk, nbc)
+        return o[c, bi * b:min(h, bi * b + b), bj * b:min(w, bj * b + b)]
+    for r in range(first_tail, total, 97):
+        assert np.array_equal(block(outs["tc"], r).view(np.uint32), block(outs["tcs"], r).view(np.uint32)), r
+    # and the head did not: the cluster kernel's arithmetic differs in the last bits
+    assert not all(np.array_equal(block(outs["tc"], r), block(outs["tcs"], r)) for r in range(0, 6400, 101))
+    oplan = O.Plan(b * b, m, seed)
+    yo = O.encode(oplan, frames, gop)
+    rng = np.random.default_rng(seed)
+    rows = np.concatenate([rng.choice(first_tail, 48, replace=False),
+                           first_tail + rng.choice(total - first_tail, 48, replace=False)])
+    r_hat = O.decode_blocks(oplan, yo.reshape(-1, m)[rows], iters)
+    got, want = [], []
+    for i, r in enumerate(rows):
+        c, blk = divmod(int(r), nblk)
+        bi, bj = divmod(blk, nbc)
+        hh, ww = min(b, h - bi * b), min(b, w - bj * b)
+        key = frames[(c // (gop - 1)) * gop].astype(np.float64)
+        sl = (slice(bi * b, bi * b + hh), slice(bj * b, bj * b + ww))
+        want.append((key[sl] + r_hat[i].reshape(b, b)[:hh, :ww]).ravel())
+        got.append(outs["tc"][c][sl].astype(np.float64).ravel())
+    got, want = np.concatenate(got), np.concatenate(want)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    print("720p M=102 head + streaming tail, sampled blocks rel-l2 %.3g" % err)
+    assert err <= 1e-4
