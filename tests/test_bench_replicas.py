@@ -52,3 +52,22 @@ def test_one_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(7.0, 1) == 7.0
     assert bench.job_throughput(1, 10.0, 2, 5.0) == pytest.approx(4000.0)
+
+
+def test_mixed_launch_count():
+    """The mixed bench's launch count: one launch per group of up to 48 jobs of each
+    tensor-core kernel (16x16 on chip by shared-memory layout, 32x32 cluster,
+    streaming) and one per plain-kernel job."""
+    import bench
+
+    class P:
+        def __init__(self, block, m):
+            self.block, self.m = block, m
+
+    def job(b, m, tc=True):
+        return {"p": P(b, m), "tc": tc}
+    jobs = ([job(16, 40)] * 50 + [job(16, 128)] + [job(32, 102)] * 3 + [job(32, 300)] * 2 +
+            [job(8, 16)] + [job(16, 40, tc=False)] * 2)
+    # on chip: 50 jobs of M16 <= 96 (2 launches) + 1 of M16 = 128; cluster: 1;
+    # streaming: 3 (32x32 M > 128, 8x8) in 1; plain: 2
+    assert bench.mixed_launches(jobs) == 2 + 1 + 1 + 1 + 2
