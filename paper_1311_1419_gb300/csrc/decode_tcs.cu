@@ -13,19 +13,18 @@
 //
 // Neither A (up to 2 MB as fp16 hi + lo at N = 1024, M = 512) nor the tile's
 // iterates (Z and s^{k-1}: 1 MB) fit on chip, so the operands stream: a copy
-// warp feeds a four-slot ring of 32-wide K slices (64-byte-swizzled operands,
-// 48 KB per slot, so that three slices are in flight while one is consumed)
-// through the bulk-copy engine (the tile operand Z or P from this CTA's global
-// scratch, the A slice from one of the plan's two swizzled images of A, which
-// stay in L2 and make every slice one contiguous copy), one thread issues the MMAs, and
+// warp feeds a two-slot ring of 32-wide K slices (64-byte-swizzled operands,
+// 48 KB per slot) through the bulk-copy engine (the tile operand Z or P from
+// this CTA's global scratch, the A slice from one of the plan's two swizzled
+// images of A, which stay in L2 and make every slice one contiguous copy), one
+// thread issues the MMAs into a 256-column accumulator in tensor memory, and
 // two CTAs share an SM (half its shared and tensor memory each), so that one
 // tile's epilogue, bound by the iterates' global-memory traffic, overlaps the
-// other tile's MMAs.  The epilogue (8 warps, TMEM lane quarter = warp % 4,
-// column group = warp / 4) forms P = U - y (y staged once per tile in the
-// scratch, laid out for coalesced reads) into the scratch's P image and runs
-// the gradient / soft-threshold / momentum step,
-// reading and writing s^{k-1} (fp32) and Z (fp16 hi + lo, the next GEMM1's
-// operand image) in the scratch.  lambda_b needs max |A^T y_b| over all N
+// other tile's MMAs.  The epilogue (8 warps: TMEM lane quarter = warp % 4, two
+// column groups) forms P = U - y (y staged once per tile in the scratch, laid
+// out for coalesced reads) into the scratch's P image and runs the gradient /
+// soft-threshold / momentum step, reading and writing s^{k-1} (fp32) and Z
+// (fp16 hi + lo, the next GEMM1's operand image) in the scratch.  lambda_b needs max |A^T y_b| over all N
 // coefficients before the first step, so GEMM2 runs once more at k = 0 for it.
 // Mixed precision: a split product uses three MMAs (hi.hi + lo.hi + hi.lo),
 // a bulk one hi.hi only.  Every mbarrier wait is bounded and reports through
