@@ -190,3 +190,19 @@ def test_tcs_full_720p_sampled(B, ctx, precision, tol):
     err = np.linalg.norm(got - want) / np.linalg.norm(want)
     print("720p M=512 precision %d: sampled blocks rel-l2 %.3g" % (precision, err))
     assert err <= tol
+
+
+@pytest.mark.parametrize("h,w,b,m", [(1, 1, 32, 300), (3, 5, 8, 20), (17, 9, 16, 150)])
+def test_tcs_tiny_frames(B, ctx, h, w, b, m):
+    # frames smaller than one block: every block is mostly padding, one row per tile
+    gop, iters = 3, 25
+    frames, got, u8 = _run(B, ctx, h, w, gop, b, m, iters, seed=14)
+    ref = _oracle(frames, b, gop, 1, m, iters, 14)
+    err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert err <= 1e-4, err
+    assert np.array_equal(u8, np.clip(np.rint(got), 0, 255).astype(np.uint8))
+
+
+def test_batch_of_no_jobs_is_a_no_op(B, ctx):
+    B.cs_decode_batch(ctx, [], [], [], [], None, None, torch.cuda.current_stream())
+    B.cs_ctx_status(ctx)
