@@ -535,11 +535,11 @@ def main():
             else:
                 groups.add(("tc8",))
                 # a large 32x32 job also launches its streaming tail on the SMs whole
-                # clusters leave idle (the library's rule: tiles // (clusters x 30 +
-                # 2 x idle SMs) rounds; 15 clusters of 8 are co-resident on this part)
+                # clusters leave idle (the library's rule: a tail once the job has more
+                # tiles than clusters x 30; 15 clusters of 8 are co-resident on this part)
                 tiles = -(-(n_cs * nblk) // 128)
                 idle = 2 * (torch.cuda.get_device_properties(dev).multi_processor_count - 8 * 15)
-                if idle > 0 and tiles // (15 * 30 + idle) > 0:
+                if idle > 0 and tiles > 15 * 30:
                     groups.add(("tc8 tail",))
         return len(groups) + plain
     launches_per_step = 2 * len(wl["ms"]) + decode_launches()

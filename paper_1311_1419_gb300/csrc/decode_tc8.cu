@@ -864,17 +864,21 @@ static double job_cost8(const DecodeArgs& d) {
 // of 8) take a tail of each large job on the streaming kernel, two CTAs each.
 // A tile there lasts about kTcsTileRatio times a cluster's tile, so the tail is
 // r rounds of 2 x idle tiles with r (2 x idle) + clusters x r x kTcsTileRatio <=
-// the job's tiles: both kernels then finish at about the same time.  The split
-// depends on the job alone, so a job decodes to the same bits in any batch.
+// the job's tiles, or, when not one whole round fits, a partial round of the
+// tiles beyond clusters x kTcsTileRatio: both kernels then finish at about the
+// same time.  The split depends on the job alone, so a job decodes to the same
+// bits in any batch.
 constexpr int kTcsTileRatio = 30;
 
 static long long tail_rows(const DecodeArgs& d, int clusters, int idle_ctas) {
     if (idle_ctas <= 0 || !tcs_supported(d.plan)) return 0;
     const long long total = (long long)d.gs.n_cs * d.gs.nblk;
     const long long tiles = (total + kTile - 1) / kTile;
-    const long long rounds = tiles / ((long long)clusters * kTcsTileRatio + idle_ctas);
-    if (rounds <= 0) return 0;
-    const long long tail_tiles = rounds * idle_ctas;
+    const long long one_round = (long long)clusters * kTcsTileRatio;
+    const long long rounds = tiles / (one_round + idle_ctas);
+    const long long tail_tiles =
+        rounds > 0 ? rounds * idle_ctas : std::min<long long>(idle_ctas, tiles - one_round);
+    if (tail_tiles <= 0) return 0;
     return total - (tiles - tail_tiles) * kTile;
 }
 
