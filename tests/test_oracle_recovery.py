@@ -199,3 +199,49 @@ def test_psnr_closed_form_and_uint8_rounding():
     assert O.psnr(ref, ref) == math.inf
     x = np.array([-3.0, 0.5, 1.5, 2.5, 254.5, 255.4, 300.0])
     assert list(O.to_uint8(x)) == [0, 0, 2, 2, 254, 255, 255]
+
+
+def test_block_lambda_by_explicit_loops():
+    """lambda_b = lambda_rel * max_j |sum_i A_ij y_bi| on a hand-built 3 x 4 A.
+    The second row's largest entry of A^T y is negative, so a maximum taken
+    without the absolute value gives a different number."""
+    a = np.array([[1.0, -2.0, 0.5, 3.0],
+                  [0.0, 4.0, -1.0, 1.0],
+                  [2.0, 1.0, 1.0, -0.5]])
+    y = np.array([[1.0, 1.0, 1.0],
+                  [0.0, -3.0, 0.5]])
+    want = []
+    for b in range(y.shape[0]):
+        best = 0.0
+        for j in range(a.shape[1]):
+            acc = 0.0
+            for i in range(a.shape[0]):
+                acc += a[i, j] * y[b, i]
+            best = max(best, abs(acc))
+        want.append(0.01 * best)
+    # A^T y_0 = (3, 3, 0.5, 3.5); A^T y_1 = (1, -11.5, 3.5, -3.25)
+    assert want == pytest.approx([0.035, 0.115], abs=1e-15)
+    assert np.array_equal(O.block_lambda(a, y, 0.01), np.array(want))
+
+
+def test_lambda_at_the_lasso_threshold_gives_the_zero_solution():
+    """For the LASSO, s = 0 is optimal exactly when lambda >= ||A^T y||_inf (the
+    subgradient condition at 0).  So lambda_rel = 1 must decode every block to
+    zero, and lambda_rel just below 1 must leave the coefficient of largest
+    |A^T y| nonzero: a norm other than the max-abs one fails one of the two."""
+    plan = O.Plan(64, 16, seed=12)
+    frames = scenes.surveillance_video(2, 24, 24, seed=5)
+    y = O.encode(plan, frames, gop=2)[0]                  # 9 blocks of 8 x 8
+    corr = y @ plan.a                                     # A^T y per block
+    assert np.any(np.argmax(corr, axis=1) != np.argmax(np.abs(corr), axis=1))
+    s_at = O.fista(plan.a, y, plan.lipschitz, O.block_lambda(plan.a, y, 1.0), 200)
+    assert np.array_equal(s_at, np.zeros_like(s_at))
+    assert np.array_equal(O.decode_blocks(plan, y, 200, lambda_rel=1.0), np.zeros((9, 64)))
+    s_below = O.fista(plan.a, y, plan.lipschitz, O.block_lambda(plan.a, y, 0.999), 200)
+    top = np.argmax(np.abs(corr), axis=1)
+    assert np.all(s_below[np.arange(9), top] != 0.0)
+    # at lambda_rel = 0.01 the decode is the FISTA run with the loop-built lambda
+    lam = np.array([0.01 * max(abs(sum(plan.a[i, j] * y[b, i] for i in range(16)))
+                               for j in range(64)) for b in range(9)])
+    want = O.fista(plan.a, y, plan.lipschitz, lam, 60) @ plan.psi.T
+    assert np.allclose(O.decode_blocks(plan, y, 60, lambda_rel=0.01), want, rtol=0, atol=1e-9)

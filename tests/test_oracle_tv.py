@@ -97,3 +97,37 @@ def test_4x4_matches_linear_program():
     # the optimal value is unique (the minimiser need not be): compare it, and feasibility
     assert np.abs(d @ r).sum() == pytest.approx(tv_star, rel=1e-4)
     assert np.linalg.norm(plan.phi @ r - y) / np.linalg.norm(y) < 1e-5
+
+
+def test_tv_decode_adds_back_each_gops_own_key():
+    """Two static GOPs with different keys: the residuals are zero, TV recovery
+    keeps them zero, and every CS frame decodes to its own GOP's key
+    (frame t uses key floor(t/G) G, Sec. 3.2, Eq. 4)."""
+    from paper_1311_1419_gb300 import scenes
+
+    plan = O.Plan(64, 16, seed=1)
+    keys = scenes.surveillance_video(2, 24, 16, seed=9)
+    assert not np.array_equal(keys[0], keys[1])
+    gop = 3
+    frames = np.stack([keys[0]] * gop + [keys[1]] * gop)
+    y = O.encode(plan, frames, gop)
+    out = O.decode_tv(plan, keys, y, gop, 2 * gop, 20)
+    assert np.array_equal(out[:2], np.stack([keys[0]] * 2).astype(np.float64))
+    assert np.array_equal(out[2:], np.stack([keys[1]] * 2).astype(np.float64))
+
+
+def test_tv_decode_is_key_plus_recovered_residual():
+    """With moving content the decoded frame minus its key is the TV recovery of
+    that frame's residual blocks, cropped (Eq. 4), for every GOP."""
+    from paper_1311_1419_gb300 import scenes
+
+    plan = O.Plan(64, 32, seed=3)
+    frames = scenes.surveillance_video(6, 20, 28, seed=4)
+    gop = 3
+    y = O.encode(plan, frames, gop)
+    keys = frames[::gop]
+    out = O.decode_tv(plan, keys, y, gop, 6, 15)
+    for i, t in enumerate([1, 2, 4, 5]):
+        r = O.tv_adm(plan.phi, y[i], plan.lipschitz, 15)
+        want = frames[(t // gop) * gop].astype(np.float64) + O.unblockify(r, 20, 28, 8)
+        assert np.array_equal(out[i], want)
