@@ -5,6 +5,7 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <new>
 #include <string>
@@ -28,6 +29,56 @@ int cuda_fail(cudaError_t err, const char* what) {
     g_last_error = std::string(what) + ": " + cudaGetErrorName(err) + " (" +
                    cudaGetErrorString(err) + ")";
     return err == cudaErrorMemoryAllocation ? CS_ENOMEM : CS_ECUDA;
+}
+
+cudaError_t slot_ring_init(SlotRing* r, int n) {
+    for (int i = 0; i < n; ++i) {
+        cudaEvent_t e = nullptr;
+        cudaError_t err = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (err != cudaSuccess) return err;
+        r->ev.push_back(e);
+    }
+    return cudaSuccess;
+}
+
+void slot_ring_destroy(SlotRing* r) {
+    for (cudaEvent_t e : r->ev) cudaEventDestroy(e);
+    r->ev.clear();
+}
+
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st == cudaStreamCaptureStatusActive;
+}
+
+cudaError_t slot_take(SlotRing* r, cudaStream_t s, int* slot) {
+    if (r->ev.empty()) return cudaErrorInvalidValue;
+    const int i = (int)(r->next++ % r->ev.size());
+    *slot = i;
+    return cudaStreamWaitEvent(s, r->ev[i], capturing(s) ? cudaEventWaitExternal : 0);
+}
+
+cudaError_t slot_done(SlotRing* r, int slot, cudaStream_t s) {
+    return capturing(s) ? cudaEventRecordWithFlags(r->ev[slot], s, cudaEventRecordExternal)
+                        : cudaEventRecord(r->ev[slot], s);
+}
+
+cudaStream_t fork_stream(const cs_ctx* ctx, cudaStream_t s, int which) {
+    int set = 0;
+    for (size_t i = 0; i < ctx->streams.size(); ++i)
+        if (ctx->streams[i] == s) set = (int)i + 1;
+    return ctx->fork_streams[(size_t)set * kForkStreams + which];
+}
+
+// Device scratch of the decode kernels counts against the context's HBM
+// budget: with a budget it may take at most half of it, and no more than the
+// serving pool (once it exists) and earlier scratch leave.
+static size_t scratch_room(const cs_ctx* ctx) {
+    if (!ctx->hbm_budget) return SIZE_MAX;
+    const size_t used = ctx->scratch_bytes + serving_pool_bytes(ctx);
+    const size_t room = ctx->hbm_budget > used ? ctx->hbm_budget - used : 0;
+    const size_t half = ctx->hbm_budget / 2;
+    return std::min(room, half > ctx->scratch_bytes ? half - ctx->scratch_bytes : (size_t)0);
 }
 
 // Validate a call's parameters against the plan and derive the GOP shape.
@@ -166,6 +217,7 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
     if (e == cudaSuccess) e = cudaMalloc(&ctx->err_dev, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->err_dev, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counters_dev, sizeof(int) * kTileCounters);
+    if (e == cudaSuccess) e = slot_ring_init(&ctx->counter_ring, kTileCounters);
     for (int i = 0; e == cudaSuccess && i < 8; ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -173,10 +225,11 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
     }
     int prio_least = 0, prio_greatest = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
-    for (int i = 0; e == cudaSuccess && i < kForkStreams; ++i) {
+    // one fork set for callers' streams and one per serving stream
+    for (int i = 0; e == cudaSuccess && i < kForkStreams * (1 + (int)ctx->streams.size()); ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking,
-                                         i == kForkTc8Head ? prio_greatest : prio_least);
+                                         i % kForkStreams == kForkTc8Head ? prio_greatest : prio_least);
         if (e == cudaSuccess) ctx->fork_streams.push_back(s);
     }
     if (e != cudaSuccess) {
@@ -203,6 +256,9 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     if (ctx->counters_dev) cudaFree(ctx->counters_dev);
     if (ctx->tc8_scratch) cudaFree(ctx->tc8_scratch);
     if (ctx->tcs_scratch) cudaFree(ctx->tcs_scratch);
+    slot_ring_destroy(&ctx->counter_ring);
+    slot_ring_destroy(&ctx->tc8_ring);
+    slot_ring_destroy(&ctx->tcs_ring);
     delete ctx;
     return CS_OK;
 }
@@ -263,9 +319,23 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
             if (e == cudaSuccess) e = launch_tcs_images(p->a, p->a_tcs, n, m, p->tc_ea, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e == cudaSuccess) {
-                // the streaming decode's per-CTA iterates, one ring per context
+                // the streaming decode's per-CTA iterates, one ring per context, as
+                // many per-launch areas (up to kTcsSlotsMax) as the budget allows;
+                // none fits: this context decodes these shapes without the
+                // streaming kernel
                 std::lock_guard<std::mutex> lock(ctx->mu);
-                if (!ctx->tcs_scratch) e = cudaMalloc(&ctx->tcs_scratch, tcs_scratch_bytes(ctx->sm_count));
+                if (!ctx->tcs_scratch) {
+                    const size_t slot = tcs_slot_bytes(ctx->sm_count);
+                    const int n = (int)std::min<size_t>(kTcsSlotsMax, scratch_room(ctx) / slot);
+                    if (n > 0) {
+                        e = cudaMalloc(&ctx->tcs_scratch, (size_t)n * slot);
+                        if (e == cudaSuccess) e = slot_ring_init(&ctx->tcs_ring, n);
+                        if (e == cudaSuccess) {
+                            ctx->tcs_slots = n;
+                            ctx->scratch_bytes += (size_t)n * slot;
+                        }
+                    }
+                }
             }
         }
         if (e == cudaSuccess && tc_chip && n == 256 && ranges[2] > 0.f) {
@@ -276,9 +346,15 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
         if (e == cudaSuccess && tc_chip && n == 1024) {
-            // the cluster decode's s^K all-gather, one per context
+            // the cluster decode's s^K all-gather, one ring per context (when the
+            // budget has no room for it, 32 x 32 blocks skip the cluster kernel)
             std::lock_guard<std::mutex> lock(ctx->mu);
-            if (!ctx->tc8_scratch) e = cudaMalloc(&ctx->tc8_scratch, tc8_scratch_bytes(ctx->sm_count));
+            const size_t bytes = (size_t)kScratchSlots * tc8_slot_bytes(ctx->sm_count);
+            if (!ctx->tc8_scratch && bytes <= scratch_room(ctx)) {
+                e = cudaMalloc(&ctx->tc8_scratch, bytes);
+                if (e == cudaSuccess) e = slot_ring_init(&ctx->tc8_ring, kScratchSlots);
+                if (e == cudaSuccess) ctx->scratch_bytes += bytes;
+            }
         }
     }
     if (gram) cudaFree(gram);
@@ -374,7 +450,7 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
     if (!tcs_jobs.empty() && !tc_jobs.empty()) {
         // the streaming kernel's launch on its own fork stream, joined back on s:
         // its CTAs take SMs as the on-chip launches' tails drain
-        cudaStream_t fs = ctx->fork_streams[kForkTcs];
+        cudaStream_t fs = fork_stream(ctx, s, kForkTcs);
         cudaEvent_t fork = nullptr, join = nullptr;
         e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join, cudaEventDisableTiming);

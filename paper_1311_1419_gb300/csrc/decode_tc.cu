@@ -722,7 +722,8 @@ cudaError_t launch_tc_images(const float* a, uint8_t* img, int n, int m, int ea,
 
 bool tc_supported(const cs_plan* plan, int precision) {
     (void)precision;
-    return plan->a_tc != nullptr && tc_plan_supported(plan->n, plan->m);
+    return plan->a_tc != nullptr && tc_plan_supported(plan->n, plan->m) &&
+           (plan->n != 1024 || plan->ctx->tc8_scratch != nullptr);
 }
 
 static void fill_job(const DecodeArgs& d, int tile_begin, TcJob* J, bool* bf) {
@@ -781,9 +782,13 @@ static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool 
     L.beta = jobs[0]->beta;
     L.err = jobs[0]->plan->ctx->err_dev;
     cs_ctx* ctx = jobs[0]->plan->ctx;
-    L.tile_counter = ctx->counters_dev + (ctx->next_counter.fetch_add(1) % kTileCounters);
+    std::lock_guard<std::mutex> lock(ctx->launch_mu);
+    int cslot = 0;
+    cudaError_t e = slot_take(&ctx->counter_ring, s, &cslot);
+    if (e != cudaSuccess) return e;
+    L.tile_counter = ctx->counters_dev + cslot;
     L.drop_arrival = ctx->debug_flags.exchange(0) & CS_DEBUG_DROP_ARRIVAL;
-    cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
+    e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     int tiles = 0;
     for (int i = 0; i < n_jobs; ++i) {
@@ -795,8 +800,10 @@ static cudaError_t launch_group(const DecodeArgs* const* jobs, int n_jobs, bool 
     L.n_tiles = tiles;
     const int sms = ctx->sm_count;
     const int grid = tiles < sms ? tiles : sms;
-    if (mx <= 96) return bf ? launch_kernel<true, 96>(L, grid, s) : launch_kernel<false, 96>(L, grid, s);
-    return bf ? launch_kernel<true, 128>(L, grid, s) : launch_kernel<false, 128>(L, grid, s);
+    if (mx <= 96) e = bf ? launch_kernel<true, 96>(L, grid, s) : launch_kernel<false, 96>(L, grid, s);
+    else e = bf ? launch_kernel<true, 128>(L, grid, s) : launch_kernel<false, 128>(L, grid, s);
+    if (e != cudaSuccess) return e;
+    return slot_done(&ctx->counter_ring, cslot, s);
 }
 
 static double job_cost(const DecodeArgs& d) {
@@ -854,7 +861,7 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
         if (e == cudaSuccess) e = cudaEventRecord(fork, s);
         std::vector<cudaEvent_t> joins;
         for (size_t i = 0; e == cudaSuccess && i < launches.size(); ++i) {
-            cudaStream_t fs = i == 0 ? s : ctx->fork_streams[(i - 1) % kForkTcGroups];
+            cudaStream_t fs = i == 0 ? s : fork_stream(ctx, s, (int)((i - 1) % kForkTcGroups));
             if (i > 0) e = cudaStreamWaitEvent(fs, fork, 0);
             if (e == cudaSuccess) e = launch_group(launches[i].jobs, launches[i].n, launches[i].bf,
                                                    launches[i].mx, fs);

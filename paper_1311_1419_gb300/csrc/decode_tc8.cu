@@ -771,8 +771,8 @@ cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaS
 
 static size_t tc8_slot_floats(int sm_count) { return (size_t)(sm_count / kCl + 1) * kTile * kN; }
 
-size_t tc8_scratch_bytes(int sm_count) {
-    return (size_t)kScratchSlots * tc8_slot_floats(sm_count) * sizeof(float);
+size_t tc8_slot_bytes(int sm_count) {
+    return tc8_slot_floats(sm_count) * sizeof(float);
 }
 
 static void fill_job8(const DecodeArgs& d, int tile_begin, Tc8Job* J) {
@@ -825,8 +825,11 @@ static cudaError_t launch_group8(const DecodeArgs* const* jobs, int n_jobs, bool
     Tc8Launch L{};
     L.beta = jobs[0]->beta;
     L.err = ctx->err_dev;
-    L.scratch = ctx->tc8_scratch +
-                (ctx->tc8_next_slot.fetch_add(1) % kScratchSlots) * tc8_slot_floats(ctx->sm_count);
+    std::lock_guard<std::mutex> lock(ctx->launch_mu);
+    int slot = 0;
+    cudaError_t e = slot_take(&ctx->tc8_ring, s, &slot);
+    if (e != cudaSuccess) return e;
+    L.scratch = ctx->tc8_scratch + (size_t)slot * tc8_slot_floats(ctx->sm_count);
     int tiles = 0;
     for (int i = 0; i < n_jobs; ++i) {
         fill_job8(*jobs[i], tiles, &L.jobs[i]);
@@ -835,7 +838,7 @@ static cudaError_t launch_group8(const DecodeArgs* const* jobs, int n_jobs, bool
     L.n_jobs = n_jobs;
     L.n_tiles = tiles;
     const void* fn = bf ? (const void*)k_fista_tc8<true> : (const void*)k_fista_tc8<false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes);
     if (e != cudaSuccess) return e;
     // the epilogue's setmaxnreg.inc draws on the registers the CTA was launched with
     cudaFuncAttributes fa;
@@ -853,7 +856,9 @@ static cudaError_t launch_group8(const DecodeArgs* const* jobs, int n_jobs, bool
         k_fista_tc8<true><<<clusters * kCl, kThreads, kSmemBytes, s>>>(L);
     else
         k_fista_tc8<false><<<clusters * kCl, kThreads, kSmemBytes, s>>>(L);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return slot_done(&ctx->tc8_ring, slot, s);
 }
 
 static double job_cost8(const DecodeArgs& d) {
@@ -917,8 +922,8 @@ cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStre
         cudaStream_t hs = s, fs = nullptr;
         cudaEvent_t fork = nullptr, join_h = nullptr, join_t = nullptr;
         if (!tail[bf].empty()) {
-            hs = ctx->fork_streams[kForkTc8Head];
-            fs = ctx->fork_streams[kForkTc8Tail];
+            hs = fork_stream(ctx, s, kForkTc8Head);
+            fs = fork_stream(ctx, s, kForkTc8Tail);
             e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_h, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join_t, cudaEventDisableTiming);

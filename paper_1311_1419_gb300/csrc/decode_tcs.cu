@@ -708,8 +708,8 @@ bool tcs_plan_supported(int n, int m) {
 size_t tcs_operand_bytes(int n, int m) {
     return 4ull * (size_t)(m16_of_s(m) + m32_of_s(m)) * (size_t)n * 2;
 }
-size_t tcs_scratch_bytes(int sm_count) {
-    return (size_t)kScratchSlots * (size_t)(kCtasPerSm * sm_count) * kScrBytes;
+size_t tcs_slot_bytes(int sm_count) {
+    return (size_t)(kCtasPerSm * sm_count) * kScrBytes;
 }
 
 cudaError_t launch_tcs_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s) {
@@ -773,11 +773,15 @@ static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, boo
     TcsLaunch L{};
     L.beta = jobs[0]->beta;
     L.err = ctx->err_dev;
-    L.tile_counter = ctx->counters_dev + (ctx->next_counter.fetch_add(1) % kTileCounters);
+    std::lock_guard<std::mutex> lock(ctx->launch_mu);
+    int cslot = 0, sslot = 0;
+    cudaError_t e = slot_take(&ctx->counter_ring, s, &cslot);
+    if (e == cudaSuccess) e = slot_take(&ctx->tcs_ring, s, &sslot);
+    if (e != cudaSuccess) return e;
+    L.tile_counter = ctx->counters_dev + cslot;
     L.drop_arrival = ctx->debug_flags.exchange(0) & CS_DEBUG_DROP_ARRIVAL;
-    L.scratch = ctx->tcs_scratch + (ctx->tcs_next_slot.fetch_add(1) % kScratchSlots) *
-                                       (size_t)(kCtasPerSm * ctx->sm_count) * kScrBytes;
-    cudaError_t e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
+    L.scratch = ctx->tcs_scratch + (size_t)sslot * tcs_slot_bytes(ctx->sm_count);
+    e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
     if (e != cudaSuccess) return e;
     int tiles = 0;
     for (int i = 0; i < n_jobs; ++i) {
@@ -795,7 +799,10 @@ static cudaError_t launch_group_s(const DecodeArgs* const* jobs, int n_jobs, boo
         k_fista_tcs<true><<<grid, kThreads, kSmemBytes, s>>>(L);
     else
         k_fista_tcs<false><<<grid, kThreads, kSmemBytes, s>>>(L);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = slot_done(&ctx->counter_ring, cslot, s);
+    if (e == cudaSuccess) e = slot_done(&ctx->tcs_ring, sslot, s);
+    return e;
 }
 
 int tcs_ctas_per_sm() { return kCtasPerSm; }

@@ -20,6 +20,7 @@ constexpr int kMaxIters = 1 << 17;
 constexpr int kMaxN = 4096;
 constexpr int kTileCounters = 256;   // per-launch tile counters of the persistent decode
 constexpr int kScratchSlots = 16;    // per-launch scratch areas of the 32 x 32 cluster decode
+constexpr int kTcsSlotsMax = 8;      // per-launch iterate scratch areas of the streaming decode
 
 void set_error(const std::string& msg);
 int fail(int status, const std::string& msg);
@@ -34,6 +35,24 @@ int cuda_fail(cudaError_t err, const char* what);
 struct Ticket;
 struct Pool;
 
+// A ring of per-launch device resources (tile counters, scratch areas).  A
+// launch takes the next slot; its stream first waits for the completion event
+// of the slot's previous holder, and the event is recorded again after the
+// launch.  So two launches never hold one slot at the same time, whatever the
+// number of streams.  Inside a stream capture the wait and the record become
+// external event nodes of the graph, so that replays order themselves the same
+// way against eager launches and other replays.  The caller holds the
+// context's launch_mu from slot_take to slot_done, so the holders of a slot
+// record its event in the order in which they took it.
+struct SlotRing {
+    std::vector<cudaEvent_t> ev;
+    uint64_t next = 0;
+};
+cudaError_t slot_ring_init(SlotRing* r, int n);
+void slot_ring_destroy(SlotRing* r);
+cudaError_t slot_take(SlotRing* r, cudaStream_t s, int* slot);
+cudaError_t slot_done(SlotRing* r, int slot, cudaStream_t s);
+
 }  // namespace csvc
 
 struct cs_ctx {
@@ -42,17 +61,17 @@ struct cs_ctx {
     size_t hbm_budget = 0;
     float* beta_dev = nullptr;          // FISTA momentum (t_k - 1)/t_{k+1}, k = 1..kMaxIters
     int* err_dev = nullptr;             // set to 1 by a kernel whose bounded wait gave up
-    int* counters_dev = nullptr;        // csvc::kTileCounters tile counters, used round robin
-    // s^K all-gather of the 32 x 32 cluster decode: a ring of kScratchSlots
-    // per-launch areas, so that launches in flight on different streams (serving)
-    // never share one
+    int* counters_dev = nullptr;        // csvc::kTileCounters tile counters (counter_ring)
+    // s^K all-gather of the 32 x 32 cluster decode: csvc::kScratchSlots
+    // per-launch areas (tc8_ring)
     float* tc8_scratch = nullptr;
-    std::atomic<uint64_t> tc8_next_slot{0};
-    // iterates of the streaming tensor-core decode: kScratchSlots per-launch
-    // areas of sm_count per-CTA scratches
+    // iterates of the streaming tensor-core decode: tcs_slots per-launch areas
+    // of (CTAs per SM x sm_count) per-CTA scratches (tcs_ring)
     uint8_t* tcs_scratch = nullptr;
-    std::atomic<uint64_t> tcs_next_slot{0};
-    std::atomic<uint64_t> next_counter{0};  // lock-free: launches happen under ctx->mu too
+    int tcs_slots = 0;
+    size_t scratch_bytes = 0;           // tc8_scratch + tcs_scratch
+    std::mutex launch_mu;               // held from slot_take to slot_done
+    csvc::SlotRing counter_ring, tc8_ring, tcs_ring;
     std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
     // autotuned decode shape per (N, M): engine, plain-kernel threads and blocks per CTA
     std::mutex tune_mu;
@@ -64,7 +83,10 @@ struct cs_ctx {
     std::vector<csvc::Ticket*> live;
     uint64_t next_ticket = 1;
     std::vector<cudaStream_t> streams;
-    std::vector<cudaStream_t> fork_streams;   // extra persistent launches of one batched decode
+    // extra persistent launches of one batched decode: csvc::kForkStreams fork
+    // streams per origin, set 0 for callers' own streams, set 1 + i for serving
+    // stream i (so that serving requests never queue behind one another's forks)
+    std::vector<cudaStream_t> fork_streams;
     int next_stream = 0;
 };
 
@@ -143,11 +165,11 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
 // 32 x 32 blocks (N = 1024): clusters of 8 CTAs (decode_tc8.cu)
 cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaStream_t s);
-size_t tc8_scratch_bytes(int sm_count);
+size_t tc8_slot_bytes(int sm_count);   // one per-launch area of the cluster decode
 // any N in {64, 256, 1024}, M <= 512, iterates in global memory (decode_tcs.cu)
 bool tcs_plan_supported(int n, int m);
 size_t tcs_operand_bytes(int n, int m);
-size_t tcs_scratch_bytes(int sm_count);
+size_t tcs_slot_bytes(int sm_count);   // one per-launch area of the streaming decode
 cudaError_t launch_tcs_images(const float* a, uint8_t* img, int n, int m, int ea, cudaStream_t s);
 bool tcs_supported(const cs_plan* plan);
 cudaError_t launch_decode_tcs(const DecodeArgs& d, cudaStream_t s);
@@ -159,9 +181,12 @@ int tcs_ctas_per_sm();
 // streaming launch, 4 the streaming tail of cluster-kernel jobs, 5 (the device's
 // highest stream priority) the cluster kernel when it has tails beside it
 constexpr int kForkTcGroups = 3, kForkTcs = 3, kForkTc8Tail = 4, kForkTc8Head = 5, kForkStreams = 6;
+// The fork stream `which` of the set that belongs to origin stream s.
+cudaStream_t fork_stream(const cs_ctx* ctx, cudaStream_t s, int which);
 
 // serving (serving.cu)
 void serving_destroy(cs_ctx* ctx);
+size_t serving_pool_bytes(const cs_ctx* ctx);   // 0 until the first cs_submit
 
 // metrics (metrics.cu)
 cudaError_t launch_psnr(const uint8_t* ref, const float* test, int n_frames, int h, int w,

@@ -77,6 +77,8 @@ namespace {
 void CUDART_CB mark_done(void* p) { static_cast<Ticket*>(p)->done_ms.store(now_ms()); }
 }  // namespace
 
+size_t serving_pool_bytes(const cs_ctx* ctx) { return ctx->pool ? ctx->pool->size : 0; }
+
 void serving_destroy(cs_ctx* ctx) {
     for (Ticket* t : ctx->live) {
         if (t->done_event) cudaEventDestroy(t->done_event);
@@ -116,7 +118,13 @@ extern "C" int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params,
     if (!ctx->pool) {
         Pool* p = new (std::nothrow) Pool();
         if (!p) return fail(CS_ENOMEM, "host allocation failed");
-        p->size = ctx->hbm_budget ? ctx->hbm_budget / kAlign * kAlign : kDefaultPool;
+        // the budget less the decode kernels' scratch already allocated
+        const size_t avail = ctx->hbm_budget > ctx->scratch_bytes ? ctx->hbm_budget - ctx->scratch_bytes : 0;
+        p->size = ctx->hbm_budget ? avail / kAlign * kAlign : kDefaultPool;
+        if (p->size == 0) {
+            delete p;
+            return fail(CS_ENOMEM, "the HBM budget is taken by decode scratch");
+        }
         cudaError_t e = cudaMalloc(&p->base, p->size);
         if (e != cudaSuccess) {
             delete p;
@@ -173,11 +181,19 @@ extern "C" int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* laten
         Ticket* t = ctx->live[i];
         if (t->id != ticket) continue;
         cudaError_t e = cudaEventQuery(t->done_event);
+        if (e != cudaSuccess && e != cudaErrorNotReady) {
+            // the request failed on the device: report it once and retire the ticket
+            const int st = cuda_fail(e, "cs_poll");
+            ctx->pool->release(t->offset, t->bytes);
+            cudaEventDestroy(t->done_event);
+            delete t;
+            ctx->live.erase(ctx->live.begin() + i);
+            return st;
+        }
         if (e == cudaErrorNotReady || t->done_ms.load() < 0.0) {
             *done = 0;
             return CS_OK;
         }
-        if (e != cudaSuccess) return cuda_fail(e, "cs_poll");
         *done = 1;
         if (latency_ms) *latency_ms = (float)(t->done_ms.load() - t->submit_ms);
         ctx->pool->release(t->offset, t->bytes);

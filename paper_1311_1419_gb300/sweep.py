@@ -49,7 +49,10 @@ def _psnr(ref, test):
     return float("inf") if mse == 0 else 10 * np.log10(255.0 ** 2 / mse)
 
 
-def table1_shape(ctx, iters=200, gops=(3, 5, 7), crs=(40, 60, 80), n_gops=6, seed=0):
+def table1_shape(ctx, iters=200, gops=(3, 5, 7), crs=(40, 60, 80), n_gops=6, seed=0,
+                 keep_frames=False):
+    """One row per (GOP, CS-frame CR); with keep_frames each row also carries
+    the clip ("frames") and the decoded CS frames ("decoded", float64)."""
     rows = []
     for g in gops:
         frames = scenes.surveillance_video(g * n_gops, H, W, seed=seed)
@@ -61,10 +64,12 @@ def table1_shape(ctx, iters=200, gops=(3, 5, 7), crs=(40, 60, 80), n_gops=6, see
                          "total_cr_table_i": B.cs_total_cr(g, CR_KEY, N / m),
                          "total_cr_raw_key": B.cs_raw_key_cr(g, H, W, BLK, m),
                          "psnr_cs_db": _psnr(frames[cs], dec)})
+            if keep_frames:
+                rows[-1].update(frames=frames[:g * n_gops], decoded=dec)
     return rows
 
 
-def fig5_shape(ctx, iters=200, cr=50, gop=5, n_gops=8, seed=0):
+def fig5_shape(ctx, iters=200, cr=50, gop=5, n_gops=8, seed=0, keep_frames=False):
     m = max(1, int(np.rint(N / cr)))
     frames = scenes.surveillance_video(gop * n_gops, H, W, seed=seed)
     dec = _decode(ctx, frames, gop, m, iters)
@@ -73,7 +78,10 @@ def fig5_shape(ctx, iters=200, cr=50, gop=5, n_gops=8, seed=0):
         idx = [g * (gop - 1) + pos - 1 for g in range(n_gops)]
         ref = frames[[g * gop + pos for g in range(n_gops)]]
         per_pos.append(_psnr(ref, dec[idx]))
-    return {"gop": gop, "cr_cs": cr, "m": m, "psnr_by_position_db": per_pos}
+    out = {"gop": gop, "cr_cs": cr, "m": m, "psnr_by_position_db": per_pos}
+    if keep_frames:
+        out.update(frames=frames, decoded=dec)
+    return out
 
 
 def fig6_shape(ctx, iters=200, gop=5, crs=(10, 20, 30, 40, 50, 60, 70, 80), n_gops=6, seed=0):

@@ -38,3 +38,37 @@ def test_fig5_shape_psnr_decays_within_the_gop(ctx):
     p = f5["psnr_by_position_db"]
     assert len(p) == 4
     assert all(a > b for a, b in zip(p, p[1:])), p
+
+
+def _vs_oracle(frames, dec, gop, m, iters):
+    """Frame rel-l2 and PSNR difference of the library's decode against the FP64
+    oracle's decode of the same clip, plan and iteration count."""
+    plan = O.Plan(256, m, 0)
+    y = O.encode(plan, frames, gop)
+    want, _ = O.decode(plan, frames[::gop], y, gop, frames.shape[0], iters)
+    cs = O.cs_frame_indices(frames.shape[0], gop)
+    rel = np.linalg.norm(dec - want) / np.linalg.norm(want)
+    dpsnr = O.psnr(frames[cs], dec) - O.psnr(frames[cs], want)
+    return rel, dpsnr
+
+
+def test_table1_shape_decodes_match_the_oracle(ctx):
+    """Every decode of the Table I shape (GOP 3, 5, 7 x rate 23:40, 23:60, 23:80,
+    i.e. M = 6, 4, 3 measurements per 16 x 16 block, K = 200) equals the
+    oracle's within the FP32 tolerance: frame rel-l2 <= 1e-4, PSNR within 0.01 dB."""
+    from paper_1311_1419_gb300 import sweep
+    rows = sweep.table1_shape(ctx, iters=200, n_gops=2, keep_frames=True)
+    assert sorted({r["m"] for r in rows}) == [3, 4, 6]
+    for r in rows:
+        rel, dpsnr = _vs_oracle(r["frames"], r["decoded"], r["gop"], r["m"], 200)
+        assert rel <= 1e-4, (r["gop"], r["m"], rel)
+        assert abs(dpsnr) <= 0.01, (r["gop"], r["m"], dpsnr)
+
+
+def test_fig5_shape_decode_matches_the_oracle(ctx):
+    """The Fig. 5 shape (1 key + 4 CS frames, CR_cs 50, M = 5, K = 200)."""
+    from paper_1311_1419_gb300 import sweep
+    f5 = sweep.fig5_shape(ctx, iters=200, n_gops=3, keep_frames=True)
+    assert f5["m"] == 5
+    rel, dpsnr = _vs_oracle(f5["frames"], f5["decoded"], 5, 5, 200)
+    assert rel <= 1e-4 and abs(dpsnr) <= 0.01, (rel, dpsnr)
