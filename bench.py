@@ -1,11 +1,21 @@
 #!/usr/bin/env python
 """Recovered Mpixel/s of the block-CS video codec hot path on GB300.
 
-One step = the whole hot path over the CIF M-sweep clip: for each M in
-{26, 51, 77, 128}, encode all 8 GOPs (64 frames, 352x288, GOP 8, 16x16 blocks)
-then decode them with 300 FISTA iterations and score the result (PSNR).  The
-four plans (Phi, A, L) are built once before timing, like weights; their build
-time is reported as plan_ms.  value = recovered CS-frame pixels per second.
+Default workload: the 720p clip (1280x720, 96 frames, GOP 16, 32x32 blocks,
+M = 102, FISTA 300 iterations, FP32-grade products).  One step = the whole hot
+path over the clip: encode every CS frame (y = Phi r per block), decode all of
+them in one batched call, score the result (PSNR).  The plan (Phi, A, L) is
+built and the decode shape autotuned once before timing, like weights; their
+times are reported as plan_ms and autotune.  value = recovered CS-frame pixels
+per second over the device-resident step; e2e = the same through the
+host-buffer entry point cs_codec_host (copies inside the timed region).
+
+Beside the headline, the same JSON line carries the other workloads: the CIF
+M-sweep (cif_sweep), the plain per-block FP32 decode of the 720p clip
+(plain_engine, and the tensor path's ratio to it), the 64-GOP heterogeneous
+batch (mixed64), the mixed-precision decodes of the clip, TV recovery and a
+serving sweep.  --workload cif or mixed64 puts that workload in the headline
+instead; --no-extras leaves the others out.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -30,21 +40,21 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 WORKLOADS = {
+    "720p": {
+        "workload": "720p 1280x720, 96 frames, GOP 16 (1 raw key + 15 CS), 32x32 blocks (N=1024), "
+                    "M=102 (10%), Gaussian Phi N(0,1/M) Philox seed 0, FISTA 300 iters, "
+                    "lambda=0.01*||A^T y||_inf, synthetic surveillance scene, FP32-grade products",
+        "metric": "recovered Mpixel/s at fixed iters (720p, 32x32 blocks, FISTA 300 iters)",
+        "height": 720, "width": 1280, "frames": 96, "gop": 16, "block": 32,
+        "ms": [102], "iters": 300, "lambda_rel": 0.01, "seed": 0, "oracle_frames": 1,
+    },
     "cif": {
         "workload": "CIF 352x288, 64 frames, GOP 8 (1 raw key + 7 CS), 16x16 blocks (N=256), "
                     "M in {26,51,77,128} (CR sweep), Gaussian Phi N(0,1/M) Philox seed 0, "
                     "FISTA 300 iters, lambda=0.01*||A^T y||_inf, synthetic surveillance scene",
         "metric": "recovered Mpixel/s at fixed iters (CIF M-sweep, FISTA 300 iters)",
         "height": 288, "width": 352, "frames": 64, "gop": 8, "block": 16,
-        "ms": [26, 51, 77, 128], "iters": 300, "lambda_rel": 0.01, "seed": 0, "oracle_frames": 5,
-    },
-    "720p": {
-        "workload": "720p 1280x720, 96 frames, GOP 16 (1 raw key + 15 CS), 32x32 blocks (N=1024), "
-                    "M=102 (10%), Gaussian Phi N(0,1/M) Philox seed 0, FISTA 300 iters, "
-                    "lambda=0.01*||A^T y||_inf, synthetic surveillance scene",
-        "metric": "recovered Mpixel/s at fixed iters (720p, 32x32 blocks, FISTA 300 iters)",
-        "height": 720, "width": 1280, "frames": 96, "gop": 16, "block": 32,
-        "ms": [102], "iters": 300, "lambda_rel": 0.01, "seed": 0, "oracle_frames": 1,
+        "ms": [26, 51, 77, 128], "iters": 300, "lambda_rel": 0.01, "seed": 0, "oracle_frames": 2,
     },
 }
 WORKLOADS["mixed64"] = {
@@ -55,13 +65,12 @@ WORKLOADS["mixed64"] = {
     "metric": "recovered Mpixel/s at fixed iters (64 heterogeneous GOPs, one graph-captured batch)",
     "iters": 300, "lambda_rel": 0.01, "seed": 0, "jobs": 64,
 }
-WORKLOAD = WORKLOADS["cif"]
-METRIC = WORKLOAD["metric"]
+DEFAULT_WORKLOAD = "720p"
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the CIF step's decode, its
-# two tensor-core launches together, from one ncu capture of that exact configuration;
-# reported as roofline.traffic for it only (null for any other configuration or kernel)
-CIF_DECODE_DRAM_BYTES = 62_840_000
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the decode of one
+# step, from one ncu capture of that exact configuration (FP32-grade, batched);
+# reported as roofline.traffic for it only, null for anything else
+DECODE_DRAM_BYTES = {"cif": 62_840_000}
 FP32_LANES_PER_SM = 128
 
 
@@ -255,6 +264,8 @@ def serving_run(B, torch, dev, precision, tail, rates, seconds, hbm_budget=8 << 
         B.cs_ctx_destroy(ctx)
 
 
+
+
 def oracle_sample(frames, wl, n_cs_frames: int):
     """Time the FP64 oracle on the first n_cs_frames CS frames at every M.
 
@@ -279,6 +290,20 @@ def oracle_sample(frames, wl, n_cs_frames: int):
     return secs, pixels, out
 
 
+def parity(frames, got, want):
+    """Error of decoded CS frames 1.. (got) against the oracle's (want), both
+    [n][H][W] of the first GOP: whole-frame rel-l2, rel-l2 of the recovered
+    residual (the key frame taken out of the denominator), and PSNR difference."""
+    from oracle import cs_oracle as O
+
+    n = want.shape[0]
+    orig = frames[1:1 + n]
+    key = frames[0].astype(np.float64)
+    return {"frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+            "residual_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want - key)),
+            "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want))}
+
+
 def run_reference(args, wl, frames):
     """The reference arm: the FP64 CPU oracle as it stands, bounded samples."""
     n_cs = 1
@@ -291,8 +316,9 @@ def run_reference(args, wl, frames):
         secs.append(s)
     total = sum(secs)
     value = pixels * args.steps / total / 1e6
-    sample = ("first CS frame of the clip (396 blocks) at each M in %s, %d iters, per step"
-              % (wl["ms"], wl["iters"]))
+    nblk = (-(-wl["height"] // wl["block"])) * (-(-wl["width"] // wl["block"]))
+    sample = ("first CS frame of the clip (%d blocks) at each M in %s, %d iters, per step"
+              % (nblk, wl["ms"], wl["iters"]))
     line = {
         "impl": "reference", "metric": wl["metric"], "value": value, "unit": "Mpixel/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -327,21 +353,41 @@ def mixed_launches(jobs) -> int:
     return sum(-(-c // 48) for c in groups.values())
 
 
-def run_mixed64(args, wl):
-    """The heterogeneous batch: every GOP a job of its own plan, one batched call
-    captured in a CUDA graph and replayed; value = CS pixels per second."""
-    import torch
+def mixed64_oracle(O, job, iters, lambda_rel, max_blocks=8):
+    """Oracle check of one job of the mix on sampled blocks: the first row of
+    blocks (up to max_blocks) of the job's first CS frame, recovered by the FP64
+    oracle from its own measurements and compared with the library's frame."""
+    p, clip = job["p"], job["clip"]
+    b, h, w = p.block, p.height, p.width
+    plan = O.Plan(b * b, p.m, job["seed"])
+    res = clip[1].astype(np.int64) - clip[0].astype(np.int64)
+    k = min(max_blocks, -(-w // b))
+    y = O.blockify(res.astype(np.float64), b)[:k] @ plan.phi.T
+    r_hat = O.decode_blocks(plan, y, iters, lambda_rel)
+    rows = min(b, h)
+    cols = min(k * b, w)
+    want = np.zeros((rows, k * b))
+    for j in range(k):
+        want[:, j * b:(j + 1) * b] = r_hat[j].reshape(b, b)[:rows]
+    key = clip[0][:rows, :cols].astype(np.float64)
+    want = key + want[:, :cols]
+    got = job["out"][0, :rows, :cols].cpu().numpy().astype(np.float64)
+    orig = clip[1][:rows, :cols]
+    return {"blocks": k, "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+            "residual_rel_l2": float(np.linalg.norm(got - want) / max(np.linalg.norm(want - key), 1e-30)),
+            "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want))}
 
-    import __graft_entry__
-    from paper_1311_1419_gb300 import binding as B
+
+def run_mixed64(args, wl, B, torch, dev, steps, warmup, with_oracle=True):
+    """The heterogeneous batch: every GOP a job of its own plan, one batched call
+    captured in a CUDA graph and replayed; returns the measurement as a dict
+    (value = CS pixels per second), with the oracle's error on sampled blocks of
+    one job per (N, M) bucket."""
     from paper_1311_1419_gb300 import scenes
 
-    __graft_entry__.build()
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
     rng = np.random.default_rng(wl["seed"])
     res = [scenes.RESOLUTIONS[k] for k in ("qcif", "cif", "720p")]
-    ctx = B.cs_ctx_create(0)
+    ctx = B.cs_ctx_create(dev.index)
     stream = torch.cuda.Stream(dev)
     jobs = []
     t0 = time.perf_counter()
@@ -362,7 +408,8 @@ def run_mixed64(args, wl):
             nblk = (-(-h // b)) * (-(-w // b))
             y = torch.empty((gop - 1, nblk, m), dtype=torch.float32, device=dev)
             B.cs_encode_gop(plan, p, torch.from_numpy(clip).to(dev), y, stream)
-            jobs.append({"plan": plan, "p": p, "key": torch.from_numpy(np.ascontiguousarray(clip[:1])).to(dev),
+            jobs.append({"plan": plan, "p": p, "seed": i, "clip": clip[:2],
+                         "key": torch.from_numpy(np.ascontiguousarray(clip[:1])).to(dev),
                          "y": y, "out": torch.empty((gop - 1, h, w), dtype=torch.float32, device=dev),
                          "pixels": (gop - 1) * h * w, "tc": tc, "blocks": (gop - 1) * nblk,
                          "flops": (gop - 1) * nblk * (4.0 * m * n * wl["iters"] + 2.0 * m * n)})
@@ -382,12 +429,12 @@ def run_mixed64(args, wl):
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g, stream=stream, capture_error_mode="thread_local"):
                 B.cs_decode_batch(ctx, *args_, None, stream)
-            for _ in range(args.warmup):
+            for _ in range(warmup):
                 g.replay()
             torch.cuda.synchronize(dev)
             times = []
-            with ClockSampler(0) as clocks:
-                for _ in range(args.steps):
+            with ClockSampler(dev.index) as clocks:
+                for _ in range(steps):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(stream)
@@ -399,22 +446,345 @@ def run_mixed64(args, wl):
         ms = sum(times) / len(times)
         pixels = sum(j["pixels"] for j in jobs)
         tc_pix = sum(j["pixels"] for j in jobs if j["tc"])
-        line = {
+        gflop = sum(j["flops"] for j in jobs) / 1e9
+        out = {
             "metric": wl["metric"], "value": pixels / (ms / 1e3) / 1e6, "unit": "Mpixel/s",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16x2/f32",
-            "data": "synthetic", "config": {"workload": wl["workload"]},
-            "jobs": len(jobs), "tensor_core_jobs": sum(j["tc"] for j in jobs),
-            "pixels_per_step": pixels, "tensor_core_pixel_share": tc_pix / pixels,
-            "gflop_per_step": sum(j["flops"] for j in jobs) / 1e9,
-            "gpu_launches": mixed_launches(jobs), "clocks": clocks.summary(), "setup_s": setup_s,
-            "autotuned_shapes": len(tuned),
+            "ms_per_step": ms, "steps": steps, "warmup": warmup, "dtype": "bf16x2/f32",
+            "workload": wl["workload"], "jobs": len(jobs),
+            "tensor_core_jobs": sum(j["tc"] for j in jobs), "pixels_per_step": pixels,
+            "tensor_core_pixel_share": tc_pix / pixels, "gflop_per_step": gflop,
+            "achieved_tflops": gflop / ms, "gpu_launches": mixed_launches(jobs) * steps,
+            "clocks": clocks.summary(), "setup_s": setup_s, "autotuned_shapes": len(tuned),
         }
-        print(json.dumps(line), flush=True)
+        if with_oracle:
+            from oracle import cs_oracle as O
+            seen, errs = set(), {}
+            for j in jobs:
+                key = (j["p"].block * j["p"].block, j["p"].m)
+                if key in seen:
+                    continue
+                seen.add(key)
+                errs["N=%d,M=%d" % key] = mixed64_oracle(O, j, wl["iters"], wl["lambda_rel"])
+            out["vs_oracle"] = {
+                "sample": "first block row (up to 8 blocks) of the first CS frame of one job per "
+                          "(N, M) bucket, FP64 oracle from its own measurements",
+                "buckets": errs,
+                "max_frame_rel_l2": max(e["frame_rel_l2"] for e in errs.values()),
+                "max_residual_rel_l2": max(e["residual_rel_l2"] for e in errs.values()),
+                "max_abs_dpsnr_db": max(abs(e["dpsnr_db"]) for e in errs.values())}
+        return out
     finally:
         for j in jobs:
             B.cs_plan_destroy(j["plan"])
         B.cs_ctx_destroy(ctx)
+
+
+def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e=True,
+              want_mixed=True, no_batch=False):
+    """Plans, autotune, then `steps` timed steps of the whole hot path over the
+    clip (encode every M, one batched decode, PSNR), device-resident with L2
+    flushed before each step; then the same through cs_codec_host from pinned
+    host memory (e2e); then the mixed-precision decodes.  Returns a dict of the
+    measurements and the live buffers (release with codec_free)."""
+    from paper_1311_1419_gb300 import scenes
+
+    h, w, gop, b, iters = wl["height"], wl["width"], wl["gop"], wl["block"], wl["iters"]
+    n = b * b
+    n_gops = wl["frames"] // gop
+    n_cs = n_gops * (gop - 1)
+    nblk = (-(-h // b)) * (-(-w // b))
+    cs_idx = [t for t in range(wl["frames"]) if t % gop]
+    frames = scenes.surveillance_video(wl["frames"], h, w, seed=wl["seed"])
+    ms = wl["ms"]
+
+    ctx = B.cs_ctx_create(dev.index)
+    t0 = time.perf_counter()
+    plans = {m: B.cs_make_phi(ctx, n, m, wl["seed"]) for m in ms}
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    params = {m: B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops,
+                               lambda_rel=wl["lambda_rel"], engine=engine) for m in ms}
+    t0 = time.perf_counter()
+    tuned = {str(m): dict(zip(("engine", "plain_threads", "plain_blocks_per_cta", "ns_per_block_iter"),
+                              B.cs_autotune(ctx, plans[m]))) for m in ms}
+    autotune_s = time.perf_counter() - t0
+
+    stream = torch.cuda.Stream(dev)
+    frames_dev = torch.from_numpy(frames).to(dev)
+    keys_dev = torch.from_numpy(np.ascontiguousarray(frames[::gop])).to(dev)
+    cs_dev = torch.from_numpy(np.ascontiguousarray(frames[cs_idx])).to(dev)
+    y_dev = {m: torch.empty((n_cs, nblk, m), dtype=torch.float32, device=dev) for m in ms}
+    out_f = {m: torch.empty((n_cs, h, w), dtype=torch.float32, device=dev) for m in ms}
+    out_u = {m: torch.empty((n_cs, h, w), dtype=torch.uint8, device=dev) for m in ms}
+    psnr_dev = {m: torch.empty(n_cs, dtype=torch.float64, device=dev) for m in ms}
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    plan_list = [plans[m] for m in ms]
+    param_list = [params[m] for m in ms]
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    # our kernels per step: one encode and one PSNR per M, and the decode: one
+    # launch per call with no_batch, else one per (operand type, shared-memory
+    # layout) group of the 16x16 tensor path (M16 <= 96 or <= 128), one per group
+    # of the 32x32 cluster path (and its streaming tail), one per group of the
+    # streaming path, one per plain-kernel job (FP32: one operand type)
+    def decode_launches():
+        if no_batch:
+            return len(ms)
+        groups, plain = set(), 0
+        for m in ms:
+            m16 = (m + 15) // 16 * 16
+            eng = engine if engine != B.CS_ENGINE_AUTO else tuned[str(m)]["engine"]
+            if eng == B.CS_ENGINE_PLAIN:
+                plain += 1
+            elif eng == B.CS_ENGINE_TC_STREAM:
+                groups.add(("tcs",))
+            elif n == 256:
+                groups.add(("tc", m16 <= 96))
+            else:
+                groups.add(("tc8",))
+                # a large 32x32 job also launches its streaming tail on the SMs whole
+                # clusters leave idle (the library's rule: a tail once the job has more
+                # tiles than clusters x 30; 15 clusters of 8 are co-resident on this part)
+                tiles = -(-(n_cs * nblk) // 128)
+                if n_sm - 8 * 15 > 0 and tiles > 15 * 30:
+                    groups.add(("tc8 tail",))
+        return len(groups) + plain
+    launches_per_step = 2 * len(ms) + decode_launches()
+
+    enc_ev, dec_ev, psnr_ev = [], [], []
+
+    def ev_pair():
+        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def step(record):
+        if record:
+            a0, a1 = ev_pair()
+            a0.record(stream)
+        for m in ms:
+            B.cs_encode_gop(plans[m], params[m], frames_dev, y_dev[m], stream)
+        if record:
+            a1.record(stream)
+            enc_ev.append((a0, a1))
+            d0, d1 = ev_pair()
+            d0.record(stream)
+        if no_batch:
+            for m in ms:
+                B.cs_decode_gop(plans[m], params[m], keys_dev, y_dev[m], out_f[m], out_u[m], stream)
+        else:
+            B.cs_decode_batch(ctx, plan_list, param_list, [keys_dev] * len(ms),
+                              [y_dev[m] for m in ms], [out_f[m] for m in ms],
+                              [out_u[m] for m in ms], stream)
+        if record:
+            d1.record(stream)
+            dec_ev.append((d0, d1))
+            c0, c1 = ev_pair()
+            c0.record(stream)
+        for m in ms:
+            B.cs_psnr(cs_dev, out_f[m], n_cs, h, w, psnr_dev[m], stream)
+        if record:
+            c1.record(stream)
+            psnr_ev.append((c0, c1))
+
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            step(False)
+        torch.cuda.synchronize(dev)
+        step_ms = []
+        with ClockSampler(dev.index) as clocks:
+            for _ in range(steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                barrier()
+                e0, e1 = ev_pair()
+                e0.record(stream)
+                step(True)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                barrier()
+                step_ms.append(e0.elapsed_time(e1))
+        clock_info = clocks.summary()
+
+        # end to end through the C ABI's host-buffer entry point: the clip in
+        # from pinned host memory, encode, batched decode, PSNR, uint8 frames
+        # and PSNRs out, all inside the timed region
+        e2e_ms, h2d, d2h = [], 0, 0
+        if want_e2e:
+            clip_pin = torch.from_numpy(frames).pin_memory()
+            u8_pin = [torch.empty((n_cs, h, w), dtype=torch.uint8).pin_memory() for _ in ms]
+            ps_pin = [torch.empty(n_cs, dtype=torch.float64).pin_memory() for _ in ms]
+            h2d = clip_pin.numel()
+            d2h = sum(u.numel() + 8 * p.numel() for u, p in zip(u8_pin, ps_pin))
+            for it in range(warmup + steps):
+                flush.zero_()
+                torch.cuda.synchronize(dev)
+                barrier()
+                e0, e1 = ev_pair()
+                e0.record(stream)
+                B.cs_codec_host(ctx, plan_list, param_list, clip_pin, u8_pin, ps_pin, stream)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                barrier()
+                if it >= warmup:
+                    e2e_ms.append(e0.elapsed_time(e1))
+            # the host path decodes to the same bytes as the device-resident step
+            for i, m in enumerate(ms):
+                assert torch.equal(u8_pin[i], out_u[m].cpu()), "cs_codec_host differs (M=%d)" % m
+    B.cs_ctx_status(ctx)
+
+    def avg(evs):
+        return sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs)
+    res = {"ctx": ctx, "plans": plans, "params": params, "frames": frames, "stream": stream,
+           "keys_dev": keys_dev, "cs_dev": cs_dev, "y_dev": y_dev, "out_f": out_f, "flush": flush,
+           "tuned": tuned, "plan_ms": plan_ms, "autotune_s": autotune_s, "step_ms": step_ms,
+           "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "clocks": clock_info,
+           "launches_per_step": launches_per_step, "dec_ms": avg(dec_ev), "enc_ms": avg(enc_ev),
+           "psnr_ms": avg(psnr_ev), "n_cs": n_cs, "nblk": nblk,
+           "pixels_step": len(ms) * n_cs * h * w,
+           "flops": sum(decode_flops(n_cs * nblk, m, n, iters) for m in ms),
+           "psnr": {str(m): float(np.mean(psnr_dev[m].cpu().numpy())) for m in ms},
+           "enc_bytes": sum(frames.nbytes + 4 * n_cs * nblk * m for m in ms),
+           "psnr_bytes": len(ms) * n_cs * h * w * (1 + 4)}
+    res["tc_used"] = engine == B.CS_ENGINE_TC or (
+        engine == B.CS_ENGINE_AUTO and all(t["engine"] in (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM)
+                                           for t in tuned.values()))
+    res["mixed"], res["mixed_out"] = {}, {}
+    if want_mixed and res["tc_used"]:
+        # the same batched decode with mixed precision: bulk products in one 16-bit
+        # MMA, the last 20 iterations FP32-grade (or split bf16 throughout)
+        for name, prec, tail in (("fp16_tail20", B.CS_FP16, 20), ("bf16_tail20", B.CS_BF16, 20),
+                                 ("bf16x2", B.CS_BF16X2, 0)):
+            mp = [B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops,
+                                lambda_rel=wl["lambda_rel"], engine=engine, precision=prec,
+                                fp32_tail_iters=tail) for m in ms]
+            mo = [torch.empty((n_cs, h, w), dtype=torch.float32, device=dev) for _ in ms]
+            evs = []
+            with torch.cuda.stream(stream):
+                for it in range(2 + 3):
+                    flush.zero_()
+                    a0, a1 = ev_pair()
+                    a0.record(stream)
+                    B.cs_decode_batch(ctx, plan_list, mp, [keys_dev] * len(ms),
+                                      [y_dev[m] for m in ms], mo, None, stream)
+                    a1.record(stream)
+                    if it >= 2:
+                        evs.append((a0, a1))
+                torch.cuda.synchronize(dev)
+            B.cs_ctx_status(ctx)
+            res["mixed"][name] = {"decode_ms_per_step": avg(evs),
+                                  "achieved_tflops": res["flops"] / (avg(evs) / 1e3) / 1e12,
+                                  "vs_fp32_decode": res["dec_ms"] / avg(evs)}
+            res["mixed_out"][name] = {m: mo[i] for i, m in enumerate(ms)}
+    return res
+
+
+def codec_free(B, res):
+    for p in res["plans"].values():
+        B.cs_plan_destroy(p)
+    B.cs_ctx_destroy(res["ctx"])
+
+
+def roofline(flops, ms, peaks, peak_kind, tc_used, clock_info, n_sm, traffic=None):
+    """The decode's achieved algorithmic TFLOP/s against the tensor peak (the
+    measured bf16 burst figure: the decode launch lasts well under a second; the
+    kind::f16 MMAs with fp16 operands run at the bf16 rate), or, on the plain
+    kernel, against the FP32 FMA peak of the SIMT lanes."""
+    achieved = flops / (ms / 1e3) / 1e12
+    if tc_used:
+        peak, bound = peaks["bf16_tflops"], "tensor"
+        src = "%s bf16 dense, burst (MEASURED_PEAKS.json bf16_tflops)" % peak_kind
+    else:
+        clk = clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak, bound = n_sm * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12, "alu"
+        src = "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"
+    return {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": "decode", "peak_source": src}
+
+
+def hbm_kernels(res, peaks):
+    def gbs(ms_, nbytes):
+        return {"ms_per_step": ms_, "bytes_per_step": nbytes, "achieved_gbs": nbytes / (ms_ / 1e3) / 1e9,
+                "peak_gbs": peaks["hbm_gbs"], "frac": nbytes / (ms_ / 1e3) / 1e9 / peaks["hbm_gbs"]}
+    return {"encode": gbs(res["enc_ms"], res["enc_bytes"]), "psnr": gbs(res["psnr_ms"], res["psnr_bytes"]),
+            "note": "algorithmic bytes (each encode call reads the clip once and writes its y; "
+                    "frames re-read by later calls may hit L2)"}
+
+
+def tv_run(B, torch, dev, res, wl, iters, with_oracle):
+    """TV recovery (the paper's TVAL3 regulariser) of the clip at its largest M
+    on the plain per-block kernel, timed once after a warm-up call; the oracle
+    checks the first block row of the first CS frame."""
+    h, w, b = wl["height"], wl["width"], wl["block"]
+    m = max(wl["ms"])
+    n_cs, stream = res["n_cs"], res["stream"]
+    tv_out = torch.empty((n_cs, h, w), dtype=torch.float32, device=dev)
+    with torch.cuda.stream(stream):
+        for it in range(2):
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            B.cs_decode_gop_tv(res["plans"][m], res["params"][m], res["keys_dev"], res["y_dev"][m],
+                               tv_out, None, stream)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+    B.cs_ctx_status(res["ctx"])
+    tv_ms = a0.elapsed_time(a1)
+    tv_psnr = torch.empty(n_cs, dtype=torch.float64, device=dev)
+    B.cs_psnr(res["cs_dev"], tv_out, n_cs, h, w, tv_psnr, stream)
+    torch.cuda.synchronize(dev)
+    out = {"workload": "the clip at M=%d, %d iters, beta=1/8, mu=1, plain FP32 kernel" % (m, iters),
+           "decode_ms": tv_ms, "mpixel_per_s": n_cs * h * w / (tv_ms / 1e3) / 1e6,
+           "psnr_db": float(np.mean(tv_psnr.cpu().numpy()))}
+    if with_oracle:
+        from oracle import cs_oracle as O
+        frames = res["frames"]
+        oplan = O.Plan(b * b, m, wl["seed"])
+        k = min(8, -(-w // b))
+        res1 = frames[1].astype(np.int64) - frames[0].astype(np.int64)
+        y0 = O.blockify(res1.astype(np.float64), b)[:k] @ oplan.phi.T
+        r0 = O.tv_adm(oplan.phi, y0, oplan.lipschitz, iters)
+        rows = min(b, h)
+        full = np.zeros((rows, k * b))
+        for j in range(k):
+            full[:, j * b:(j + 1) * b] = r0[j].reshape(b, b)[:rows]
+        cols = min(k * b, w)
+        want = frames[0][:rows, :cols].astype(np.float64) + full[:, :cols]
+        got = tv_out[0, :rows, :cols].cpu().numpy().astype(np.float64)
+        out["vs_oracle"] = {"sample": "first %d blocks of the first CS frame's first block row" % k,
+                            "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                            "dpsnr_db": float(O.psnr(frames[1][:rows, :cols], got) -
+                                                  O.psnr(frames[1][:rows, :cols], want))}
+    return out
+
+
+def plain_run(B, torch, dev, res, wl):
+    """The plain per-block FP32 decode (one CTA per block group, SIMT) of the
+    same clip, one batched call, timed once after a warm-up call."""
+    h, w, gop, b, iters = wl["height"], wl["width"], wl["gop"], wl["block"], wl["iters"]
+    ms = wl["ms"]
+    n_gops = wl["frames"] // gop
+    stream = res["stream"]
+    pp = [B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops, lambda_rel=wl["lambda_rel"],
+                        engine=B.CS_ENGINE_PLAIN) for m in ms]
+    outs = [torch.empty((res["n_cs"], h, w), dtype=torch.float32, device=dev) for _ in ms]
+    with torch.cuda.stream(stream):
+        for it in range(2):
+            res["flush"].zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            B.cs_decode_batch(res["ctx"], [res["plans"][m] for m in ms], pp,
+                              [res["keys_dev"]] * len(ms), [res["y_dev"][m] for m in ms], outs,
+                              None, stream)
+            a1.record(stream)
+            torch.cuda.synchronize(dev)
+    B.cs_ctx_status(res["ctx"])
+    pms = a0.elapsed_time(a1)
+    err = max(float(torch.linalg.norm(outs[i] - res["out_f"][m]) / torch.linalg.norm(res["out_f"][m]))
+              for i, m in enumerate(ms))
+    return {"engine": "plain FP32 SIMT kernel (CS_ENGINE_PLAIN) at its default launch shape",
+            "decode_ms": pms, "mpixel_per_s": res["pixels_step"] / (pms / 1e3) / 1e6,
+            "achieved_tflops": res["flops"] / (pms / 1e3) / 1e12,
+            "tensor_decode_speedup": pms / res["dec_ms"],
+            "rel_l2_vs_tensor_decode": err}
 
 
 def main():
@@ -424,45 +794,40 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--engine", choices=["auto", "plain", "tc", "tcs"], default="auto")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cif",
-                    help="cif: the CIF M-sweep (default); 720p: 32x32 blocks, M = 102")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
+                    help="720p (default): 32x32 blocks, M = 102; cif: the CIF M-sweep; "
+                         "mixed64: the heterogeneous batch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-m", type=int, default=0,
                     help="run a single M of the sweep (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
     ap.add_argument("--no-batch", action="store_true",
                     help="one decode call per M instead of one batched launch")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="leave out the other workloads (CIF sweep, plain engine, mixed64, serving)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-tv", action="store_true", help="skip the TV-recovery measurement")
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision decode measurement")
-    ap.add_argument("--serving-sweep", action="store_true",
-                    help="sweep the arrival rate to saturation, FP32 and mixed precision")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)  # at least 3 untimed warm-up steps, always
     rank, world, local = dist_env()
     wl = dict(WORKLOADS[args.workload])
-    if args.workload == "mixed64":
-        if args.impl == "reference":
-            if rank == 0:
-                print(json.dumps({"impl": "reference", "unavailable":
-                                  "the oracle arm is measured on the cif and 720p workloads"}))
-            return
-        if rank == 0:
-            run_mixed64(args, wl)
-        return
-    if args.only_m:
+    if args.only_m and args.workload != "mixed64":
         if args.only_m not in wl["ms"]:
             ap.error("--only-m must be one of %s" % wl["ms"])
         wl["ms"] = [args.only_m]
 
-    from paper_1311_1419_gb300 import scenes
-
-    frames = scenes.surveillance_video(wl["frames"], wl["height"], wl["width"], seed=wl["seed"])
-
     if args.impl == "reference":
         if rank == 0:
-            run_reference(args, wl, frames)
+            if args.workload == "mixed64":
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the oracle arm is measured on the 720p and cif workloads"}))
+            else:
+                from paper_1311_1419_gb300 import scenes
+                frames = scenes.surveillance_video(wl["frames"], wl["height"], wl["width"],
+                                                   seed=wl["seed"])
+                run_reference(args, wl, frames)
         return
 
     import torch
@@ -482,302 +847,94 @@ def main():
             import torch.distributed as dist
             dist.barrier()
 
+    peaks, peak_kind = read_peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    if args.workload == "mixed64":
+        if rank == 0:
+            r = run_mixed64(args, wl, B, torch, dev, args.steps, args.warmup)
+            line = dict(r)
+            line.update({"n_gpus": 1, "higher_is_better": True, "scaling": "weak",
+                         "vs_baseline": None, "data": "synthetic",
+                         "config": {"workload": wl["workload"]}})
+            line.pop("workload")
+            print(json.dumps(line), flush=True)
+        return
+
     engine = {"auto": B.CS_ENGINE_AUTO, "plain": B.CS_ENGINE_PLAIN, "tc": B.CS_ENGINE_TC,
               "tcs": B.CS_ENGINE_TC_STREAM}[args.engine]
-    h, w, gop, b, iters = wl["height"], wl["width"], wl["gop"], wl["block"], wl["iters"]
-    n = b * b
-    n_gops = wl["frames"] // gop
-    n_cs = n_gops * (gop - 1)
-    nblk = (-(-h // b)) * (-(-w // b))
-    cs_idx = [t for t in range(wl["frames"]) if t % gop]
+    res = codec_run(wl, B, torch, dev, world, barrier, args.steps, args.warmup, engine,
+                    want_e2e=not args.no_e2e, want_mixed=not args.no_mixed, no_batch=args.no_batch)
+    total_ms = max_over_ranks(sum(res["step_ms"]), world, dev)
+    e2e_total = max_over_ranks(sum(res["e2e_ms"]), world, dev) if res["e2e_ms"] else float("nan")
+    value = job_throughput(world, res["pixels_step"], args.steps, total_ms) / 1e6
+    e2e_value = job_throughput(world, res["pixels_step"], args.steps, e2e_total) / 1e6
+    all_fp32 = all(p.precision == B.CS_FP32 for p in res["params"].values())
+    traffic = DECODE_DRAM_BYTES.get(args.workload) if (
+        res["tc_used"] and all_fp32 and not args.no_batch and not args.only_m) else None
+    roof = roofline(res["flops"], res["dec_ms"], peaks, peak_kind, res["tc_used"], res["clocks"],
+                    n_sm, traffic)
+    mixed = res["mixed"]
+    for name in mixed:
+        mixed[name]["frac"] = mixed[name]["achieved_tflops"] / roof["peak"]
+    solo = rank == 0 and world == 1
+    extras = solo and not args.no_extras
 
-    ctx = B.cs_ctx_create(local)
-    t0 = time.perf_counter()
-    plans = {m: B.cs_make_phi(ctx, n, m, wl["seed"]) for m in wl["ms"]}
-    plan_ms = 1e3 * (time.perf_counter() - t0)
-    params = {m: B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops,
-                               lambda_rel=wl["lambda_rel"], engine=engine) for m in wl["ms"]}
-    # the decode shape of every (N, M) is picked by timing, once, before the timed region
-    tuned = {str(m): dict(zip(("engine", "plain_threads", "plain_blocks_per_cta", "ns_per_block_iter"),
-                              B.cs_autotune(ctx, plans[m]))) for m in wl["ms"]}
-
-    stream = torch.cuda.Stream(dev)
-    frames_dev = torch.from_numpy(frames).to(dev)
-    keys_host = np.ascontiguousarray(frames[::gop])
-    keys_dev = torch.from_numpy(keys_host).to(dev)
-    cs_dev = torch.from_numpy(np.ascontiguousarray(frames[cs_idx])).to(dev)
-    y_dev = {m: torch.empty((n_cs, nblk, m), dtype=torch.float32, device=dev) for m in wl["ms"]}
-    out_f = {m: torch.empty((n_cs, h, w), dtype=torch.float32, device=dev) for m in wl["ms"]}
-    out_u = {m: torch.empty((n_cs, h, w), dtype=torch.uint8, device=dev) for m in wl["ms"]}
-    psnr_dev = {m: torch.empty(n_cs, dtype=torch.float64, device=dev) for m in wl["ms"]}
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    dec_ev = []
-    plan_list = [plans[m] for m in wl["ms"]]
-    param_list = [params[m] for m in wl["ms"]]
-    # our kernels per step: one encode and one PSNR per M, and the decode: one
-    # launch per call with --no-batch, else one per (operand type, shared-memory
-    # layout) group of the 16x16 tensor path (M16 <= 96 or <= 128), one per group
-    # of the 32x32 cluster path, one per group of the streaming path, one per
-    # plain-kernel job (FP32: one operand type)
-    def decode_launches():
-        if args.no_batch:
-            return len(wl["ms"])
-        groups, plain = set(), 0
-        for m in wl["ms"]:
-            m16 = (m + 15) // 16 * 16
-            eng = engine if engine != B.CS_ENGINE_AUTO else tuned[str(m)]["engine"]
-            if eng == B.CS_ENGINE_PLAIN:
-                plain += 1
-            elif eng == B.CS_ENGINE_TC_STREAM:
-                groups.add(("tcs",))
-            elif n == 256:
-                groups.add(("tc", m16 <= 96))
-            else:
-                groups.add(("tc8",))
-                # a large 32x32 job also launches its streaming tail on the SMs whole
-                # clusters leave idle (the library's rule: a tail once the job has more
-                # tiles than clusters x 30; 15 clusters of 8 are co-resident on this part)
-                tiles = -(-(n_cs * nblk) // 128)
-                idle = 2 * (torch.cuda.get_device_properties(dev).multi_processor_count - 8 * 15)
-                if idle > 0 and tiles > 15 * 30:
-                    groups.add(("tc8 tail",))
-        return len(groups) + plain
-    launches_per_step = 2 * len(wl["ms"]) + decode_launches()
-
-    enc_ev, psnr_ev = [], []
-
-    def ev_pair():
-        return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-
-    def step(record_decode: bool, fr, keys):
-        if record_decode:
-            a0, a1 = ev_pair()
-            a0.record(stream)
-        for m in wl["ms"]:
-            B.cs_encode_gop(plans[m], params[m], fr, y_dev[m], stream)
-        if record_decode:
-            a1.record(stream)
-            enc_ev.append((a0, a1))
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-        if args.no_batch:
-            for m in wl["ms"]:
-                B.cs_decode_gop(plans[m], params[m], keys, y_dev[m], out_f[m], out_u[m], stream)
-        else:
-            B.cs_decode_batch(ctx, plan_list, param_list, [keys] * len(wl["ms"]),
-                              [y_dev[m] for m in wl["ms"]], [out_f[m] for m in wl["ms"]],
-                              [out_u[m] for m in wl["ms"]], stream)
-        if record_decode:
-            e1.record(stream)
-            dec_ev.append((e0, e1))
-        if record_decode:
-            c0, c1 = ev_pair()
-            c0.record(stream)
-        for m in wl["ms"]:
-            B.cs_psnr(cs_dev, out_f[m], n_cs, h, w, psnr_dev[m], stream)
-        if record_decode:
-            c1.record(stream)
-            psnr_ev.append((c0, c1))
-
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step(False, frames_dev, keys_dev)
-        torch.cuda.synchronize(dev)
-
-        # device-resident timed region, L2 flushed before every step
-        step_ms = []
-        with ClockSampler(local) as clocks:
-            for _ in range(args.steps):
-                flush.zero_()
-                torch.cuda.synchronize(dev)
-                barrier()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                step(True, frames_dev, keys_dev)
-                e1.record(stream)
-                torch.cuda.synchronize(dev)
-                barrier()
-                step_ms.append(e0.elapsed_time(e1))
-        clock_info = clocks.summary()
-
-        # end to end through the C ABI from pinned host memory
-        frames_pin = torch.from_numpy(frames).pin_memory()
-        keys_pin = torch.from_numpy(keys_host).pin_memory()
-        u8_pin = {m: torch.empty((n_cs, h, w), dtype=torch.uint8).pin_memory() for m in wl["ms"]}
-        ps_pin = {m: torch.empty(n_cs, dtype=torch.float64).pin_memory() for m in wl["ms"]}
-        fr_in = torch.empty_like(frames_dev)
-        key_in = torch.empty_like(keys_dev)
-        h2d = frames_pin.numel() + keys_pin.numel()
-        d2h = sum(u8_pin[m].numel() + 8 * ps_pin[m].numel() for m in wl["ms"])
-        e2e_ms = []
-        for it in range(0 if args.no_e2e else args.warmup + args.steps):
-            flush.zero_()
-            torch.cuda.synchronize(dev)
-            barrier()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fr_in.copy_(frames_pin, non_blocking=True)
-            key_in.copy_(keys_pin, non_blocking=True)
-            step(False, fr_in, key_in)
-            for m in wl["ms"]:
-                u8_pin[m].copy_(out_u[m], non_blocking=True)
-                ps_pin[m].copy_(psnr_dev[m], non_blocking=True)
-            e1.record(stream)
-            torch.cuda.synchronize(dev)
-            barrier()
-            if it >= args.warmup:
-                e2e_ms.append(e0.elapsed_time(e1))
-
-    total_ms = max_over_ranks(sum(step_ms), world, dev)
-    e2e_total = max_over_ranks(sum(e2e_ms), world, dev) if e2e_ms else float("nan")
-    pixels_step = len(wl["ms"]) * n_cs * h * w
-    value = job_throughput(world, pixels_step, args.steps, total_ms) / 1e6
-    e2e_value = job_throughput(world, pixels_step, args.steps, e2e_total) / 1e6
-
-    # roofline of the dominant kernel (the decode), from its own launch events
-    dec_ms = sum(a.elapsed_time(b_) for a, b_ in dec_ev) / len(dec_ev)
-    blocks = n_cs * nblk
-    flops = sum(decode_flops(blocks, m, n, iters) for m in wl["ms"])
-    peaks, peak_kind = read_peaks()
-    # the tensor-core roofline applies when every plan decodes on the tensor cores
-    tc_used = engine == B.CS_ENGINE_TC or (
-        engine == B.CS_ENGINE_AUTO and all(t["engine"] == B.CS_ENGINE_TC for t in tuned.values()))
-    achieved = flops / (dec_ms / 1e3) / 1e12
-    # the captured traffic belongs to the CIF sweep's batched FP32 tensor-core decode only
-    traffic = CIF_DECODE_DRAM_BYTES if (tc_used and args.workload == "cif" and not args.no_batch
-                                        and not args.only_m and
-                                        all(p.precision == B.CS_FP32 for p in params.values())) else None
-    if tc_used:
-        # kind::f16 MMAs (fp16 operands): the measured bf16 peak x the nominal
-        # fp16:bf16 ratio of 1; sustained, as the decode runs inside a long step
-        peak = peaks["bf16_tflops_sustained"]
-        bound = "tensor"
-    else:
-        clk = clock_info.get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        peak = n_sm * FP32_LANES_PER_SM * 2 * clk * 1e6 / 1e12
-        bound = "alu"
-    psnr = {m: float(np.mean(psnr_dev[m].cpu().numpy())) for m in wl["ms"]}
-
-    # the HBM-bound kernels beside the decode: encode (frames in, y out, per M) and
-    # the PSNR tail (uint8 reference + float32 frames in), achieved algorithmic GB/s
-    def gbs(evs, nbytes):
-        ms_ = sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs)
-        return {"ms_per_step": ms_, "bytes_per_step": nbytes, "achieved_gbs": nbytes / (ms_ / 1e3) / 1e9,
-                "peak_gbs": peaks["hbm_gbs"], "frac": nbytes / (ms_ / 1e3) / 1e9 / peaks["hbm_gbs"]}
-    enc_bytes = sum(frames.nbytes + 4 * n_cs * nblk * m for m in wl["ms"])
-    psnr_bytes = len(wl["ms"]) * n_cs * h * w * (1 + 4)
-    hbm_kernels = {"encode": gbs(enc_ev, enc_bytes), "psnr": gbs(psnr_ev, psnr_bytes),
-                   "note": "algorithmic bytes (each encode call reads the clip once and writes "
-                           "its y; frames re-read by later calls may hit L2)"}
-
-    # the same batched decode with mixed precision: bulk products in one 16-bit
-    # MMA, the last 20 iterations FP32-grade (or split bf16 throughout)
-    mixed, mixed_out = None, {}
-    if tc_used and not args.no_mixed:
-        mixed = {}
-        for name, prec, tail in (("fp16_tail20", B.CS_FP16, 20), ("bf16_tail20", B.CS_BF16, 20),
-                                 ("bf16x2", B.CS_BF16X2, 0)):
-            mp = [B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops,
-                                lambda_rel=wl["lambda_rel"], engine=engine, precision=prec,
-                                fp32_tail_iters=tail) for m in wl["ms"]]
-            mo = [torch.empty((n_cs, h, w), dtype=torch.float32, device=dev) for _ in wl["ms"]]
-            evs = []
-            with torch.cuda.stream(stream):
-                for it in range(2 + 3):
-                    flush.zero_()
-                    a0 = torch.cuda.Event(enable_timing=True)
-                    a1 = torch.cuda.Event(enable_timing=True)
-                    a0.record(stream)
-                    B.cs_decode_batch(ctx, plan_list, mp, [keys_dev] * len(wl["ms"]),
-                                      [y_dev[m] for m in wl["ms"]], mo, None, stream)
-                    a1.record(stream)
-                    if it >= 2:
-                        evs.append((a0, a1))
-                torch.cuda.synchronize(dev)
-            B.cs_ctx_status(ctx)
-            mms = sum(a.elapsed_time(b_) for a, b_ in evs) / len(evs)
-            ach = flops / (mms / 1e3) / 1e12
-            mixed[name] = {"decode_ms_per_step": mms, "achieved_tflops": ach,
-                           "frac": ach / peak,
-                           "vs_fp32_decode": dec_ms / mms}
-            mixed_out[name] = {m: mo[i] for i, m in enumerate(wl["ms"])}
-
-    # TV recovery (the paper's TVAL3 regulariser) on the plain per-block kernel:
-    # the clip at the largest M, timed once after a warm-up call
     tv = None
-    tv_m = max(wl["ms"])
-    if not args.no_tv and args.engine != "tc":
-        tv_out = torch.empty((n_cs, h, w), dtype=torch.float32, device=dev)
-        with torch.cuda.stream(stream):
-            B.cs_decode_gop_tv(plans[tv_m], params[tv_m], keys_dev, y_dev[tv_m], tv_out, None, stream)
-            torch.cuda.synchronize(dev)
-            a0, a1 = ev_pair()
-            a0.record(stream)
-            B.cs_decode_gop_tv(plans[tv_m], params[tv_m], keys_dev, y_dev[tv_m], tv_out, None, stream)
-            a1.record(stream)
-            torch.cuda.synchronize(dev)
-        B.cs_ctx_status(ctx)
-        tv_ms = a0.elapsed_time(a1)
-        tv_psnr = torch.empty(n_cs, dtype=torch.float64, device=dev)
-        B.cs_psnr(cs_dev, tv_out, n_cs, h, w, tv_psnr, stream)
-        torch.cuda.synchronize(dev)
-        tv = {"workload": "the clip at M=%d, %d iters, beta=1/8, mu=1, plain FP32 kernel" % (tv_m, iters),
-              "decode_ms": tv_ms, "mpixel_per_s": n_cs * h * w / (tv_ms / 1e3) / 1e6,
-              "psnr_db": float(np.mean(tv_psnr.cpu().numpy()))}
+    if not args.no_tv and args.engine != "tc" and rank == 0:
+        tv = tv_run(B, torch, dev, res, wl, wl["iters"], with_oracle=solo and not args.no_cpu_baseline)
+    plain = plain_run(B, torch, dev, res, wl) if (extras and res["tc_used"]) else None
+
+    cif = None
+    if extras and args.workload != "cif":
+        cwl = dict(WORKLOADS["cif"])
+        cres = codec_run(cwl, B, torch, dev, 1, barrier, 5, 3, B.CS_ENGINE_AUTO, want_e2e=False,
+                         want_mixed=False)
+        cif = {"workload": cwl["workload"], "steps": 5, "warmup": 3,
+               "value": cres["pixels_step"] * 5 / (sum(cres["step_ms"]) / 1e3) / 1e6,
+               "unit": "Mpixel/s", "ms_per_step": sum(cres["step_ms"]) / 5,
+               "decode_ms_per_step": cres["dec_ms"], "decode_gflop_per_step": cres["flops"] / 1e9,
+               "roofline": roofline(cres["flops"], cres["dec_ms"], peaks, peak_kind, cres["tc_used"],
+                                    cres["clocks"], n_sm, DECODE_DRAM_BYTES["cif"]),
+               "gpu_launches": cres["launches_per_step"] * 5, "psnr_db": cres["psnr"]}
+        if not args.no_cpu_baseline:
+            _, _, cref = oracle_sample(cres["frames"], cwl, cwl["oracle_frames"])
+            cif["parity_vs_oracle"] = {
+                str(m): parity(cres["frames"],
+                               cres["out_f"][m][:cwl["oracle_frames"]].cpu().numpy().astype(np.float64),
+                               cref[m]) for m in cwl["ms"]}
+        codec_free(B, cres)
+
+    mixed64 = None
+    if extras:
+        mwl = dict(WORKLOADS["mixed64"])
+        mixed64 = run_mixed64(args, mwl, B, torch, dev, 3, 3, with_oracle=not args.no_cpu_baseline)
 
     serving = None
-    if rank == 0 and world == 1 and not args.no_serving:
-        rates = [50, 100, 200, 300, 400, 600] if args.serving_sweep else [100]
-        secs = 3.0 if args.serving_sweep else 2.0
+    if solo and not args.no_serving:
+        rates = [50, 100, 200, 400] if extras else [100]
         serving = {"workload": SERVING["workload"],
-                   "fp32": serving_run(B, torch, dev, B.CS_FP32, 0, rates, secs)}
-        if args.serving_sweep:
-            serving["fp16_tail20"] = serving_run(B, torch, dev, B.CS_FP16, 20, rates, secs)
+                   "fp32": serving_run(B, torch, dev, B.CS_FP32, 0, rates, 2.0)}
+        if extras:
+            serving["fp16_tail20"] = serving_run(B, torch, dev, B.CS_FP16, 20, [200, 400], 2.0)
 
-    cpu = None
-    parity = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    cpu = parity_d = None
+    if solo and not args.no_cpu_baseline:
         n_sample = wl["oracle_frames"]
-        secs, pix, ref = oracle_sample(frames, wl, n_sample)
+        secs, pix, ref = oracle_sample(res["frames"], wl, n_sample)
+        nblk = res["nblk"]
         cpu = {"value": pix / secs / 1e6, "unit": "Mpixel/s", "cores": os.cpu_count(),
                "kind": "oracle",
-               "sample": "first %d CS frames (%d blocks) at each M in %s, %d iters; numpy "
+               "sample": "first %d CS frame(s) (%d blocks) at each M in %s, %d iters; numpy "
                          "FP64 (BLAS threads = cores)" % (n_sample, n_sample * nblk, wl["ms"],
-                                                          iters)}
-        from oracle import cs_oracle as O
-        parity = {}
-        for m in wl["ms"]:
-            got = out_f[m][:n_sample].cpu().numpy().astype(np.float64)
-            want = ref[m]
-            orig = frames[1:1 + n_sample]
-            parity[str(m)] = {
-                "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
-                "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want)),
-            }
-        for name, outs in mixed_out.items():
-            errs = {}
-            for m in wl["ms"]:
-                got = outs[m][:n_sample].cpu().numpy().astype(np.float64)
-                want = ref[m]
-                orig = frames[1:1 + n_sample]
-                errs[str(m)] = {
-                    "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
-                    "dpsnr_db": float(O.psnr(orig, got) - O.psnr(orig, want))}
-            mixed[name]["vs_oracle"] = errs
-        if tv is not None:
-            # the oracle's TV decode of the first CS frame
-            oplan = O.Plan(n, tv_m, wl["seed"])
-            y0 = O.encode(oplan, frames[:gop], gop)[:1]
-            r0 = O.tv_adm(oplan.phi, y0[0], oplan.lipschitz, iters)
-            want = frames[0].astype(np.float64) + O.unblockify(r0, h, w, b)
-            got = tv_out[0].cpu().numpy().astype(np.float64)
-            tv["vs_oracle"] = {"frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
-                               "dpsnr_db": float(O.psnr(frames[1:2], got[None]) -
-                                                 O.psnr(frames[1:2], want[None]))}
+                                                          wl["iters"])}
+        parity_d = {str(m): parity(res["frames"],
+                                   res["out_f"][m][:n_sample].cpu().numpy().astype(np.float64), ref[m])
+                    for m in wl["ms"]}
+        parity_d["sample"] = "first %d CS frame(s), every block, FP64 oracle" % n_sample
+        for name, outs in res["mixed_out"].items():
+            mixed[name]["vs_oracle"] = {
+                str(m): parity(res["frames"], outs[m][:n_sample].cpu().numpy().astype(np.float64), ref[m])
+                for m in wl["ms"]}
 
     if rank == 0:
         line = {
@@ -790,33 +947,30 @@ def main():
                        "one batched launch (%d plans)" % len(wl["ms"]),
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "replicas x%d" % world},
-            "roofline": {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "decode",
-                         "peak_source": ("%s bf16 dense, sustained" % peak_kind) if bound == "tensor"
-                         else "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"},
+            "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": None if not e2e_ms else {
-                "value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
-            "gpu_launches": launches_per_step * args.steps,
-            "clocks": clock_info,
-            "plan_ms": plan_ms,
-            "autotune": tuned,
-            "decode_ms_per_step": dec_ms,
-            "decode_gflop_per_step": flops / 1e9,
-            "psnr_db": {str(m): psnr[m] for m in wl["ms"]},
-            "parity_vs_oracle": parity,
-            "mixed_precision": mixed,
-            "hbm_kernels": hbm_kernels,
+            "e2e": None if not res["e2e_ms"] else {
+                "value": e2e_value, "unit": "Mpixel/s", "h2d_bytes_per_step": res["h2d"],
+                "d2h_bytes_per_step": res["d2h"], "entry_point": "cs_codec_host"},
+            "gpu_launches": res["launches_per_step"] * args.steps,
+            "clocks": res["clocks"],
+            "plan_ms": res["plan_ms"],
+            "autotune": res["tuned"],
+            "decode_ms_per_step": res["dec_ms"],
+            "decode_gflop_per_step": res["flops"] / 1e9,
+            "psnr_db": res["psnr"],
+            "parity_vs_oracle": parity_d,
+            "mixed_precision": mixed or None,
+            "hbm_kernels": hbm_kernels(res, peaks),
+            "plain_engine": plain,
+            "cif_sweep": cif,
+            "mixed64": mixed64,
             "tv_recovery": tv,
             "serving": serving,
         }
         print(json.dumps(line), flush=True)
 
-    for p in plans.values():
-        B.cs_plan_destroy(p)
-    B.cs_ctx_destroy(ctx)
+    codec_free(B, res)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

@@ -239,6 +239,28 @@ int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t
               const float* y_host, uint8_t* frames_u8_host, uint64_t* ticket);
 int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms);
 
+/* ---- the whole codec of a clip, host memory in and out ------------------------
+ * cs_codec_host: encode a clip and decode it again under n_plans plans, from
+ * and to HOST memory (Sec. 3: key + CS frames per GOP; Sec. 3.1: every CS
+ * frame's residual measured per block; Sec. 3.2, Eqs. 1-4: every residual block
+ * recovered and added back to its key; Sec. 4: PSNR of the decoded frames).
+ * clip_host: uint8 [n_gops*G][H][W]; every params[i] must give the same H, W,
+ * G and n_gops, and its block and M must match plans[i].  The clip is copied to
+ * the device once; each plan measures it as cs_encode_gop does; all plans'
+ * measurements are decoded in one cs_decode_batch call (results identical to
+ * cs_decode_gop); each decoded CS frame is scored against the original with
+ * cs_psnr.  Outputs per plan i: frames_u8_host[i], uint8 [n_gops*(G-1)][H][W]
+ * (the decoded CS frames in clip order, keys left out), and psnr_host[i],
+ * double [n_gops*(G-1)].  Device staging belongs to the context: one buffer
+ * that grows with the largest call so far (a cudaMalloc, after the previous
+ * call using it has finished); calls on different streams take turns on it.
+ * Enqueues on `stream` and returns; the host buffers must stay valid until the
+ * stream has passed the call (pinned memory makes the copies asynchronous).
+ * Errors as the calls it makes; CS_EINVAL for mismatched shapes. */
+int cs_codec_host(cs_ctx* ctx, int32_t n_plans, cs_plan* const* plans, const cs_params* params,
+                  const uint8_t* clip_host, uint8_t* const* frames_u8_host,
+                  double* const* psnr_host, cs_stream_t stream);
+
 /* ---- allocation-free Lipschitz estimate -------------------------------------
  * The paper has no counterpart to this call; it is a service for callers that
  * must not allocate device memory: a serving process whose HBM was reserved

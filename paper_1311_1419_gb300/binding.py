@@ -85,6 +85,8 @@ _SIGS = {
                                  ctypes.POINTER(ctypes.c_uint64)]),
     "cs_poll": (ctypes.c_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_i32),
                                ctypes.POINTER(ctypes.c_float)]),
+    "cs_codec_host": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(cs_params),
+                                     _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     "cs_lambda_max_noalloc": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp]),
     "cs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "cs_last_error": (ctypes.c_char_p, []),
@@ -275,6 +277,19 @@ def cs_poll(ctx: int, ticket: int):
     lat = ctypes.c_float()
     _check(load().cs_poll(ctx, int(ticket), ctypes.byref(done), ctypes.byref(lat)))
     return bool(done.value), float(lat.value)
+
+
+def cs_codec_host(ctx: int, plans, params, clip_host, frames_u8_host, psnr_host,
+                  stream=None) -> None:
+    """Encode + batched decode + PSNR of one clip under every plan, host memory
+    in and out; sequences of equal length (host buffers as arrays, CPU tensors
+    or ints)."""
+    n = len(plans)
+    pl = (_vp * n)(*plans)
+    pa = (cs_params * n)(*params)
+    fu = (_vp * n)(*[_host_ptr(x) for x in frames_u8_host])
+    ps = (_vp * n)(*[_host_ptr(x) for x in psnr_host])
+    _check(load().cs_codec_host(ctx, n, pl, pa, _host_ptr(clip_host), fu, ps, _stream(stream)))
 
 
 def cs_lambda_max_noalloc(phi_dev, n: int, m: int, lambda_max_dev, stream=None) -> None:

@@ -218,6 +218,7 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
     if (e == cudaSuccess) e = cudaMemset(ctx->err_dev, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&ctx->counters_dev, sizeof(int) * kTileCounters);
     if (e == cudaSuccess) e = slot_ring_init(&ctx->counter_ring, kTileCounters);
+    if (e == cudaSuccess) e = slot_ring_init(&ctx->stage_ring, 1);
     for (int i = 0; e == cudaSuccess && i < 8; ++i) {
         cudaStream_t s;
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -259,6 +260,8 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     slot_ring_destroy(&ctx->counter_ring);
     slot_ring_destroy(&ctx->tc8_ring);
     slot_ring_destroy(&ctx->tcs_ring);
+    slot_ring_destroy(&ctx->stage_ring);
+    if (ctx->stage) cudaFree(ctx->stage);
     delete ctx;
     return CS_OK;
 }

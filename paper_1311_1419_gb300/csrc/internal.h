@@ -72,6 +72,11 @@ struct cs_ctx {
     size_t scratch_bytes = 0;           // tc8_scratch + tcs_scratch
     std::mutex launch_mu;               // held from slot_take to slot_done
     csvc::SlotRing counter_ring, tc8_ring, tcs_ring;
+    // device staging of cs_codec_host (grown on demand), one holder at a time
+    std::mutex stage_mu;
+    uint8_t* stage = nullptr;
+    size_t stage_bytes = 0;
+    csvc::SlotRing stage_ring;
     std::atomic<int> debug_flags{0};        // CS_DEBUG_*, consumed by the next launch
     // autotuned decode shape per (N, M): engine, plain-kernel threads and blocks per CTA
     std::mutex tune_mu;

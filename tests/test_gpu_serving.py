@@ -26,7 +26,8 @@ CAMERAS = [  # (h, w, gop, m, iters, precision, tail, seed, block)
     (96, 128, 8, 13, 100, 3, 20, 13, 16),
     (144, 176, 5, 51, 40, 0, 0, 14, 16),
     (288, 352, 4, 102, 40, 0, 0, 15, 32),    # the 8-CTA cluster kernel
-    (160, 192, 3, 200, 30, 0, 0, 16, 32),    # the plain kernel (M > 128)
+    (160, 192, 3, 200, 30, 0, 0, 16, 32),    # M > 128: the streaming kernel's scratch does not
+                                             # fit this context's budget, so the plain kernel
 ]
 
 

@@ -51,3 +51,28 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(B):
         B.cs_lambda_max_noalloc(phi, 300, 257, out)
     assert ei.value.status == B.CS_EINVAL
     assert "256" in B.cs_last_error()
+
+
+def test_noalloc_calls_leave_device_memory_unchanged(B):
+    """After a first call (which looks up the array's address), further calls
+    change neither the device's free memory nor torch's allocations: nothing
+    is allocated and kept."""
+    ctx = B.cs_ctx_create(0)
+    plan = B.cs_make_phi(ctx, 256, 96, 5)
+    try:
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        phi = B.cs_plan_phi(plan)
+        B.cs_lambda_max_noalloc(phi, 256, 96, out)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
+        for _ in range(3):
+            B.cs_lambda_max_noalloc(phi, 256, 96, out)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0
+        assert torch.cuda.memory_allocated() == alloc0
+        assert 1.0001 * out.item() == pytest.approx(B.cs_plan_lipschitz(plan), rel=1e-10)
+    finally:
+        B.cs_plan_destroy(plan)
+        B.cs_ctx_destroy(ctx)
