@@ -37,6 +37,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "cluster_ptx.h"
 #include "internal.h"
 #include "tc_ptx.h"
 
@@ -118,94 +119,6 @@ struct Tc8Launch {
 
 namespace {
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t cluster_id() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t n_clusters() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
-// Address of the same shared-memory location in CTA `rank` of the cluster.
-__device__ __forceinline__ uint32_t mapa(uint32_t saddr, uint32_t rank) {
-    uint32_t d;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(d) : "r"(saddr), "r"(rank));
-    return d;
-}
-// Every thread of every CTA of the cluster; global and shared writes before it
-// are visible to every thread of the cluster after it.
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile(
-        "fence.acq_rel.gpu;\n\t"
-        "barrier.cluster.arrive.release.aligned;\n\t"
-        "barrier.cluster.wait.acquire.aligned;\n\t"
-        "fence.acq_rel.gpu;" ::: "memory");
-}
-__device__ __forceinline__ void st_async_u32(uint32_t raddr, uint32_t v, uint32_t rbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(
-                     raddr),
-                 "r"(v), "r"(rbar)
-                 : "memory");
-}
-// Bulk copy of this CTA's shared memory into a peer's (addresses from mapa),
-// completion counted in bytes on the peer's barrier.
-__device__ __forceinline__ void bulk_s2peer(uint32_t rdst, uint32_t src, uint32_t bytes, uint32_t rbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            rdst),
-        "r"(src), "r"(bytes), "r"(rbar)
-        : "memory");
-}
-
-template <bool BF>
-__device__ __forceinline__ uint32_t pack2(float2 v) {
-    if constexpr (BF) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(v.x, v.y);
-        return *reinterpret_cast<uint32_t*>(&h);
-    } else {
-        __half2 h = __floats2half2_rn(v.x, v.y);
-        return *reinterpret_cast<uint32_t*>(&h);
-    }
-}
-template <bool BF>
-__device__ __forceinline__ float2 unpack2(uint32_t v) {
-    if constexpr (BF) {
-        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
-        return __bfloat1622float2(h);
-    } else {
-        __half2 h = *reinterpret_cast<__half2*>(&v);
-        return __half22float2(h);
-    }
-}
-template <bool BF>
-__device__ __forceinline__ uint16_t pack1(float v) {
-    if constexpr (BF) {
-        __nv_bfloat16 h = __float2bfloat16_rn(v);
-        return *reinterpret_cast<uint16_t*>(&h);
-    } else {
-        __half h = __float2half_rn(v);
-        return *reinterpret_cast<uint16_t*>(&h);
-    }
-}
-template <bool BF>
-__device__ __forceinline__ float unpack1(uint16_t v) {
-    if constexpr (BF) {
-        return __bfloat162float(*reinterpret_cast<__nv_bfloat16*>(&v));
-    } else {
-        return __half2float(*reinterpret_cast<__half*>(&v));
-    }
-}
-__device__ __forceinline__ float2 u2f2(uint32_t a, uint32_t b) {
-    return make_float2(__uint_as_float(a), __uint_as_float(b));
-}
-
 __device__ __forceinline__ bool wait_bar(Misc8* ms, uint64_t* bar, uint32_t parity, int* err) {
     if (*(volatile int*)&ms->abort) return false;
     if (mbar_wait(bar, parity, kWaitNs)) return true;
@@ -217,31 +130,6 @@ __device__ __forceinline__ void cta_sync() {
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-}
-
-// Owner of measurement rows: the m16 / 8 row groups are dealt to the 8 CTAs,
-// the first (groups % 8) CTAs taking one more.
-__device__ __forceinline__ void owner_rows(int p, int m16, int* row0, int* rows) {
-    const int groups = m16 / 8, base = groups / kCl, extra = groups % kCl;
-    const int ng = base + (p < extra ? 1 : 0);
-    const int g0 = p * base + (p < extra ? p : extra);
-    *row0 = 8 * g0;
-    *rows = 8 * ng;
-}
-// Owner of measurement row m (inverse of owner_rows).
-__device__ __forceinline__ int owner_of(int m, int m16) {
-    const int groups = m16 / 8, base = groups / kCl, extra = groups % kCl;
-    const int g = m >> 3, big = extra * (base + 1);
-    return g < big ? g / (base + 1) : extra + (g - big) / base;
-}
-// Slot of sender s in receiver r's incoming buffers (s != r): 0 .. 6.
-__device__ __forceinline__ int slot_of(int s, int r) { return (s - r + kCl - 1) % kCl; }
-
-// Byte offset of P[b][m] in the MN-major operand: 8-row groups 2 KB apart, two
-// 64-block atoms of 1 KB in each, 128-byte swizzle inside the atom.
-__device__ __forceinline__ uint32_t p_off(uint32_t b, uint32_t m) {
-    return (m >> 3) * 2048u + (b >> 6) * 1024u + (m & 7u) * 128u + ((((b & 63u) >> 3) ^ (m & 7u)) << 4) +
-           ((b & 7u) << 1);
 }
 
 template <bool BF>
@@ -399,7 +287,10 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
         if (J.iters > 0 && lane == 0) {
             // incoming data of iteration 0 and the tile's lambda exchange
             mbar_arrive_expect_tx(&ms->bar_lam, (kCl - 1) * kTile * 4);
-            mbar_arrive_expect_tx(&ms->bar_urecv, (uint32_t)((kCl - 1) * rows_q * kTile * 4));
+            // a CTA that owns no measurement rows receives no partials: its barrier
+            // is never armed (an arming of 0 bytes would complete at once, and two
+            // such phases could pass before the epilogue looked)
+            if (rows_q > 0) mbar_arrive_expect_tx(&ms->bar_urecv, (uint32_t)((kCl - 1) * rows_q * kTile * 4));
             const uint32_t pb = (uint32_t)((J.m16 - rows_q) * kTile * 2) * (0 >= J.split_from ? 2u : 1u);
             mbar_arrive_expect_tx(&ms->bar_precv, pb);
         }
@@ -430,10 +321,12 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             }
             __syncwarp();
             // this CTA's rows have all their partials: arm the next iteration's
-            ok = wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err) && ok;
-            ph_urecv ^= 1;
-            if (k + 1 < J.iters && lane == 0)
-                mbar_arrive_expect_tx(&ms->bar_urecv, (uint32_t)((kCl - 1) * rows_q * kTile * 4));
+            if (rows_q > 0) {
+                ok = wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err) && ok;
+                ph_urecv ^= 1;
+                if (k + 1 < J.iters && lane == 0)
+                    mbar_arrive_expect_tx(&ms->bar_urecv, (uint32_t)((kCl - 1) * rows_q * kTile * 4));
+            }
             __syncwarp();
             // this CTA's residual rows are written: broadcast them
             ok = wait_bar(ms, &ms->bar_pown, ph_pown, L.err) && ok;
@@ -586,8 +479,10 @@ __device__ __forceinline__ void epi_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             __syncwarp();
             if (lane == 0) mbar_arrive(&ms->bar_stage);
             // --- residual rows of this CTA: P = (U su - y) sp ---
-            wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err);
-            ph_urecv ^= 1;
+            if (rows_q > 0) {
+                wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err);
+                ph_urecv ^= 1;
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (i >= per_q) break;
