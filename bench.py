@@ -180,9 +180,13 @@ SERVING = {
 }
 
 
-def serving_run(B, torch, dev, precision, tail, rates, seconds, hbm_budget=8 << 30):
-    """Open-loop serving: Poisson arrivals over the camera mix at each rate;
-    returns one dict per rate (p50/p99 latency, Mpixel/s, admitted, refused)."""
+def serving_run(B, torch, dev, configs, rates, seconds, hbm_budget=8 << 30, batch_ref=True):
+    """Open-loop serving: Poisson arrivals over the camera mix.  configs: list of
+    (name, serving mode, precision, FP32-grade tail); every config runs every
+    rate on the same cameras.  Returns {name: [one dict per rate: p50/p99
+    latency, Mpixel/s, admitted, refused]}, plus, with batch_ref, the same
+    cameras' GOPs decoded in one cs_decode_batch per precision (the throughput
+    the serving loop is compared with)."""
     from paper_1311_1419_gb300 import scenes
 
     rng = np.random.default_rng(SERVING["seed"])
@@ -191,6 +195,7 @@ def serving_run(B, torch, dev, precision, tail, rates, seconds, hbm_budget=8 << 
     ctx = B.cs_ctx_create(dev.index, hbm_budget)
     cams = []
     stream = torch.cuda.Stream(dev)
+    out = {}
     try:
         for cid in range(SERVING["cameras"]):
             h, w = res[rng.choice(4, p=[0.4, 0.3, 0.2, 0.1])]
@@ -198,72 +203,98 @@ def serving_run(B, torch, dev, precision, tail, rates, seconds, hbm_budget=8 << 
             b = (16, 32)[rng.integers(2)]
             m = max(1, int(np.rint(b * b * rng.uniform(0.05, 0.25))))
             plan = B.cs_make_phi(ctx, b * b, m, cid)
-            tc = (m + 15) // 16 * 16 <= 512       # on-chip or streaming tensor-core kernel
-            p = B.make_params(h, w, gop, b, m, iters=SERVING["iters"],
-                              precision=precision if tc else B.CS_FP32,
-                              fp32_tail_iters=tail if tc else 0)
             off = cid % (33 - gop)
             clip = base[(h, w)][off:off + gop]
             nblk = (-(-h // b)) * (-(-w // b))
+            p32 = B.make_params(h, w, gop, b, m, iters=SERVING["iters"])
             y = torch.empty((gop - 1, nblk, m), dtype=torch.float32, device=dev)
-            B.cs_encode_gop(plan, p, torch.from_numpy(np.ascontiguousarray(clip)).to(dev), y,
-                            stream)
+            B.cs_encode_gop(plan, p32, torch.from_numpy(np.ascontiguousarray(clip)).to(dev), y, stream)
             stream.synchronize()
-            cams.append({"plan": plan, "p": p, "key": torch.from_numpy(
-                np.ascontiguousarray(clip[:1])).pin_memory(), "y": y.cpu().pin_memory(),
-                "shape": (gop - 1, h, w), "pixels": (gop - 1) * h * w, "free": []})
-        results = []
-        for rate in rates:
-            t_next = 0.0
-            arrivals = []
-            while t_next < seconds:
-                t_next += rng.exponential(1.0 / rate)
-                arrivals.append((t_next, int(rng.integers(len(cams)))))
-            inflight, lat, pixels, refused = {}, [], 0, 0
-            backlog = []
-            t0 = time.perf_counter()
-            i = 0
-            while i < len(arrivals) or backlog or inflight:
-                now = time.perf_counter() - t0
-                while i < len(arrivals) and arrivals[i][0] <= now:
-                    backlog.append((arrivals[i][1], t0 + arrivals[i][0]))
-                    i += 1
-                while backlog:                      # admit as slots and memory free up
-                    c = cams[backlog[0][0]]
-                    out = c["free"].pop() if c["free"] else torch.empty(
-                        c["shape"], dtype=torch.uint8).pin_memory()
-                    try:
-                        t = B.cs_submit(ctx, c["plan"], c["p"], c["key"], c["y"], out)
-                    except B.CsError as e:
-                        c["free"].append(out)
-                        if e.status != B.CS_EAGAIN:
-                            raise
-                        refused += 1
-                        break
-                    cid, t_arr = backlog.pop(0)
-                    inflight[t] = (cid, out, time.perf_counter() - t_arr)
-                for t in list(inflight):
-                    done, ms = B.cs_poll(ctx, t)
-                    if done:
-                        cid, out, queued = inflight.pop(t)
-                        # arrival to completion: admission queueing + submit-to-done
-                        lat.append(1e3 * queued + ms)
-                        pixels += cams[cid]["pixels"]
-                        cams[cid]["free"].append(out)
-            wall = time.perf_counter() - t0
-            B.cs_ctx_status(ctx)
-            lat_ms = np.array(lat)
-            results.append({"rate_per_s": rate, "requests": len(lat), "refused_retries": refused,
-                            "p50_ms": float(np.percentile(lat_ms, 50)),
-                            "p99_ms": float(np.percentile(lat_ms, 99)),
-                            "mpixel_per_s": pixels / wall / 1e6})
-        return results
+            cams.append({"plan": plan, "dims": (h, w, gop, b, m), "y_dev": y,
+                         "key_dev": torch.from_numpy(np.ascontiguousarray(clip[:1])).to(dev),
+                         "key": torch.from_numpy(np.ascontiguousarray(clip[:1])).pin_memory(),
+                         "y": y.cpu().pin_memory(), "shape": (gop - 1, h, w),
+                         "pixels": (gop - 1) * h * w, "free": []})
+
+        def params(c, precision, tail):
+            h, w, gop, b, m = c["dims"]
+            return B.make_params(h, w, gop, b, m, iters=SERVING["iters"], precision=precision,
+                                 fp32_tail_iters=tail)
+
+        for name, mode, precision, tail in configs:
+            B.cs_ctx_set_serving(ctx, mode)
+            prm = [params(c, precision, tail) for c in cams]
+            rows = []
+            for rate in rates:
+                t_next = 0.0
+                arrivals = []
+                while t_next < seconds:
+                    t_next += rng.exponential(1.0 / rate)
+                    arrivals.append((t_next, int(rng.integers(len(cams)))))
+                inflight, lat, pixels, refused = {}, [], 0, 0
+                backlog = []
+                t0 = time.perf_counter()
+                i = 0
+                while i < len(arrivals) or backlog or inflight:
+                    now = time.perf_counter() - t0
+                    while i < len(arrivals) and arrivals[i][0] <= now:
+                        backlog.append((arrivals[i][1], t0 + arrivals[i][0]))
+                        i += 1
+                    while backlog:                      # admit as slots and memory free up
+                        c = cams[backlog[0][0]]
+                        o = c["free"].pop() if c["free"] else torch.empty(
+                            c["shape"], dtype=torch.uint8).pin_memory()
+                        try:
+                            t = B.cs_submit(ctx, c["plan"], prm[backlog[0][0]], c["key"], c["y"], o)
+                        except B.CsError as e:
+                            c["free"].append(o)
+                            if e.status != B.CS_EAGAIN:
+                                raise
+                            refused += 1
+                            break
+                        cid, t_arr = backlog.pop(0)
+                        inflight[t] = (cid, o, time.perf_counter() - t_arr)
+                    for t in list(inflight):
+                        done, ms = B.cs_poll(ctx, t)
+                        if done:
+                            cid, o, queued = inflight.pop(t)
+                            # arrival to completion: admission queueing + submit-to-done
+                            lat.append(1e3 * queued + ms)
+                            pixels += cams[cid]["pixels"]
+                            cams[cid]["free"].append(o)
+                wall = time.perf_counter() - t0
+                B.cs_ctx_status(ctx)
+                lat_ms = np.array(lat)
+                rows.append({"rate_per_s": rate, "requests": len(lat), "refused_retries": refused,
+                             "p50_ms": float(np.percentile(lat_ms, 50)),
+                             "p99_ms": float(np.percentile(lat_ms, 99)),
+                             "mpixel_per_s": pixels / wall / 1e6})
+            out[name] = rows
+        if batch_ref:
+            # every camera's GOP once, in one batched call on the best kernels
+            for precision, tail, name in ((B.CS_FP32, 0, "batched_fp32"),
+                                          (B.CS_FP16, 20, "batched_fp16_tail20")):
+                prm = [params(c, precision, tail) for c in cams]
+                outs = [torch.empty(c["shape"], dtype=torch.uint8, device=dev) for c in cams]
+                args_ = ([c["plan"] for c in cams], prm, [c["key_dev"] for c in cams],
+                         [c["y_dev"] for c in cams], None, outs)
+                with torch.cuda.stream(stream):
+                    B.cs_decode_batch(ctx, *args_, stream)
+                    torch.cuda.synchronize(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    B.cs_decode_batch(ctx, *args_, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize(dev)
+                ms = e0.elapsed_time(e1)
+                out[name] = {"gops": len(cams), "ms": ms,
+                             "mpixel_per_s": sum(c["pixels"] for c in cams) / (ms / 1e3) / 1e6}
+        return out
     finally:
         for c in cams:
             B.cs_plan_destroy(c["plan"])
         B.cs_ctx_destroy(ctx)
-
-
 
 
 def oracle_sample(frames, wl, n_cs_frames: int):
@@ -912,10 +943,15 @@ def main():
     serving = None
     if solo and not args.no_serving:
         rates = [50, 100, 200, 400] if extras else [100]
-        serving = {"workload": SERVING["workload"],
-                   "fp32": serving_run(B, torch, dev, B.CS_FP32, 0, rates, 2.0)}
+        cfgs = [("queue_fp32", B.CS_SERVING_QUEUE, B.CS_FP32, 0)]
         if extras:
-            serving["fp16_tail20"] = serving_run(B, torch, dev, B.CS_FP16, 20, [200, 400], 2.0)
+            cfgs += [("launch_fp32", B.CS_SERVING_LAUNCH, B.CS_FP32, 0),
+                     ("queue_fp16_tail20", B.CS_SERVING_QUEUE, B.CS_FP16, 20)]
+        serving = {"workload": SERVING["workload"],
+                   "modes": "queue: the device work queue (one persistent streaming-kernel launch "
+                            "drains the tiles of every request in flight); launch: one decode launch "
+                            "per request on the kernel its shape picks"}
+        serving.update(serving_run(B, torch, dev, cfgs, rates, 2.0, batch_ref=extras))
 
     cpu = parity_d = None
     if solo and not args.no_cpu_baseline:

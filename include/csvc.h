@@ -232,12 +232,32 @@ double cs_raw_key_cr(int32_t gop, int32_t height, int32_t width, int32_t block, 
  * request larger than the whole pool returns CS_ENOMEM).  Admitted requests
  * run on the context's streams and overlap on the device.  *ticket identifies
  * the request.
+ * With the device work queue (the default, see cs_ctx_set_serving), a request
+ * the streaming tensor-core decode covers (N = 64, 256 or 1024 with M <= 512;
+ * CS_FP32 or CS_FP16; engine CS_ENGINE_AUTO or CS_ENGINE_TC_STREAM; the
+ * context's decode scratch allocated, see cs_ctx_create) is not launched on its
+ * own: once its inputs are on the device its tiles join a queue in device-
+ * visible memory, which one persistent launch of that kernel drains, so tiles
+ * of every request in flight share the SMs as they arrive (continuous
+ * batching).  The launch ends itself after 20 ms without work and is started
+ * again by the next cs_submit or cs_poll.  Its results are bit for bit those of
+ * cs_decode_gop with CS_ENGINE_TC_STREAM.  Any other request runs as its own
+ * decode launch on the context's streams.
  * cs_poll: non-blocking; *done = 1 once the output is in frames_u8_host, then
  * *latency_ms is the submit-to-completion time, the request's device memory
- * and slot are released and the ticket is retired. */
+ * and slot are released and the ticket is retired.  Call it often: it also
+ * restarts the queue's launch when work is waiting.  A request whose decode
+ * gave up a bounded device wait still completes; cs_ctx_status reports it. */
 int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params, const uint8_t* key_host,
               const float* y_host, uint8_t* frames_u8_host, uint64_t* ticket);
 int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms);
+/* cs_ctx_set_serving: how cs_submit runs requests from now on: CS_SERVING_QUEUE
+ * (the device work queue where it applies; the default) or CS_SERVING_LAUNCH
+ * (one decode launch per request, on the kernel cs_decode_gop would pick).
+ * The paper has no counterpart (its decoder is offline). */
+#define CS_SERVING_LAUNCH 0
+#define CS_SERVING_QUEUE 1
+int cs_ctx_set_serving(cs_ctx* ctx, int32_t mode);
 
 /* ---- the whole codec of a clip, host memory in and out ------------------------
  * cs_codec_host: encode a clip and decode it again under n_plans plans, from

@@ -88,6 +88,7 @@ _SIGS = {
     "cs_codec_host": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(cs_params),
                                      _vp, ctypes.POINTER(_vp), ctypes.POINTER(_vp), _vp]),
     "cs_lambda_max_noalloc": (ctypes.c_int, [_vp, _i32, _i32, _vp, _vp]),
+    "cs_ctx_set_serving": (ctypes.c_int, [_vp, _i32]),
     "cs_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "cs_last_error": (ctypes.c_char_p, []),
 }
@@ -290,6 +291,14 @@ def cs_codec_host(ctx: int, plans, params, clip_host, frames_u8_host, psnr_host,
     fu = (_vp * n)(*[_host_ptr(x) for x in frames_u8_host])
     ps = (_vp * n)(*[_host_ptr(x) for x in psnr_host])
     _check(load().cs_codec_host(ctx, n, pl, pa, _host_ptr(clip_host), fu, ps, _stream(stream)))
+
+
+CS_SERVING_LAUNCH, CS_SERVING_QUEUE = 0, 1
+
+
+def cs_ctx_set_serving(ctx: int, mode: int) -> None:
+    """CS_SERVING_QUEUE (device work queue, the default) or CS_SERVING_LAUNCH."""
+    _check(load().cs_ctx_set_serving(ctx, int(mode)))
 
 
 def cs_lambda_max_noalloc(phi_dev, n: int, m: int, lambda_max_dev, stream=None) -> None:

@@ -166,6 +166,11 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
 
 }  // namespace
 
+int prepare_decode_args(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
+                        float* out_f32, uint8_t* out_u8, DecodeArgs* d, int* engine) {
+    return prepare_decode(plan, params, key, y, out_f32, out_u8, d, engine);
+}
+
 int decode_enqueue(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
                    float* out_f32, uint8_t* out_u8, cudaStream_t stream) {
     DecodeArgs d;
@@ -224,6 +229,7 @@ int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes) {
         e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
         if (e == cudaSuccess) ctx->streams.push_back(s);
     }
+    if (e == cudaSuccess) e = tcsq_create(ctx);
     int prio_least = 0, prio_greatest = 0;
     if (e == cudaSuccess) e = cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
     // one fork set for callers' streams and one per serving stream
@@ -246,6 +252,7 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     if (!ctx) return CS_OK;
     cudaSetDevice(ctx->device);
     for (cudaStream_t s : ctx->streams) cudaStreamSynchronize(s);
+    tcsq_destroy(ctx);
     serving_destroy(ctx);
     for (cudaStream_t s : ctx->streams) cudaStreamDestroy(s);
     for (cudaStream_t s : ctx->fork_streams) {
@@ -502,6 +509,14 @@ int cs_ctx_set_debug(cs_ctx* ctx, int32_t flags) {
     if (!ctx) return fail(CS_EINVAL, "null ctx");
     if (flags & ~CS_DEBUG_DROP_ARRIVAL) return fail(CS_EINVAL, "unknown debug flag");
     ctx->debug_flags.store(flags);
+    return CS_OK;
+}
+
+int cs_ctx_set_serving(cs_ctx* ctx, int32_t mode) {
+    if (!ctx) return fail(CS_EINVAL, "null ctx");
+    if (mode != CS_SERVING_QUEUE && mode != CS_SERVING_LAUNCH) return fail(CS_EINVAL, "bad serving mode");
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    ctx->serving_queue = mode == CS_SERVING_QUEUE;
     return CS_OK;
 }
 

@@ -33,7 +33,11 @@
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <atomic>
+#include <new>
 #include <vector>
 
 #include "internal.h"
@@ -66,16 +70,7 @@ constexpr size_t kScrZ = 0, kScrP = 512 * 1024, kScrS = 768 * 1024, kScrY = 1280
 constexpr uint64_t kWaitNs = 1000000000ull;                 // 1 s per wait
 constexpr uint32_t kBarEpi = 1;                             // named barrier of the epilogue
 
-struct MiscS {
-    uint64_t full[kStages], empty[kStages];
-    uint64_t acc_full, acc_empty;
-    uint64_t p_ready, z_ready, drain;
-    uint32_t tmem_base;
-    int abort;
-    int next_tile;
-    uint32_t colmax[kTile];
-};
-static_assert(sizeof(MiscS) <= 1024, "barrier block");
+
 
 }  // namespace
 
@@ -100,11 +95,40 @@ struct TcsJob {
     float su, sg, sp;       // U = acc su, G = acc sg, P operand = P sp
 };
 
+// The device work queue of the serving path (see TcsQueue below): one entry per
+// tile, published by the host in any order; a CTA claims position h once its
+// entry's seq reads h + 1.
+constexpr int kQJobs = 64;
+constexpr int kQRing = 16384;
+struct QEntry {
+    unsigned long long seq;  // position + 1 once published (0: empty)
+    int job;                 // job slot
+    int tile;                // tile of the job
+};
+struct QJob {
+    TcsJob job;
+    unsigned int done_target;  // the slot's cumulative tile count when this job is done
+    unsigned int seq;          // written to done_seq[slot] by the job's last tile
+};
+// Host-mapped (pinned) memory: the host writes jobs and entries, the CTAs claim
+// positions (system-scope CAS on head) and report finished jobs.
+struct QShared {
+    unsigned long long head;   // next position to claim
+    int closing;               // set by a CTA that found nothing to do for the idle limit
+    int pad;
+    unsigned int done_seq[kQJobs];
+    QJob jobs[kQJobs];
+    QEntry ring[kQRing];
+};
+
 constexpr int kMaxJobsS = 48;
 struct TcsLaunch {
     const float* beta;
     int* err;
     int* tile_counter;
+    QShared* q;               // non-null: take tiles from the device work queue
+    unsigned int* q_done;     // per job slot, tiles finished (cumulative), device memory
+    unsigned long long q_idle_ns;
     uint8_t* scratch;       // this launch's area: gridDim.x x kScrBytes
     int drop_arrival;       // test hook: CTA 0 withholds one epilogue warp's first P-ready arrival
     int n_jobs;
@@ -113,6 +137,21 @@ struct TcsLaunch {
 };
 
 namespace {
+
+struct MiscS {
+    uint64_t full[kStages], empty[kStages];
+    uint64_t acc_full, acc_empty;
+    uint64_t p_ready, z_ready, drain;
+    uint32_t tmem_base;
+    int abort;
+    int next_tile;          // >= 0: a tile was claimed; -1: no more tiles
+    int qjob;               // device-queue job slot of the claimed tile (-1: a launch's own job)
+    long long tile_in_job;  // the claimed tile's index within its job
+    uint32_t q_target, q_seq;
+    TcsJob job;             // the claimed tile's job
+    uint32_t colmax[kTile];
+};
+static_assert(sizeof(MiscS) <= 1024, "barrier block");
 
 template <bool BF>
 __device__ __forceinline__ uint32_t pack2s(float2 v) {
@@ -149,10 +188,81 @@ __device__ __forceinline__ int job_of_s(const TcsLaunch& L, int tile) {
     return j;
 }
 
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_acquire_sys_s32(const int* p) {
+    int v;
+    asm volatile("ld.acquire.sys.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys_u32(unsigned int* p, unsigned int v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// The CTA's next tile, claimed by thread 0 and shared through shared memory
+// (job descriptor included): from the launch's own jobs by an atomic counter, or
+// from the device work queue, waiting (bounded by the idle limit) for the host
+// to publish one.  Returns -1 when there is none: every role then leaves.
 __device__ __forceinline__ int fetch_tile_s(const TcsLaunch& L, MiscS* ms) {
-    if (threadIdx.x == 0) ms->next_tile = atomicAdd(L.tile_counter, 1);
+    if (threadIdx.x == 0) {
+        int got = -1;
+        if (L.q == nullptr) {
+            const int t = atomicAdd(L.tile_counter, 1);
+            if (t < L.n_tiles) {
+                const int j = job_of_s(L, t);
+                ms->job = L.jobs[j];
+                ms->tile_in_job = t - L.jobs[j].tile_begin;
+                ms->qjob = -1;
+                got = 0;
+            }
+        } else {
+            const uint64_t t0 = globaltimer_ns();
+            while (!ld_acquire_sys_s32(&L.q->closing)) {
+                const unsigned long long h = *(volatile unsigned long long*)&L.q->head;
+                const QEntry* e = &L.q->ring[h % kQRing];
+                if (ld_acquire_sys_u64(&e->seq) == h + 1) {
+                    // read the entry before claiming it: once claimed, the host may
+                    // reuse it for position h + kQRing
+                    const int js = *(volatile const int*)&e->job;
+                    const int tl = *(volatile const int*)&e->tile;
+                    if (atomicCAS_system(&L.q->head, h, h + 1) == h) {
+                        const QJob& qj = L.q->jobs[js];
+                        ms->job = qj.job;
+                        ms->q_target = qj.done_target;
+                        ms->q_seq = qj.seq;
+                        ms->tile_in_job = tl;
+                        ms->qjob = js;
+                        got = 0;
+                        break;
+                    }
+                    continue;   // another CTA took it: look again at once
+                }
+                if (globaltimer_ns() - t0 > L.q_idle_ns) {
+                    // idle for the limit: close the launch (every CTA leaves; tiles
+                    // published from now on wait for the host's next launch)
+                    atomicCAS_system(&L.q->closing, 0, 1);
+                    break;
+                }
+                __nanosleep(1000);
+            }
+        }
+        ms->next_tile = got;
+    }
     __syncthreads();
     return ms->next_tile;
+}
+
+// After a queue tile's outputs are written: count it, and let the job's last
+// tile tell the host (outputs first visible, then the job's sequence number).
+__device__ __forceinline__ void finish_tile_s(const TcsLaunch& L, MiscS* ms) {
+    if (threadIdx.x == 0 && ms->qjob >= 0) {
+        __threadfence_system();
+        const unsigned int done = atomicAdd(&L.q_done[ms->qjob], 1u) + 1u;
+        if (done == ms->q_target) st_release_sys_u32(&L.q->done_seq[ms->qjob], ms->q_seq);
+    }
 }
 __device__ __forceinline__ void cta_sync_s() {
     fence_before_sync();
@@ -194,8 +304,8 @@ __device__ __forceinline__ void copy_role(const TcsLaunch& L, MiscS* ms, uint8_t
     bool ok = true;
     for (;;) {
         const int tile = fetch_tile_s(L, ms);
-        if (tile >= L.n_tiles) break;
-        const TcsJob& J = L.jobs[job_of_s(L, tile)];
+        if (tile < 0) break;
+        const TcsJob& J = ms->job;
         cta_sync_s();   // B
         const int n = J.n, m16 = J.m16;
         const size_t img1 = (size_t)m16 * n * 2, img2 = (size_t)((m16 + 31) / 32 * 32) * n * 2;
@@ -274,8 +384,8 @@ __device__ __forceinline__ void mma_role_s(const TcsLaunch& L, MiscS* ms, uint8_
     bool ok = true;
     for (;;) {
         const int tile = fetch_tile_s(L, ms);
-        if (tile >= L.n_tiles) break;
-        const TcsJob& J = L.jobs[job_of_s(L, tile)];
+        if (tile < 0) break;
+        const TcsJob& J = ms->job;
         cta_sync_s();   // B
         const int n = J.n, m16 = J.m16;
         for (int pass = 0; pass < 2 * J.iters; ++pass) {
@@ -327,7 +437,8 @@ __device__ __forceinline__ void mma_role_s(const TcsLaunch& L, MiscS* ms, uint8_
                 ++acc;
             }
         }
-        cta_sync_s();   // C
+        cta_sync_s();   // C: the epilogue has written the tile's outputs
+        finish_tile_s(L, ms);
     }
     if (lane == 0) {
         // every MMA issued so far has completed before tensor memory is freed
@@ -509,15 +620,15 @@ __device__ __forceinline__ void epi_role_s(const TcsLaunch& L, MiscS* ms, uint8_
     bool first_tile = true;
     for (;;) {
         const int tile = fetch_tile_s(L, ms);
-        if (tile >= L.n_tiles) break;
-        const TcsJob& J = L.jobs[job_of_s(L, tile)];
+        if (tile < 0) break;
+        const TcsJob& J = ms->job;
         const GopShape& gs = J.gs;
         const int n = J.n, m16 = J.m16, K = J.iters;
         const int bsz = gs.b;
         if (cg == 0) ms->colmax[r] = 0u;
         for (int i = et; i < bsz * bsz; i += kEpiThreads) c_s[i] = J.dct[i];
         cta_sync_s();   // B
-        const long long tile_row0 = J.row0 + (long long)(tile - J.tile_begin) * kTile;
+        const long long tile_row0 = J.row0 + ms->tile_in_job * kTile;
         uint8_t* p_hi = scr + kScrP;
         uint8_t* p_lo = p_hi + (size_t)p_slices(m16) * kTBytes;
         float4* y4 = reinterpret_cast<float4*>(scr + kScrY);
@@ -829,5 +940,172 @@ cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStre
 }
 
 cudaError_t launch_decode_tcs(const DecodeArgs& d, cudaStream_t s) { return launch_decode_tcs_batch(&d, 1, s); }
+
+}  // namespace csvc
+
+// ---------------------------------------------------------------------------
+// The device work queue of the serving path.  One persistent launch of this
+// kernel takes tiles of any admitted request (any N, M this kernel covers, fp16
+// operands) as the host publishes them; CTAs that find nothing for
+// kQueueIdleNs close the launch, and the host launches it again when work
+// arrives.  Ring entries are published from a host callback on the request's
+// stream once its inputs are on the device, so requests overlap on the SMs
+// tile by tile whatever their size.
+namespace csvc {
+
+constexpr unsigned long long kQueueIdleNs = 20000000ull;   // 20 ms
+
+struct TcsQueue {
+    QShared* host = nullptr;           // host-mapped; host writes jobs and entries
+    QShared* dev = nullptr;            // the same memory's device address
+    unsigned int* done_dev = nullptr;  // device: tiles finished per job slot (cumulative)
+    unsigned int done_total[kQJobs] = {};
+    bool slot_used[kQJobs] = {};
+    unsigned int next_seq = 1;
+    unsigned long long next_pos = 0;   // next ring position handed out
+    cudaStream_t stream = nullptr;     // the persistent launch
+    cudaEvent_t running = nullptr;     // recorded after it: complete = not running
+    bool launched = false;
+};
+
+namespace {
+struct PublishArgs {
+    QShared* q;
+    unsigned long long p0;
+    int n, job;
+};
+// Host callback (no CUDA calls): publish positions p0 .. p0 + n - 1, each entry
+// made valid by its sequence number last.
+void CUDART_CB publish_cb(void* a) {
+    PublishArgs* pa = static_cast<PublishArgs*>(a);
+    std::atomic_thread_fence(std::memory_order_acquire);
+    for (int i = 0; i < pa->n; ++i) {
+        QEntry& e = pa->q->ring[(pa->p0 + i) % kQRing];
+        e.job = pa->job;
+        e.tile = i;
+        __atomic_store_n(&e.seq, pa->p0 + (unsigned long long)i + 1ull, __ATOMIC_RELEASE);
+    }
+    delete pa;
+}
+}  // namespace
+
+cudaError_t tcsq_create(cs_ctx* ctx) {
+    TcsQueue* q = new (std::nothrow) TcsQueue();
+    if (!q) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaHostAlloc(&q->host, sizeof(QShared), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        memset(q->host, 0, sizeof(QShared));
+        e = cudaHostGetDevicePointer((void**)&q->dev, q->host, 0);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&q->done_dev, sizeof(unsigned int) * kQJobs);
+    if (e == cudaSuccess) e = cudaMemset(q->done_dev, 0, sizeof(unsigned int) * kQJobs);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->running, cudaEventDisableTiming);
+    ctx->tcsq = q;
+    return e;
+}
+
+void tcsq_destroy(cs_ctx* ctx) {
+    TcsQueue* q = ctx->tcsq;
+    if (!q) return;
+    if (q->host) __atomic_store_n(&q->host->closing, 1, __ATOMIC_RELEASE);
+    if (q->stream) {
+        cudaStreamSynchronize(q->stream);
+        cudaStreamDestroy(q->stream);
+    }
+    if (q->running) cudaEventDestroy(q->running);
+    if (q->done_dev) cudaFree(q->done_dev);
+    if (q->host) cudaFreeHost(q->host);
+    delete q;
+    ctx->tcsq = nullptr;
+}
+
+bool tcsq_accepts(const DecodeArgs& d) {
+    return d.plan->ctx->tcsq && tcs_supported(d.plan) &&
+           (d.precision == CS_FP32 || d.precision == CS_FP16);
+}
+
+// Launch the persistent kernel if it is not running and some position handed
+// out has not been claimed yet.  Caller holds ctx->mu.
+cudaError_t tcsq_kick(cs_ctx* ctx) {
+    TcsQueue* q = ctx->tcsq;
+    if (q->launched) {
+        const cudaError_t st = cudaEventQuery(q->running);
+        if (st == cudaErrorNotReady) return cudaSuccess;
+        if (st != cudaSuccess) return st;
+        q->launched = false;
+    }
+    const unsigned long long head = __atomic_load_n(&q->host->head, __ATOMIC_ACQUIRE);
+    if (head >= q->next_pos) return cudaSuccess;
+    __atomic_store_n(&q->host->closing, 0, __ATOMIC_RELEASE);
+    TcsLaunch L{};
+    L.beta = ctx->beta_dev;
+    L.err = ctx->err_dev;
+    L.q = q->dev;
+    L.q_done = q->done_dev;
+    L.q_idle_ns = kQueueIdleNs;
+    std::lock_guard<std::mutex> lock(ctx->launch_mu);
+    int sslot = 0;
+    cudaError_t e = slot_take(&ctx->tcs_ring, q->stream, &sslot);
+    if (e != cudaSuccess) return e;
+    L.scratch = ctx->tcs_scratch + (size_t)sslot * tcs_slot_bytes(ctx->sm_count);
+    e = cudaFuncSetAttribute((const void*)k_fista_tcs<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemBytes);
+    if (e != cudaSuccess) return e;
+    k_fista_tcs<false><<<kCtasPerSm * ctx->sm_count, kThreads, kSmemBytes, q->stream>>>(L);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = slot_done(&ctx->tcs_ring, sslot, q->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(q->running, q->stream);
+    if (e == cudaSuccess) q->launched = true;
+    return e;
+}
+
+// Post one request's decode: a job slot and ring positions are taken now; the
+// entries are published by a host callback on `s` once the work already on `s`
+// (the request's copy-in) is done.  Caller holds ctx->mu.  Returns CS_EAGAIN
+// when no job slot or ring room is free.
+int tcsq_post(cs_ctx* ctx, const DecodeArgs& d, cudaStream_t s, int* slot, unsigned int* seq) {
+    TcsQueue* q = ctx->tcsq;
+    const long long total = (long long)d.gs.n_cs * d.gs.nblk;
+    const int tiles = (int)((total + kTile - 1) / kTile);
+    if (tiles <= 0) return fail(CS_EINVAL, "empty request");
+    if (tiles > kQRing) return fail(CS_EINVAL, "request larger than the device work queue");
+    int js = -1;
+    for (int i = 0; i < kQJobs && js < 0; ++i)
+        if (!q->slot_used[i]) js = i;
+    if (js < 0) return fail(CS_EAGAIN, "no free queue job slot");
+    const unsigned long long head = __atomic_load_n(&q->host->head, __ATOMIC_ACQUIRE);
+    if (q->next_pos + (unsigned long long)tiles - head > (unsigned long long)kQRing)
+        return fail(CS_EAGAIN, "device work queue full");
+    QJob& qj = q->host->jobs[js];
+    fill_job_s(d, 0, &qj.job);
+    q->done_total[js] += (unsigned int)tiles;
+    qj.done_target = q->done_total[js];
+    qj.seq = q->next_seq++;
+    if (q->next_seq == 0) q->next_seq = 1;
+    PublishArgs* pa = new (std::nothrow) PublishArgs{q->host, q->next_pos, tiles, js};
+    if (!pa) return fail(CS_ENOMEM, "host allocation failed");
+    std::atomic_thread_fence(std::memory_order_release);
+    cudaError_t e = cudaLaunchHostFunc(s, publish_cb, pa);
+    if (e != cudaSuccess) {
+        delete pa;
+        q->done_total[js] -= (unsigned int)tiles;
+        return cuda_fail(e, "queue publish");
+    }
+    q->slot_used[js] = true;
+    q->next_pos += (unsigned long long)tiles;
+    *slot = js;
+    *seq = qj.seq;
+    // the request is posted whatever happens now: a failed launch is retried (and
+    // reported) by the next cs_poll
+    if (tcsq_kick(ctx) != cudaSuccess) set_error("device work queue: launch failed, retried at the next poll");
+    return CS_OK;
+}
+
+bool tcsq_done(cs_ctx* ctx, int slot, unsigned int seq) {
+    return __atomic_load_n(&ctx->tcsq->host->done_seq[slot], __ATOMIC_ACQUIRE) == seq;
+}
+
+void tcsq_release(cs_ctx* ctx, int slot) { ctx->tcsq->slot_used[slot] = false; }
 
 }  // namespace csvc

@@ -34,6 +34,7 @@ int cuda_fail(cudaError_t err, const char* what);
 
 struct Ticket;
 struct Pool;
+struct TcsQueue;
 
 // A ring of per-launch device resources (tile counters, scratch areas).  A
 // launch takes the next slot; its stream first waits for the completion event
@@ -84,6 +85,8 @@ struct cs_ctx {
     // serving state
     std::mutex mu;
     csvc::Pool* pool = nullptr;         // device pool carved from the HBM budget, on first use
+    csvc::TcsQueue* tcsq = nullptr;     // device work queue of the streaming decode (serving)
+    bool serving_queue = true;          // cs_submit posts to the device work queue where it can
     int max_slots = 64;
     std::vector<csvc::Ticket*> live;
     uint64_t next_ticket = 1;
@@ -188,6 +191,15 @@ int tcs_ctas_per_sm();
 constexpr int kForkTcGroups = 3, kForkTcs = 3, kForkTc8Tail = 4, kForkTc8Head = 5, kForkStreams = 6;
 // The fork stream `which` of the set that belongs to origin stream s.
 cudaStream_t fork_stream(const cs_ctx* ctx, cudaStream_t s, int which);
+
+// the device work queue of the serving path (decode_tcs.cu); callers hold ctx->mu
+cudaError_t tcsq_create(cs_ctx* ctx);
+void tcsq_destroy(cs_ctx* ctx);
+bool tcsq_accepts(const DecodeArgs& d);
+cudaError_t tcsq_kick(cs_ctx* ctx);
+int tcsq_post(cs_ctx* ctx, const DecodeArgs& d, cudaStream_t s, int* slot, unsigned int* seq);
+bool tcsq_done(cs_ctx* ctx, int slot, unsigned int seq);
+void tcsq_release(cs_ctx* ctx, int slot);
 
 // serving (serving.cu)
 void serving_destroy(cs_ctx* ctx);

@@ -37,6 +37,15 @@ struct Ticket {
     double submit_ms = 0.0;
     std::atomic<double> done_ms{-1.0};   // stamped by a host callback after the copy-out
     cudaEvent_t done_event = nullptr;
+    // posted to the device work queue: the copy-out is enqueued once the job's
+    // last tile reports
+    bool queued = false, copy_issued = false;
+    int qslot = -1;
+    unsigned int qseq = 0;
+    cudaStream_t stream = nullptr;
+    const uint8_t* out_dev = nullptr;
+    uint8_t* out_host = nullptr;
+    size_t out_b = 0;
 };
 
 struct Pool {
@@ -94,6 +103,8 @@ void serving_destroy(cs_ctx* ctx) {
 
 int decode_enqueue(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
                    float* out_f32, uint8_t* out_u8, cudaStream_t stream);
+int prepare_decode_args(cs_plan* plan, const cs_params* params, const uint8_t* key, const float* y,
+                        float* out_f32, uint8_t* out_u8, DecodeArgs* d, int* engine);
 int make_shape(const cs_plan* plan, const cs_params* p, GopShape* gs);
 
 }  // namespace csvc
@@ -150,12 +161,29 @@ extern "C" int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params,
     t->offset = off;
     t->bytes = bytes;
     t->submit_ms = now_ms();
+    // the device work queue takes the request when the streaming kernel covers it
+    DecodeArgs qd;
+    int qeng = 0;
+    bool queue = ctx->serving_queue &&
+                 prepare_decode_args(plan, params, key_dev, y_dev, nullptr, out_dev, &qd, &qeng) == CS_OK &&
+                 (params->engine == CS_ENGINE_AUTO || params->engine == CS_ENGINE_TC_STREAM) &&
+                 tcsq_accepts(qd);
     cudaError_t e = cudaEventCreateWithFlags(&t->done_event, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpyAsync(key_dev, key_host, key_b, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(y_dev, y_host, y_b, cudaMemcpyHostToDevice, s);
-    st = e == cudaSuccess ? decode_enqueue(plan, params, key_dev, y_dev, nullptr, out_dev, s)
-                          : cuda_fail(e, "cs_submit copy-in");
-    if (st == CS_OK) {
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "cs_submit copy-in");
+    } else if (queue) {
+        st = tcsq_post(ctx, qd, s, &t->qslot, &t->qseq);
+        t->queued = st == CS_OK;
+        t->stream = s;
+        t->out_dev = out_dev;
+        t->out_host = frames_u8_host;
+        t->out_b = out_b;
+    } else {
+        st = decode_enqueue(plan, params, key_dev, y_dev, nullptr, out_dev, s);
+    }
+    if (st == CS_OK && !queue) {
         e = cudaMemcpyAsync(frames_u8_host, out_dev, out_b, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaLaunchHostFunc(s, mark_done, t);
         if (e == cudaSuccess) e = cudaEventRecord(t->done_event, s);
@@ -177,9 +205,29 @@ extern "C" int cs_submit(cs_ctx* ctx, cs_plan* plan, const cs_params* params,
 extern "C" int cs_poll(cs_ctx* ctx, uint64_t ticket, int32_t* done, float* latency_ms) {
     if (!ctx || !done) return fail(CS_EINVAL, "null argument");
     std::lock_guard<std::mutex> lock(ctx->mu);
+    if (ctx->tcsq) {
+        // a launch of the queue kernel that closed while work was posted: relaunch
+        const cudaError_t ke = tcsq_kick(ctx);
+        if (ke != cudaSuccess) return cuda_fail(ke, "cs_poll: queue launch");
+    }
     for (size_t i = 0; i < ctx->live.size(); ++i) {
         Ticket* t = ctx->live[i];
         if (t->id != ticket) continue;
+        if (t->queued && !t->copy_issued) {
+            if (!tcsq_done(ctx, t->qslot, t->qseq)) {
+                *done = 0;
+                return CS_OK;
+            }
+            // decoded: copy the frames out, then stamp the time
+            tcsq_release(ctx, t->qslot);
+            t->copy_issued = true;
+            cudaError_t ce = cudaMemcpyAsync(t->out_host, t->out_dev, t->out_b, cudaMemcpyDeviceToHost, t->stream);
+            if (ce == cudaSuccess) ce = cudaLaunchHostFunc(t->stream, mark_done, t);
+            if (ce == cudaSuccess) ce = cudaEventRecord(t->done_event, t->stream);
+            if (ce != cudaSuccess) return cuda_fail(ce, "cs_poll copy-out");
+            *done = 0;
+            return CS_OK;
+        }
         cudaError_t e = cudaEventQuery(t->done_event);
         if (e != cudaSuccess && e != cudaErrorNotReady) {
             // the request failed on the device: report it once and retire the ticket
