@@ -89,9 +89,14 @@ typedef struct cs_params {
 
 /* ---- context ------------------------------------------------------------
  * cs_ctx_create: bind a context to CUDA device `device` (must be sm_103).
- * hbm_budget_bytes caps the device memory that serving admission may hand
- * out (0 = no cap).  *out receives the context; destroy it with
- * cs_ctx_destroy after every plan made from it has been destroyed. */
+ * hbm_budget_bytes caps the device memory of serving and of the decode
+ * kernels' scratch (0 = no cap): the scratch rings (allocated with the first
+ * plan whose shape needs them) take at most half of the budget and what the
+ * serving pool leaves; a ring that does not fit is not allocated, and shapes
+ * that would use it decode on another kernel.  The serving pool (allocated at
+ * the first cs_submit) gets the budget less the scratch allocated by then (1 GiB
+ * with no budget).  *out receives the context; destroy it with cs_ctx_destroy
+ * after every plan made from it has been destroyed. */
 int cs_ctx_create(cs_ctx** out, int device, size_t hbm_budget_bytes);
 int cs_ctx_destroy(cs_ctx* ctx);
 /* cs_ctx_status: synchronise the context's device, then report CS_ETIMEDOUT
