@@ -70,7 +70,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the decode of one
 # step, from one ncu capture of that exact configuration (FP32-grade, batched);
 # reported as roofline.traffic for it only, null for anything else
-DECODE_DRAM_BYTES = {"cif": 62_840_000}
+DECODE_DRAM_BYTES = {"cif": 62_840_000, "720p": 12_954_700_000}
 FP32_LANES_PER_SM = 128
 
 
@@ -831,6 +831,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-m", type=int, default=0,
                     help="run a single M of the sweep (profiling runs)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="use only the clip's first F frames, a multiple of the GOP (profiling runs)")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end loop")
     ap.add_argument("--no-batch", action="store_true",
                     help="one decode call per M instead of one batched launch")
@@ -848,6 +850,10 @@ def main():
         if args.only_m not in wl["ms"]:
             ap.error("--only-m must be one of %s" % wl["ms"])
         wl["ms"] = [args.only_m]
+    if args.frames and args.workload != "mixed64":
+        if args.frames % wl["gop"] or not 0 < args.frames <= wl["frames"]:
+            ap.error("--frames must be a multiple of the GOP (%d), at most %d" % (wl["gop"], wl["frames"]))
+        wl["frames"] = args.frames
 
     if args.impl == "reference":
         if rank == 0:
@@ -901,7 +907,7 @@ def main():
     e2e_value = job_throughput(world, res["pixels_step"], args.steps, e2e_total) / 1e6
     all_fp32 = all(p.precision == B.CS_FP32 for p in res["params"].values())
     traffic = DECODE_DRAM_BYTES.get(args.workload) if (
-        res["tc_used"] and all_fp32 and not args.no_batch and not args.only_m) else None
+        res["tc_used"] and all_fp32 and not args.no_batch and not args.only_m and not args.frames) else None
     roof = roofline(res["flops"], res["dec_ms"], peaks, peak_kind, res["tc_used"], res["clocks"],
                     n_sm, traffic)
     mixed = res["mixed"]

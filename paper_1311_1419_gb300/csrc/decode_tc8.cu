@@ -76,6 +76,7 @@ constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024;
 // tensor memory columns
 constexpr uint32_t kColG = 0, kColU = 128, kColZHi = 256, kColZLo = 320;
 constexpr uint64_t kWaitNs = 1000000000ull;
+constexpr uint64_t kDrainNs = 20000000ull;   // inbound copies land within microseconds
 
 struct Misc8 {
     uint64_t bar_load, bar_u, bar_g, bar_stage, bar_urecv, bar_pown, bar_precv, bar_lam, bar_z0,
@@ -83,6 +84,8 @@ struct Misc8 {
     uint32_t tmem_base;
     int abort;
     int load_failed;
+    // parities of the phases the roles would have waited for next (the drain)
+    uint32_t ph_urecv_end, ph_precv_end, ph_lam_end;
     uint32_t colmax[kTile];
 };
 static_assert(sizeof(Misc8) <= 1024, "barrier block");
@@ -112,6 +115,7 @@ struct Tc8Launch {
     const float* beta;
     int* err;
     float* scratch;         // [clusters][128][1024] float: s^K of a tile, all-gathered
+    int drop_arrival;       // test hook: cluster 0's CTA 0 withholds one partial-U staging arrival
     int n_jobs;
     int n_tiles;
     Tc8Job jobs[kMaxJobs8];
@@ -284,8 +288,10 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             ph_load ^= 1;
             cur_job = jid;
         }
-        if (J.iters > 0 && lane == 0) {
-            // incoming data of iteration 0 and the tile's lambda exchange
+        if (J.iters > 0 && ok && lane == 0) {
+            // incoming data of iteration 0 and the tile's lambda exchange (armed only
+            // while healthy: after a wait gave up, the open phases stay as they are
+            // for the drain at the end)
             mbar_arrive_expect_tx(&ms->bar_lam, (kCl - 1) * kTile * 4);
             // a CTA that owns no measurement rows receives no partials: its barrier
             // is never armed (an arming of 0 bytes would complete at once, and two
@@ -322,9 +328,11 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             __syncwarp();
             // this CTA's rows have all their partials: arm the next iteration's
             if (rows_q > 0) {
-                ok = wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err) && ok;
-                ph_urecv ^= 1;
-                if (k + 1 < J.iters && lane == 0)
+                if (wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err))
+                    ph_urecv ^= 1;
+                else
+                    ok = false;
+                if (ok && k + 1 < J.iters && lane == 0)
                     mbar_arrive_expect_tx(&ms->bar_urecv, (uint32_t)((kCl - 1) * rows_q * kTile * 4));
             }
             __syncwarp();
@@ -343,9 +351,11 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
                 }
             }
             __syncwarp();
-            ok = wait_bar(ms, &ms->bar_precv, ph_precv, L.err) && ok;
-            ph_precv ^= 1;
-            if (k + 1 < J.iters && lane == 0) {
+            if (wait_bar(ms, &ms->bar_precv, ph_precv, L.err))
+                ph_precv ^= 1;
+            else
+                ok = false;
+            if (ok && k + 1 < J.iters && lane == 0) {
                 const uint32_t pb = (uint32_t)((J.m16 - rows_q) * kTile * 2) * (k + 1 >= J.split_from ? 2u : 1u);
                 mbar_arrive_expect_tx(&ms->bar_precv, pb);
             }
@@ -381,6 +391,8 @@ __device__ __forceinline__ void mma_role8(const Tc8Launch& L, Misc8* ms, uint8_t
         mma_commit(&ms->bar_drain);
         mbar_wait(&ms->bar_drain, 0, kWaitNs);
         if (ms->load_failed) mbar_wait(&ms->bar_load, ph_load ^ 1, kWaitNs);
+        ms->ph_urecv_end = ph_urecv;
+        ms->ph_precv_end = ph_precv;
     }
     __syncwarp();
 }
@@ -477,12 +489,14 @@ __device__ __forceinline__ void epi_role8(const Tc8Launch& L, Misc8* ms, uint8_t
             fence_proxy_async_smem();
             fence_before_sync();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&ms->bar_stage);
+            // (the test hook withholds one warp's first arrival in cluster 0's CTA 0:
+            // the MMA warp's bounded wait gives up, its peers' waits for its data run
+            // out in turn, and every CTA drains)
+            const bool withhold = L.drop_arrival && blockIdx.x == 0 && ew == 1 && k == 0 &&
+                                  tile == (int)cluster_id();
+            if (lane == 0 && !withhold) mbar_arrive(&ms->bar_stage);
             // --- residual rows of this CTA: P = (U su - y) sp ---
-            if (rows_q > 0) {
-                wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err);
-                ph_urecv ^= 1;
-            }
+            if (rows_q > 0 && wait_bar(ms, &ms->bar_urecv, ph_urecv, L.err)) ph_urecv ^= 1;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 if (i >= per_q) break;
@@ -528,8 +542,7 @@ __device__ __forceinline__ void epi_role8(const Tc8Launch& L, Misc8* ms, uint8_t
                         st_async_u32(mapa(dst, p), v, mapa(smem_u32(&ms->bar_lam), p));
                     }
                 }
-                wait_bar(ms, &ms->bar_lam, ph_lam, L.err);
-                ph_lam ^= 1;
+                if (wait_bar(ms, &ms->bar_lam, ph_lam, L.err)) ph_lam ^= 1;
                 float lmax = __uint_as_float(ms->colmax[blk]);
 #pragma unroll
                 for (int s = 0; s < kCl - 1; ++s) lmax = fmaxf(lmax, lam_in[s * kTile + blk]);
@@ -577,6 +590,7 @@ __device__ __forceinline__ void epi_role8(const Tc8Launch& L, Misc8* ms, uint8_t
         cta_sync();   // C
         recon<true>(L, J, sm, tile, q, et, sp, blk, cgrp);
     }
+    if (et == 0) ms->ph_lam_end = ph_lam;
 }
 
 template <bool BF>
@@ -625,6 +639,18 @@ __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kThreads, 1)
         epi_role8<BF>(L, ms, sm, tbase, q, warp, lane);
     }
     cta_sync();
+    cluster_sync();   // every CTA has left its tile loop: no copy is issued from here on
+    if (ms->abort) {
+        // after a wait gave up, a peer's copy or store issued before that peer
+        // stopped may still be landing here: wait (bounded) for this CTA's open
+        // inbound phases before any CTA of the cluster leaves
+        if (warp == 0 && lane == 0) {
+            mbar_wait(&ms->bar_urecv, ms->ph_urecv_end, kDrainNs);
+            mbar_wait(&ms->bar_precv, ms->ph_precv_end, kDrainNs);
+            mbar_wait(&ms->bar_lam, ms->ph_lam_end, kDrainNs);
+        }
+        __syncthreads();
+    }
     cluster_sync();   // no CTA leaves while a peer may still write its shared memory
     if (warp == 0) tmem_dealloc(tbase, 512);
 }
@@ -725,6 +751,7 @@ static cudaError_t launch_group8(const DecodeArgs* const* jobs, int n_jobs, bool
     cudaError_t e = slot_take(&ctx->tc8_ring, s, &slot);
     if (e != cudaSuccess) return e;
     L.scratch = ctx->tc8_scratch + (size_t)slot * tc8_slot_floats(ctx->sm_count);
+    L.drop_arrival = ctx->debug_flags.exchange(0) & CS_DEBUG_DROP_ARRIVAL;
     int tiles = 0;
     for (int i = 0; i < n_jobs; ++i) {
         fill_job8(*jobs[i], tiles, &L.jobs[i]);

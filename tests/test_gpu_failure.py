@@ -21,9 +21,11 @@ def B():
     return binding
 
 
-@pytest.mark.parametrize("b,m,engine", [(16, 32, "TC"), (32, 200, "TC_STREAM")])
+@pytest.mark.parametrize("b,m,engine", [(16, 32, "TC"), (32, 200, "TC_STREAM"), (32, 102, "TC")])
 def test_withheld_arrival_times_out_and_the_context_recovers(B, b, m, engine):
-    # the on-chip kernel (16 x 16 blocks) and the streaming kernel (32 x 32, M > 128)
+    # the on-chip kernel (16 x 16 blocks), the streaming kernel (32 x 32, M > 128) and
+    # the 8-CTA cluster kernel (32 x 32, M <= 128: one CTA stops, its peers' waits for
+    # its data run out in turn, and every CTA drains its inbound copies before leaving)
     eng = getattr(B, "CS_ENGINE_" + engine)
     ctx = B.cs_ctx_create(0)
     plan = B.cs_make_phi(ctx, b * b, m, 3)
