@@ -105,8 +105,8 @@ int cs_ctx_destroy(cs_ctx* ctx);
  * Otherwise CS_OK.  The context stays usable either way. */
 int cs_ctx_status(cs_ctx* ctx);
 /* cs_ctx_set_debug: test hooks for the failure path, consumed by the next
- * launch of the context's 16 x 16 on-chip or streaming tensor-core decode
- * (CS_ENGINE_TC with N = 256, or CS_ENGINE_TC_STREAM).  CS_DEBUG_DROP_ARRIVAL makes one
+ * launch of the context's tensor-core decodes (CS_ENGINE_TC with N = 256 or
+ * 1024, or CS_ENGINE_TC_STREAM).  CS_DEBUG_DROP_ARRIVAL makes one
  * warp of that launch withhold one barrier arrival, so that a device-side wait
  * runs out (after 1 s): the launch then drains, its outputs are incomplete and
  * cs_ctx_status reports CS_ETIMEDOUT; the context stays usable.  No GPU fault
