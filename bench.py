@@ -364,10 +364,13 @@ def run_reference(args, wl, frames):
     print(json.dumps(line), flush=True)
 
 
-def mixed_launches(jobs) -> int:
+def mixed_launches(jobs, clusters=15, kappa=13) -> int:
     """Kernels one cs_decode_batch of the mix launches: one per group of up to 48
     jobs of each tensor-core kernel (16x16 on chip by shared-memory layout, 32x32
-    cluster, streaming; one operand type here) and one per plain-kernel job."""
+    cluster, streaming; one operand type here), one for the streaming tail of the
+    cluster jobs when one of them has more tiles than clusters x kappa (the
+    library's rule; 15 clusters of 8 are co-resident on this part), and one per
+    plain-kernel job."""
     groups = {}
     for j in jobs:
         b, m = j["p"].block, j["p"].m
@@ -378,6 +381,8 @@ def mixed_launches(jobs) -> int:
             key = ("tc", m16 <= 96)
         elif b == 32 and m <= 128:
             key = ("tc8",)
+            if -(-j.get("blocks", 0) // 128) > clusters * kappa:
+                groups[("tc8 tail",)] = 1
         else:
             key = ("tcs",)
         groups[key] = groups.get(key, 0) + 1
@@ -574,9 +579,9 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
                 groups.add(("tc8",))
                 # a large 32x32 job also launches its streaming tail on the SMs whole
                 # clusters leave idle (the library's rule: a tail once the job has more
-                # tiles than clusters x 30; 15 clusters of 8 are co-resident on this part)
+                # tiles than clusters x 13; 15 clusters of 8 are co-resident on this part)
                 tiles = -(-(n_cs * nblk) // 128)
-                if n_sm - 8 * 15 > 0 and tiles > 15 * 30:
+                if n_sm - 8 * 15 > 0 and tiles > 15 * 13:
                     groups.add(("tc8 tail",))
         return len(groups) + plain
     launches_per_step = 2 * len(ms) + decode_launches()

@@ -795,7 +795,7 @@ static double job_cost8(const DecodeArgs& d) {
 // tiles beyond clusters x kTcsTileRatio: both kernels then finish at about the
 // same time.  The split depends on the job alone, so a job decodes to the same
 // bits in any batch.
-constexpr int kTcsTileRatio = 30;
+constexpr int kTcsTileRatio = 13;
 
 static long long tail_rows(const DecodeArgs& d, int clusters, int idle_ctas) {
     if (idle_ctas <= 0 || !tcs_supported(d.plan)) return 0;

@@ -71,3 +71,6 @@ def test_mixed_launch_count():
     # on chip: 50 jobs of M16 <= 96 (2 launches) + 1 of M16 = 128; cluster: 1;
     # streaming: 3 (32x32 M > 128, 8x8) in 1; plain: 2
     assert bench.mixed_launches(jobs) == 2 + 1 + 1 + 1 + 2
+    # a cluster job of more than 15 x 13 tiles adds the streaming tail's launch
+    big = dict(job(32, 102), blocks=196 * 128)
+    assert bench.mixed_launches(jobs + [big]) == 2 + 1 + 1 + 1 + 2 + 1
