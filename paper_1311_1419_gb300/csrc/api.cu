@@ -348,11 +348,16 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
                 }
             }
         }
+        if (ranges[2] > 0.f) p->tc_ephi = (int)floor(log2(16384.0 / (double)ranges[2]));   // max |Phi| near 2^14
         if (e == cudaSuccess && tc_chip && n == 256 && ranges[2] > 0.f) {
-            // the tensor-core encode's Phi images, max |Phi| near 2^14
-            p->tc_ephi = (int)floor(log2(16384.0 / (double)ranges[2]));
+            // the 16 x 16 tensor-core encode's Phi images
             e = cudaMalloc(&p->phi_tc, tc_operand_bytes(n, m));
             if (e == cudaSuccess) e = launch_tc_images(p->phi, p->phi_tc, n, m, p->tc_ephi, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        } else if (e == cudaSuccess && encode_tcg_plan_supported(n, m) && ranges[2] > 0.f) {
+            // the general tensor-core encode's Phi images (every other block size and M)
+            e = cudaMalloc(&p->phi_tcg, encode_tcg_image_bytes(n, m));
+            if (e == cudaSuccess) e = launch_phi_images_g(p->phi, p->phi_tcg, n, m, p->tc_ephi, s);
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         }
         if (e == cudaSuccess && tc_chip && n == 1024) {
@@ -394,6 +399,7 @@ int cs_plan_destroy(cs_plan* p) {
     if (p->a_tc) cudaFree(p->a_tc);
     if (p->a_tcs) cudaFree(p->a_tcs);
     if (p->phi_tc) cudaFree(p->phi_tc);
+    if (p->phi_tcg) cudaFree(p->phi_tcg);
     delete p;
     return CS_OK;
 }
@@ -423,10 +429,12 @@ int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_
     if (st) return st;
     if (gs.n_cs > 0 && (!frames_dev || !y_dev)) return fail(CS_EINVAL, "null buffer");
     if (params->engine < CS_ENGINE_AUTO || params->engine > CS_ENGINE_TC_STREAM) return fail(CS_EINVAL, "bad engine");
-    // the tensor-core encode where the plan has one, unless the plain engine is asked for
-    const bool tc = params->engine != CS_ENGINE_PLAIN && encode_tc_supported(plan);
-    cudaError_t e = tc ? launch_encode_tc(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
-                       : launch_encode(plan, gs, frames_dev, y_dev, (cudaStream_t)stream);
+    // a tensor-core encode where the plan has one (the 16 x 16 kernel with Phi on chip,
+    // else the general one that streams Phi), unless the plain engine is asked for
+    const bool plain = params->engine == CS_ENGINE_PLAIN;
+    cudaError_t e = !plain && encode_tc_supported(plan) ? launch_encode_tc(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
+                    : !plain && plan->phi_tcg           ? launch_encode_tcg(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
+                                                        : launch_encode(plan, gs, frames_dev, y_dev, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "encode launch");
     return CS_OK;
 }

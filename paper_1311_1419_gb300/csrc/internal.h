@@ -114,6 +114,10 @@ struct cs_plan {
     // tensor-core encode (16 x 16 blocks, M <= 128); NULL otherwise
     uint8_t* phi_tc = nullptr;
     int tc_ephi = 0;
+    // fp16 hi / lo images of Phi * 2^tc_ephi in 64-column K chunks for the general
+    // tensor-core encode (N = 64, 256, 1024, M <= 256, where the 16 x 16 one does
+    // not apply); NULL otherwise
+    uint8_t* phi_tcg = nullptr;
     int tc_ep = 0;            // log2 scale of the residual operand P
     // images of A * 2^tc_ea (same four types, m16 x N, 128-byte-swizzled atoms)
     // for the streaming tensor-core decode; NULL when it does not take the shape
@@ -140,6 +144,12 @@ cudaError_t launch_encode_tc(const cs_plan* plan, const GopShape& gs, const uint
                              cudaStream_t s);
 cudaError_t launch_encode(const cs_plan* plan, const GopShape& gs, const uint8_t* frames,
                           float* y, cudaStream_t s);
+// the general tensor-core encode (encode_tcg.cu)
+bool encode_tcg_plan_supported(int n, int m);
+size_t encode_tcg_image_bytes(int n, int m);
+cudaError_t launch_phi_images_g(const float* phi, uint8_t* img, int n, int m, int e, cudaStream_t s);
+cudaError_t launch_encode_tcg(const cs_plan* plan, const GopShape& gs, const uint8_t* frames, float* y,
+                              cudaStream_t s);
 
 // decode (decode_plain.cu, decode_tc.cu)
 struct DecodeArgs {
