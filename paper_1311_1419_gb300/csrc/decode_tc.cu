@@ -109,6 +109,7 @@ struct TcJob {
     int split_from;         // iterations k >= split_from use the 3-MMA split
     float lambda_rel, inv_l;
     float su, sg, sp;       // U = acc su, G = acc sg, P operand = P sp
+    float tv_beta, tv_mu, tv_alpha;   // TV recovery (k_tv_tc): the splitting's penalties, step
 };
 
 constexpr int kMaxJobs = 48;
@@ -116,6 +117,7 @@ struct TcLaunch {
     const float* beta;
     int* err;
     int* tile_counter;      // zeroed before the launch; tiles are handed out in order
+    uint8_t* scratch;       // TV recovery: per-CTA state (q and lambda), kTvScrBytes each
     int drop_arrival;       // test hook: CTA 0 withholds its first residual-ready arrival
     int n_jobs;
     int n_tiles;
@@ -272,6 +274,24 @@ __device__ __forceinline__ void cta_sync() {
     fence_after_sync();
 }
 
+// The job's operand image (hi, then lo) into shared memory, by the MMA warp when
+// the CTA moves to another job.  Returns false when the wait gave up.
+template <int MX>
+__device__ __forceinline__ bool load_images(const TcLaunch& L, const TcJob& J, Misc* ms, uint8_t* sm,
+                                            int lane, uint32_t& ph_load) {
+    if (lane == 0) {
+        const uint32_t img = (uint32_t)J.m16 * kN * 2;
+        mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
+        bulk_g2s(sm + Lay<MX>::kOffAHi, J.a_img, img, &ms->bar_load);
+        bulk_g2s(sm + Lay<MX>::kOffALo, J.a_img + img, img, &ms->bar_load);
+    }
+    __syncwarp();
+    const bool loaded = wait_bar(ms, &ms->bar_load, ph_load, L.err);
+    if (!loaded) ms->load_failed = 1;
+    ph_load ^= 1;
+    return loaded;
+}
+
 // Warp 0: loads A when the CTA moves to another job and issues every MMA.  Only
 // lane 0 issues; the warp waits together.
 template <bool BF, int MX>
@@ -286,17 +306,7 @@ __device__ __forceinline__ void mma_role(const TcLaunch& L, Misc* ms, uint8_t* s
         const int jid = job_of(L, tile);
         const TcJob& J = L.jobs[jid];
         if (jid != cur_job) {
-            if (lane == 0) {
-                const uint32_t img = (uint32_t)J.m16 * kN * 2;
-                mbar_arrive_expect_tx(&ms->bar_load, 2 * img);
-                bulk_g2s(sm + Lay<MX>::kOffAHi, J.a_img, img, &ms->bar_load);
-                bulk_g2s(sm + Lay<MX>::kOffALo, J.a_img + img, img, &ms->bar_load);
-            }
-            __syncwarp();
-            const bool loaded = wait_bar(ms, &ms->bar_load, ph_load, L.err);
-            if (!loaded) ms->load_failed = 1;
-            ok = loaded && ok;
-            ph_load ^= 1;
+            ok = load_images<MX>(L, J, ms, sm, lane, ph_load) && ok;
             cur_job = jid;
         }
         cta_sync();   // B: Z = 0 is in tensor memory
@@ -640,6 +650,436 @@ __global__ void __launch_bounds__(kThreads, 1) k_fista_tc(const __grid_constant_
     if (warp == 0) tmem_dealloc(tbase, 512);
 }
 
+// ---------------------------------------------------------------------------
+// TV recovery on the same tiles (16 x 16 blocks, M16 <= 128): Eq. 1 with the
+// total variation, min ||D r||_1 s.t. Phi r = y, by the augmented-Lagrangian
+// alternating-direction iteration of the plain TV kernel (decode_tv.cu), with
+// the two Phi products of every iteration on the tensor cores:
+//
+//   GEMM1  U [128 x M16] = R [128 x 256] . Phi^T     (Phi r per block; R read from TMEM)
+//   GEMM2  G [128 x 256] = P [128 x M16] . Phi       (Phi^T P per block)
+//
+// with P = mu (Phi r - y) - lam.  The iterate r stays in tensor memory as its
+// fp16 hi + lo halves (GEMM1's A operand, where FISTA keeps Z), and the rest of
+// the state goes through a per-CTA global scratch small enough to stay in L2:
+// q = nu + beta w (2 N per block; with it the difference-side gradient is
+// D^T (beta D r - q) and the multiplier step is nu' = q - beta D r') and lam
+// (M16 per block).  lam -= mu (Phi r' - y) needs Phi r', which is the next
+// GEMM1, so it is taken there: P_k = 2 mu (U_k - y) - lam_{k-1} and lam_k =
+// lam_{k-1} - mu (U_k - y), with P_0 = -mu y.  An epilogue thread (block = TMEM
+// lane, column group cg) owns pixel rows 4 cg .. 4 cg + 3 of its block; the
+// differences reach one row into the neighbouring column groups, whose TMEM
+// columns of the same lane it reads after a barrier of the four warps of its
+// lane quarter.  Per iteration k:
+//   residual : P, lam                                   (after GEMM1; none at k = 0)
+//   r step   : r' = r - alpha (D^T (beta D r - q) + G), staged in the
+//              accumulator columns of the thread's own pixels (after GEMM2)
+//   to R     : r' split into R hi / lo, then GEMM1 of r' starts
+//   q step   : nu' = q - beta D r', w' = shrink(D r' - nu' / beta, 1 / beta),
+//              q' = nu' + beta w'                       (while GEMM1 runs)
+// Every product is FP32-grade (three MMAs per K step).
+constexpr size_t kTvScrQ = 2ull * kN * kTile * 4;                   // q: [2][N / 4][128] float4
+constexpr size_t kTvScrBytes = kTvScrQ + (size_t)kMaxM16 * kTile * 4;   // lam: [M16 / 4][128] float4
+constexpr uint32_t kBarQuarter = 3;                                 // named barriers 3 .. 6
+constexpr uint32_t kTvSmemBytes = Lay<kMaxM16>::kOffMisc + 1024 + 1024;
+
+__device__ __forceinline__ void quarter_sync(int q) { named_sync(kBarQuarter + (uint32_t)q, 128); }
+
+__device__ __forceinline__ float shrink_tv(float v, float t) { return v - fminf(fmaxf(v, -t), t); }
+
+// Row p (16 pixels) of r: its R hi and lo columns, unpacked after the wait.
+__device__ __forceinline__ void tv_ld_row(uint32_t lane_addr, int p, uint32_t (&hi)[8], uint32_t (&lo)[8]) {
+    tmem_ld8(lane_addr + kColZHi + 8 * p, hi);
+    tmem_ld8(lane_addr + kColZLo + 8 * p, lo);
+}
+__device__ __forceinline__ void tv_unpack_row(const uint32_t (&hi)[8], const uint32_t (&lo)[8], float (&r)[16]) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const float2 h = unpack2<false>(hi[e]), l = unpack2<false>(lo[e]);
+        r[2 * e] = h.x + l.x;
+        r[2 * e + 1] = h.y + l.y;
+    }
+}
+// q of plane pl (0: differences along the row, 1: down the column) at row p, as
+// float4 index v = 0 .. 3 of block blk: a warp's 32 blocks read 512 contiguous bytes.
+__device__ __forceinline__ size_t tv_q_index(int pl, int p, int v, int blk) {
+    return (size_t)(pl * (kN / 4) + 4 * p + v) * kTile + blk;
+}
+__device__ __forceinline__ void tv_ld_q(const float4* __restrict__ q4, int pl, int p, int blk, float (&o)[16]) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const float4 x = q4[tv_q_index(pl, p, v, blk)];
+        o[4 * v] = x.x;
+        o[4 * v + 1] = x.y;
+        o[4 * v + 2] = x.z;
+        o[4 * v + 3] = x.w;
+    }
+}
+__device__ __forceinline__ void tv_st_q(float4* __restrict__ q4, int pl, int p, int blk, const float (&o)[16]) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v)
+        q4[tv_q_index(pl, p, v, blk)] = make_float4(o[4 * v], o[4 * v + 1], o[4 * v + 2], o[4 * v + 3]);
+}
+
+// Residual step of iteration k for measurements mbase .. mbase + mq - 1 of the
+// thread's block: rho = U su - y (U = 0 at k = 0), P = c mu rho - lam (c = 1 at
+// k = 0, else 2; lam = lam_{k-1}), lam_k = lam_{k-1} - mu rho, and P sp written
+// as fp16 hi / lo over the staged y.
+__device__ __forceinline__ void tv_residual(const TcJob& J, uint8_t* p_hi, uint8_t* p_lo, uint32_t lane_addr,
+                                            float4* __restrict__ lam4, int blk, int mbase, int mq, int k,
+                                            bool write_p) {
+    const float mu = J.tv_mu, cmu = k == 0 ? mu : 2.f * mu;
+    const bool use_u = k > 0, read_lam = k > 1, write_lam = k > 0 && k + 1 < J.iters;
+    const float2 sp2 = make_float2(J.sp, J.sp);
+#pragma unroll
+    for (int g4 = 0; g4 < kMaxM16 / 16; ++g4) {
+        if (4 * g4 < mq) {
+            const int m = mbase + 4 * g4;
+            uint32_t u[4] = {0u, 0u, 0u, 0u};
+            if (use_u) tmem_ld4(lane_addr + kColAcc + m, u);
+            const uint32_t off = kmajor_off((uint32_t)blk, (uint32_t)m, kTile / 8);
+            const float2 y01 = *reinterpret_cast<const float2*>(p_hi + off);
+            const float2 y23 = *reinterpret_cast<const float2*>(p_lo + off);
+            const size_t li = (size_t)(m / 4) * kTile + blk;
+            const float4 lv = read_lam ? lam4[li] : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (use_u) tmem_wait_ld();
+            const float yy[4] = {y01.x, y01.y, y23.x, y23.y};
+            float l[4] = {lv.x, lv.y, lv.z, lv.w};
+            float p[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float rho = __uint_as_float(u[e]) * J.su - yy[e];
+                p[e] = cmu * rho - l[e];
+                l[e] -= mu * rho;
+            }
+            if (write_lam) lam4[li] = make_float4(l[0], l[1], l[2], l[3]);
+            const float2 p0 = mul2(make_float2(p[0], p[1]), sp2), p1 = mul2(make_float2(p[2], p[3]), sp2);
+            const uint32_t h0 = pack2<false>(p0), h1 = pack2<false>(p1);
+            if (write_p) {
+                *reinterpret_cast<uint2*>(p_hi + off) = make_uint2(h0, h1);
+                const uint32_t l0 = pack2<false>(sub2(p0, unpack2<false>(h0)));
+                const uint32_t l1 = pack2<false>(sub2(p1, unpack2<false>(h1)));
+                *reinterpret_cast<uint2*>(p_lo + off) = make_uint2(l0, l1);
+            }
+        }
+    }
+}
+
+// r step for rows p0 .. p0 + 3: r' = r - alpha (D^T t + G sg), t = beta D r - q
+// (t_h in the row, t_v down the column; both zero where the difference leaves the
+// block), r' written as fp32 into the accumulator columns of the same pixels.
+// At k = 0 (first) r = q = 0.
+__device__ __forceinline__ void tv_r_step(const TcJob& J, uint32_t lane_addr, const float4* __restrict__ q4,
+                                          int blk, int p0, bool first) {
+    const float beta = J.tv_beta, alpha = J.tv_alpha, sg = J.sg;
+    float rc[16], tvp[16];   // r of the current row; t_v of the row above
+#pragma unroll
+    for (int c = 0; c < 16; ++c) rc[c] = tvp[c] = 0.f;
+    if (!first) {
+        uint32_t h0[8], l0[8];
+        tv_ld_row(lane_addr, p0, h0, l0);
+        if (p0 > 0) {
+            uint32_t h1[8], l1[8];
+            tv_ld_row(lane_addr, p0 - 1, h1, l1);
+            float qv[16];
+            tv_ld_q(q4, 1, p0 - 1, blk, qv);
+            tmem_wait_ld();
+            float ra[16];
+            tv_unpack_row(h1, l1, ra);
+            tv_unpack_row(h0, l0, rc);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) tvp[c] = beta * (rc[c] - ra[c]) - qv[c];
+        } else {
+            tmem_wait_ld();
+            tv_unpack_row(h0, l0, rc);
+        }
+    }
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        const int p = p0 + i;
+        uint32_t g[16];
+        tmem_ld16(lane_addr + kColAcc + 16 * p, g);
+        float rn[16], qh[16], qv[16];
+        if (first) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) rn[c] = qh[c] = qv[c] = 0.f;
+            tmem_wait_ld();
+        } else {
+            uint32_t hn[8], ln[8];
+            tv_ld_row(lane_addr, p < 15 ? p + 1 : p, hn, ln);
+            tv_ld_q(q4, 0, p, blk, qh);
+            tv_ld_q(q4, 1, p, blk, qv);
+            tmem_wait_ld();
+            tv_unpack_row(hn, ln, rn);
+        }
+        float th[16], tv[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            th[c] = c < 15 ? beta * (rc[c + 1] - rc[c]) - qh[c] : 0.f;
+            tv[c] = p < 15 ? beta * (rn[c] - rc[c]) - qv[c] : 0.f;
+        }
+        uint32_t o[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float dt = (c > 0 ? th[c - 1] : 0.f) - th[c] + tvp[c] - tv[c];
+            o[c] = __float_as_uint(rc[c] - alpha * fmaf(__uint_as_float(g[c]), sg, dt));
+        }
+        tmem_st16(lane_addr + kColAcc + 16 * p, o);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            rc[c] = rn[c];
+            tvp[c] = tv[c];
+        }
+    }
+}
+
+// r' (staged in the accumulator) into R hi / lo, rows p0 .. p0 + 3.
+__device__ __forceinline__ void tv_to_r(uint32_t lane_addr, int p0) {
+#pragma unroll
+    for (int i = 0; i < 4; i += 2) {
+        uint32_t v0[16], v1[16];
+        tmem_ld16(lane_addr + kColAcc + 16 * (p0 + i), v0);
+        tmem_ld16(lane_addr + kColAcc + 16 * (p0 + i + 1), v1);
+        tmem_wait_ld();
+        uint32_t hi[2][8], lo[2][8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const float2 x0 = u2f2(v0[2 * e], v0[2 * e + 1]), x1 = u2f2(v1[2 * e], v1[2 * e + 1]);
+            hi[0][e] = pack2<false>(x0);
+            lo[0][e] = pack2<false>(sub2(x0, unpack2<false>(hi[0][e])));
+            hi[1][e] = pack2<false>(x1);
+            lo[1][e] = pack2<false>(sub2(x1, unpack2<false>(hi[1][e])));
+        }
+        tmem_st8(lane_addr + kColZHi + 8 * (p0 + i), hi[0]);
+        tmem_st8(lane_addr + kColZLo + 8 * (p0 + i), lo[0]);
+        tmem_st8(lane_addr + kColZHi + 8 * (p0 + i + 1), hi[1]);
+        tmem_st8(lane_addr + kColZLo + 8 * (p0 + i + 1), lo[1]);
+    }
+}
+
+// q step for rows p0 .. p0 + 3 with r' from R: nu' = q - beta d, w' = shrink(d -
+// nu' / beta, 1 / beta), q' = nu' + beta w', d = D r'.  At k = 0 (first) q = 0.
+__device__ __forceinline__ void tv_q_step(const TcJob& J, uint32_t lane_addr, float4* __restrict__ q4, int blk,
+                                          int p0, bool first) {
+    const float beta = J.tv_beta, ib = 1.f / beta;
+    float rc[16];
+    {
+        uint32_t h[8], l[8];
+        tv_ld_row(lane_addr, p0, h, l);
+        tmem_wait_ld();
+        tv_unpack_row(h, l, rc);
+    }
+#pragma unroll 1
+    for (int i = 0; i < 4; ++i) {
+        const int p = p0 + i;
+        uint32_t hn[8], ln[8];
+        tv_ld_row(lane_addr, p < 15 ? p + 1 : p, hn, ln);
+        float qh[16], qv[16];
+        if (first) {
+#pragma unroll
+            for (int c = 0; c < 16; ++c) qh[c] = qv[c] = 0.f;
+        } else {
+            tv_ld_q(q4, 0, p, blk, qh);
+            tv_ld_q(q4, 1, p, blk, qv);
+        }
+        tmem_wait_ld();
+        float rn[16];
+        tv_unpack_row(hn, ln, rn);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+            const float dh = c < 15 ? rc[c + 1] - rc[c] : 0.f;
+            const float dv = p < 15 ? rn[c] - rc[c] : 0.f;
+            const float nh = qh[c] - beta * dh, nv = qv[c] - beta * dv;
+            qh[c] = nh + beta * shrink_tv(dh - nh * ib, ib);
+            qv[c] = nv + beta * shrink_tv(dv - nv * ib, ib);
+        }
+        tv_st_q(q4, 0, p, blk, qh);
+        tv_st_q(q4, 1, p, blk, qv);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) rc[c] = rn[c];
+    }
+}
+
+// Warp 0 of the TV kernel: loads Phi's image when the CTA moves to another job
+// and issues GEMM1 (from k = 1) and GEMM2 of every iteration.
+template <int MX>
+__device__ __forceinline__ void mma_role_tv(const TcLaunch& L, Misc* ms, uint8_t* sm, uint32_t tbase,
+                                            uint32_t s_base, int lane) {
+    uint32_t ph_p = 0, ph_z = 0, ph_load = 0;
+    int cur_job = -1;
+    bool ok = true;
+    for (;;) {
+        const int tile = fetch_tile(L, ms);
+        if (tile >= L.n_tiles) break;
+        const int jid = job_of(L, tile);
+        const TcJob& J = L.jobs[jid];
+        if (jid != cur_job) {
+            ok = load_images<MX>(L, J, ms, sm, lane, ph_load) && ok;
+            cur_job = jid;
+        }
+        cta_sync();   // B
+        for (int k = 0; k < J.iters; ++k) {
+            if (k > 0) {
+                ok = wait_bar(ms, &ms->bar_z0, ph_z, L.err) && ok;   // r^k is in R
+                ph_z ^= 1;
+                fence_after_sync();
+                if (ok && lane == 0) {
+                    issue_gemm1_steps<false, MX>(tbase, s_base, J.m16, 0, 16, true);
+                    mma_commit(&ms->bar_u);
+                }
+                __syncwarp();
+            }
+            ok = wait_bar(ms, &ms->bar_p, ph_p, L.err) && ok;
+            ph_p ^= 1;
+            fence_after_sync();
+            if (ok && lane == 0) {
+                issue_gemm2<false, MX>(tbase, s_base, J.m16, true);
+                mma_commit(&ms->bar_g);
+            }
+            __syncwarp();
+        }
+        cta_sync();   // C
+    }
+    if (lane == 0) {
+        mma_commit(&ms->bar_drain);
+        mbar_wait(&ms->bar_drain, 0, kWaitNs);
+        if (ms->load_failed) mbar_wait(&ms->bar_load, ph_load ^ 1, kWaitNs);
+    }
+    __syncwarp();
+}
+
+// Warps 4 .. 19 of the TV kernel: every step of the iteration but the products,
+// then r^K plus the key (Eq. 4).
+template <int MX>
+__device__ __forceinline__ void epi_role_tv(const TcLaunch& L, Misc* ms, uint8_t* sm, uint32_t tbase, int warp,
+                                            int lane) {
+    const int ew = warp - kProdWarps;
+    const int q = warp & 3, cgrp = ew >> 2;
+    const int blk = 32 * q + lane;
+    const int p0 = 4 * cgrp;
+    const uint32_t lane_addr = tbase + ((uint32_t)(32 * q) << 16);
+    uint8_t* p_hi = sm + Lay<MX>::kOffPHi;
+    uint8_t* p_lo = sm + Lay<MX>::kOffPLo;
+    uint8_t* scr = L.scratch + (size_t)blockIdx.x * kTvScrBytes;
+    float4* q4 = reinterpret_cast<float4*>(scr);
+    float4* lam4 = reinterpret_cast<float4*>(scr + kTvScrQ);
+    uint32_t ph_u = 0, ph_g = 0, ph_y = 0;
+    bool first_tile = true;
+    for (;;) {
+        const int tile = fetch_tile(L, ms);
+        if (tile >= L.n_tiles) break;
+        const TcJob& J = L.jobs[job_of(L, tile)];
+        const GopShape& gs = J.gs;
+        const long long row = (long long)(tile - J.tile_begin) * kTile + blk;
+        const bool live = row < J.rows;
+        const int mq = J.m16 / 4, mbase = cgrp * mq;
+        cta_sync();   // B
+        for (int k = 0; k < J.iters; ++k) {
+            bool ok_u = true;
+            if (k > 0) {
+                ok_u = wait_bar(ms, &ms->bar_u, ph_u, L.err);
+                ph_u ^= 1;
+                fence_after_sync();
+            }
+            wait_bar(ms, &ms->bar_y, ph_y, L.err);          // y is in the P slots
+            ph_y ^= 1;
+            tv_residual(J, p_hi, p_lo, lane_addr, lam4, blk, mbase, mq, k, ok_u);
+            fence_proxy_async_smem();
+            fence_before_sync();
+            __syncwarp();
+            // (the test hook withholds one warp's first arrival in CTA 0)
+            const bool withhold = L.drop_arrival && blockIdx.x == 0 && ew == 1 && k == 0 && first_tile;
+            if (lane == 0 && !withhold) mbar_arrive(&ms->bar_p);
+
+            wait_bar(ms, &ms->bar_g, ph_g, L.err);
+            ph_g ^= 1;
+            fence_after_sync();
+            if (k > 0) quarter_sync(q);                     // the neighbours' q^k is written
+            tv_r_step(J, lane_addr, q4, blk, p0, k == 0);
+            tmem_wait_st();
+            fence_before_sync();
+            quarter_sync(q);                                // every read of r^k is done
+            fence_after_sync();
+            if (k + 1 < J.iters) {
+                tv_to_r(lane_addr, p0);
+                tmem_wait_st();
+                fence_before_sync();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ms->bar_z0);
+                quarter_sync(q);                            // the neighbours' rows of r' are in R
+                fence_after_sync();
+                tv_q_step(J, lane_addr, q4, blk, p0, k == 0);
+            }
+        }
+        // r^K (in the accumulator; zero when there are no iterations) plus the key
+        const int c_idx = live ? (int)(row / gs.nblk) : 0, bl = live ? (int)(row % gs.nblk) : 0;
+        const int g_key = c_idx / (gs.g - 1);
+        const int bi = bl / gs.nbc, bj = bl % gs.nbc;
+        const size_t frame_px = (size_t)gs.h * gs.w;
+        for (int i = 0; i < 4; ++i) {
+            const int p = p0 + i;
+            uint32_t v[16];
+            tmem_ld16(lane_addr + kColAcc + 16 * p, v);
+            tmem_wait_ld();
+            const int py = bi * 16 + p;
+            if (!live || py >= gs.h) continue;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+                const int px = bj * 16 + c;
+                if (px >= gs.w) continue;
+                const size_t off = (size_t)py * gs.w + px;
+                const float rv = J.iters > 0 ? __uint_as_float(v[c]) : 0.f;
+                const float x = (float)J.keys[(size_t)g_key * frame_px + off] + rv;
+                if (J.out_f32) J.out_f32[(size_t)c_idx * frame_px + off] = x;
+                if (J.out_u8) J.out_u8[(size_t)c_idx * frame_px + off] = (uint8_t)fminf(fmaxf(rintf(x), 0.f), 255.f);
+            }
+        }
+        cta_sync();   // C: the accumulator is reused by the next tile
+        first_tile = false;
+    }
+}
+
+template <int MX>
+__global__ void __launch_bounds__(kThreads, 1) k_tv_tc(const __grid_constant__ TcLaunch L) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+    Misc* ms = reinterpret_cast<Misc*>(sm + Lay<MX>::kOffMisc);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
+        if (lane == 0) {
+            mbar_init(&ms->bar_load, 1);
+            mbar_init(&ms->bar_u, 1);
+            mbar_init(&ms->bar_g, 1);
+            mbar_init(&ms->bar_p, kEpiWarps);
+            mbar_init(&ms->bar_z0, kEpiWarps);
+            mbar_init(&ms->bar_z1, kEpiWarps);
+            mbar_init(&ms->bar_y, kStageWarps * 32);
+            mbar_init(&ms->bar_drain, 1);
+            ms->abort = 0;
+            ms->load_failed = 0;
+            fence_mbar_init();
+        }
+        __syncwarp();
+        tmem_alloc(&ms->tmem_base, 512);
+        tmem_relinquish();
+    }
+    cta_sync();
+    const uint32_t tbase = ms->tmem_base;
+    if (warp < kProdWarps) {
+        regs_dec<kProdRegs>();
+        if (warp == 0)
+            mma_role_tv<MX>(L, ms, sm, tbase, smem_u32(sm), lane);
+        else
+            stage_role<MX>(L, ms, sm, warp - 1, lane);
+    } else {
+        regs_inc<kEpiRegs>();
+        epi_role_tv<MX>(L, ms, sm, tbase, warp, lane);
+    }
+    cta_sync();
+    if (warp == 0) tmem_dealloc(tbase, 512);
+}
+
 // Scales of the fp16 operands: max |A|, max_m sum_n |Phi[m][n]| and max |Phi|.
 __global__ void k_tc_ranges(const float* __restrict__ a, const float* __restrict__ phi, int n, int m,
                             float* __restrict__ out) {
@@ -885,6 +1325,71 @@ cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStrea
 
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s) {
     return launch_decode_tc_batch(&d, 1, s);
+}
+
+bool tv_tc_supported(const cs_plan* plan) {
+    const cs_ctx* ctx = plan->ctx;
+    return plan->n == kN && plan->phi_tc != nullptr && m16_of(plan->m) <= kMaxM16 && ctx->tcs_scratch &&
+           (size_t)ctx->sm_count * kTvScrBytes <= tcs_slot_bytes(ctx->sm_count);
+}
+
+// TV recovery of one call's blocks on the tensor cores: one persistent launch,
+// one CTA per SM, its state in a slot of the context's streaming-decode scratch.
+cudaError_t launch_decode_tv_tc(const cs_plan* plan, const GopShape& gs, int iters, float beta, float mu,
+                                float alpha, const uint8_t* key, const float* y, float* out_f32,
+                                uint8_t* out_u8, cudaStream_t s) {
+    cs_ctx* ctx = plan->ctx;
+    TcLaunch L{};
+    L.err = ctx->err_dev;
+    TcJob& J = L.jobs[0];
+    J.a_img = plan->phi_tc;   // Phi 2^tc_ephi: fp16 hi, then fp16 lo
+    J.y = y;
+    J.keys = key;
+    J.out_f32 = out_f32;
+    J.out_u8 = out_u8;
+    J.dct = plan->dct;
+    J.gs = gs;
+    J.rows = (long long)gs.n_cs * gs.nblk;
+    J.tile_begin = 0;
+    J.m16 = m16_of(plan->m);
+    J.iters = iters;
+    J.split_from = 0;
+    // P = 2 mu (U - y) - lam in fp16: FISTA's residual scale, halved once more
+    // and again for every doubling of mu above 1
+    const int ep = plan->tc_ep - 1 - (mu > 1.f ? (int)ceil(log2((double)mu)) : 0);
+    J.su = ldexpf(1.f, -plan->tc_ephi);
+    J.sg = ldexpf(1.f, -(plan->tc_ephi + ep));
+    J.sp = ldexpf(1.f, ep);
+    J.tv_beta = beta;
+    J.tv_mu = mu;
+    J.tv_alpha = alpha;
+    L.n_jobs = 1;
+    L.n_tiles = (int)((J.rows + kTile - 1) / kTile);
+    const void* fn = (const void*)k_tv_tc<kMaxM16>;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return e;
+    if (fa.numRegs < kLaunchRegs || fa.maxThreadsPerBlock < kThreads) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTvSmemBytes);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(ctx->launch_mu);
+    int cslot = 0, sslot = 0;
+    e = slot_take(&ctx->counter_ring, s, &cslot);
+    if (e == cudaSuccess) e = slot_take(&ctx->tcs_ring, s, &sslot);
+    if (e != cudaSuccess) return e;
+    L.tile_counter = ctx->counters_dev + cslot;
+    L.scratch = ctx->tcs_scratch + (size_t)sslot * tcs_slot_bytes(ctx->sm_count);
+    L.drop_arrival = ctx->debug_flags.exchange(0) & CS_DEBUG_DROP_ARRIVAL;
+    e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
+    const int grid = L.n_tiles < ctx->sm_count ? L.n_tiles : ctx->sm_count;
+    if (e == cudaSuccess) {
+        k_tv_tc<kMaxM16><<<grid, kThreads, kTvSmemBytes, s>>>(L);
+        e = cudaGetLastError();
+    }
+    // the slots are handed back even on failure: whatever was enqueued runs first
+    const cudaError_t e1 = slot_done(&ctx->counter_ring, cslot, s);
+    const cudaError_t e2 = slot_done(&ctx->tcs_ring, sslot, s);
+    return e != cudaSuccess ? e : e1 != cudaSuccess ? e1 : e2;
 }
 
 }  // namespace csvc

@@ -206,8 +206,8 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
         return fail(CS_EINVAL, "beta and mu must be finite and > 0");
     if (params->iters < 0 || params->iters > kMaxIters) return fail(CS_EINVAL, "iters out of range");
     if (params->precision != CS_FP32) return fail(CS_EINVAL, "TV recovery computes in FP32 only");
-    if (params->engine == CS_ENGINE_TC || params->engine == CS_ENGINE_TC_STREAM)
-        return fail(CS_EINVAL, "TV recovery has no tensor-core kernel");
+    if (params->engine == CS_ENGINE_TC_STREAM)
+        return fail(CS_EINVAL, "TV recovery has no streaming tensor-core kernel");
     GopShape gs;
     int st = make_shape(plan, params, &gs);
     if (st) return st;
@@ -215,6 +215,16 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
     const long long rows = (long long)gs.n_cs * gs.nblk;
     if (rows == 0) return CS_OK;
     if (!key_dev || !y_dev) return fail(CS_EINVAL, "null input pointer");
+    const float alpha = (float)(1.0 / (8.0 * (double)beta + (double)mu * plan->lipschitz));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int it = params->iters;
+    if (params->engine != CS_ENGINE_PLAIN && tv_tc_supported(plan)) {
+        const cudaError_t e = launch_decode_tv_tc(plan, gs, it, beta, mu, alpha, key_dev, y_dev, frames_f32_dev,
+                                                  frames_u8_dev, s);
+        return e == cudaSuccess ? CS_OK : cuda_fail(e, "cs_decode_gop_tv");
+    }
+    if (params->engine == CS_ENGINE_TC)
+        return fail(CS_EINVAL, "TV recovery's tensor-core kernel takes 16 x 16 blocks with M <= 128");
     if (tv_smem(gs.n, gs.m, 1) > 227 * 1024) return fail(CS_EINVAL, "block too large for the TV kernel");
     // as many blocks per CTA (8, 4, 2 or 1) as keep the state under 100 KB, so that
     // two CTAs share an SM
@@ -224,9 +234,6 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
             nr = r;
             break;
         }
-    const float alpha = (float)(1.0 / (8.0 * (double)beta + (double)mu * plan->lipschitz));
-    cudaStream_t s = (cudaStream_t)stream;
-    const int it = params->iters;
     cudaError_t e;
     switch (nr) {
         case 8: e = launch_tv<8>(plan->phi, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;

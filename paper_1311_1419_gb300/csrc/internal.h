@@ -180,6 +180,12 @@ void plain_default_shape(int n, int m, int* threads, int* blocks_per_cta);
 bool tc_supported(const cs_plan* plan, int precision);
 cudaError_t launch_decode_tc(const DecodeArgs& d, cudaStream_t s);
 cudaError_t launch_decode_tc_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
+// TV recovery on the tensor cores: 16 x 16 blocks with M <= 128, state in a slot
+// of the streaming decode's scratch (decode_tc.cu)
+bool tv_tc_supported(const cs_plan* plan);
+cudaError_t launch_decode_tv_tc(const cs_plan* plan, const GopShape& gs, int iters, float beta, float mu,
+                                float alpha, const uint8_t* key, const float* y, float* out_f32,
+                                uint8_t* out_u8, cudaStream_t s);
 // 32 x 32 blocks (N = 1024): clusters of 8 CTAs (decode_tc8.cu)
 cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaStream_t s);

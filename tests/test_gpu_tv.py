@@ -1,6 +1,7 @@
 """TV recovery on the GPU (cs_decode_gop_tv) against the FP64 oracle's TV
-augmented-Lagrangian decode: 8x8, 16x16 and 32x32 blocks, several GOPs,
-cropped edge blocks, the uint8 rule, zero residual and argument errors."""
+augmented-Lagrangian decode: 8x8, 16x16 (plain and tensor-core kernels) and
+32x32 blocks, several GOPs, cropped edge blocks, the uint8 rule, zero residual
+and argument errors."""
 import numpy as np
 import pytest
 
@@ -26,16 +27,18 @@ def ctx(B):
     B.cs_ctx_destroy(c)
 
 
-@pytest.mark.parametrize("h,w,gop,n_gops,b,m,iters", [
-    (144, 176, 4, 1, 16, 64, 100),     # QCIF, 16x16
-    (40, 56, 3, 2, 8, 24, 150),        # 8x8, cropped edge blocks, two GOPs
-    (64, 96, 3, 1, 32, 102, 60),       # 32x32
+@pytest.mark.parametrize("h,w,gop,n_gops,b,m,iters,engine", [
+    (144, 176, 4, 1, 16, 64, 100, "PLAIN"),   # QCIF, 16x16 on the plain kernel
+    (144, 176, 4, 1, 16, 64, 100, "AUTO"),    # the same on the tensor cores
+    (40, 56, 3, 2, 8, 24, 150, "AUTO"),       # 8x8, cropped edge blocks, two GOPs
+    (64, 96, 3, 1, 32, 102, 60, "AUTO"),      # 32x32
 ])
-def test_tv_matches_oracle(B, ctx, h, w, gop, n_gops, b, m, iters):
+def test_tv_matches_oracle(B, ctx, h, w, gop, n_gops, b, m, iters, engine):
     frames = scenes.surveillance_video(gop * n_gops, h, w, seed=3)
     plan = B.cs_make_phi(ctx, b * b, m, 3)
     try:
-        p = B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops)
+        p = B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops,
+                          engine=getattr(B, "CS_ENGINE_" + engine))
         nblk = (-(-h // b)) * (-(-w // b))
         y = torch.empty((n_gops * (gop - 1), nblk, m), dtype=torch.float32, device="cuda")
         B.cs_encode_gop(plan, p, torch.from_numpy(frames).cuda(), y, torch.cuda.current_stream())
