@@ -745,30 +745,56 @@ def hbm_kernels(res, peaks):
 
 
 def tv_run(B, torch, dev, res, wl, iters, with_oracle):
-    """TV recovery (the paper's TVAL3 regulariser) of the clip at its largest M
-    on the plain per-block kernel, timed once after a warm-up call; the oracle
-    checks the first block row of the first CS frame."""
+    """TV recovery (the paper's TVAL3 regulariser) of the clip at its largest M:
+    on the tensor-core TV kernel where the shape has one (16x16 blocks, M <= 128),
+    else on the plain per-block kernel, each timed once after a warm-up call; with
+    the tensor cores, the plain kernel is timed beside them on the same input.  The
+    oracle checks the first block row of the first CS frame."""
     h, w, b = wl["height"], wl["width"], wl["block"]
     m = max(wl["ms"])
     n_cs, stream = res["n_cs"], res["stream"]
-    tv_out = torch.empty((n_cs, h, w), dtype=torch.float32, device=dev)
-    with torch.cuda.stream(stream):
-        for it in range(2):
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            B.cs_decode_gop_tv(res["plans"][m], res["params"][m], res["keys_dev"], res["y_dev"][m],
-                               tv_out, None, stream)
-            a1.record(stream)
-            torch.cuda.synchronize(dev)
-    B.cs_ctx_status(res["ctx"])
-    tv_ms = a0.elapsed_time(a1)
+    n_gops = wl["frames"] // wl["gop"]
+
+    def timed(engine):
+        p = B.make_params(h, w, wl["gop"], b, m, iters=iters, n_gops=n_gops, engine=engine)
+        out = torch.empty((n_cs, h, w), dtype=torch.float32, device=dev)
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                B.cs_decode_gop_tv(res["plans"][m], p, res["keys_dev"], res["y_dev"][m], out, None,
+                                   stream)
+                a1.record(stream)
+                torch.cuda.synchronize(dev)
+        B.cs_ctx_status(res["ctx"])
+        return out, a0.elapsed_time(a1)
+
+    try:
+        tv_out, tv_ms = timed(B.CS_ENGINE_TC)
+        kernel = "tensor-core TV kernel (k_tv_tc, FP32-grade split-fp16 products)"
+    except B.CsError as e:
+        if e.status != B.CS_EINVAL:
+            raise
+        tv_out, tv_ms = timed(B.CS_ENGINE_PLAIN)
+        kernel = "plain FP32 TV kernel (k_tv_plain; the tensor-core one takes 16x16 blocks, M <= 128)"
     tv_psnr = torch.empty(n_cs, dtype=torch.float64, device=dev)
     B.cs_psnr(res["cs_dev"], tv_out, n_cs, h, w, tv_psnr, stream)
     torch.cuda.synchronize(dev)
-    out = {"workload": "the clip at M=%d, %d iters, beta=1/8, mu=1, plain FP32 kernel" % (m, iters),
+    flops = 4.0 * m * b * b * iters * n_cs * res["nblk"]
+    out = {"workload": "the clip at M=%d, %d iters, beta=1/8, mu=1" % (m, iters), "kernel": kernel,
            "decode_ms": tv_ms, "mpixel_per_s": n_cs * h * w / (tv_ms / 1e3) / 1e6,
+           "achieved_tflops": flops / (tv_ms / 1e3) / 1e12,
            "psnr_db": float(np.mean(tv_psnr.cpu().numpy()))}
+    if kernel.startswith("tensor"):
+        plain_out, plain_ms = timed(B.CS_ENGINE_PLAIN)
+        keys = res["keys_dev"].repeat_interleave(wl["gop"] - 1, dim=0).to(torch.float64)
+        d = (tv_out.to(torch.float64) - plain_out.to(torch.float64)).norm()
+        out["plain_kernel"] = {"decode_ms": plain_ms,
+                               "mpixel_per_s": n_cs * h * w / (plain_ms / 1e3) / 1e6,
+                               "tensor_speedup": plain_ms / tv_ms,
+                               "residual_rel_l2_vs_tensor": float(d / (plain_out.to(torch.float64) - keys).norm())}
+        del plain_out
     if with_oracle:
         from oracle import cs_oracle as O
         frames = res["frames"]
@@ -784,8 +810,11 @@ def tv_run(B, torch, dev, res, wl, iters, with_oracle):
         cols = min(k * b, w)
         want = frames[0][:rows, :cols].astype(np.float64) + full[:, :cols]
         got = tv_out[0, :rows, :cols].cpu().numpy().astype(np.float64)
+        key = frames[0][:rows, :cols].astype(np.float64)
         out["vs_oracle"] = {"sample": "first %d blocks of the first CS frame's first block row" % k,
                             "frame_rel_l2": float(np.linalg.norm(got - want) / np.linalg.norm(want)),
+                            "residual_rel_l2": float(np.linalg.norm(got - want) /
+                                                     max(np.linalg.norm(want - key), 1e-30)),
                             "dpsnr_db": float(O.psnr(frames[1][:rows, :cols], got) -
                                                   O.psnr(frames[1][:rows, :cols], want))}
     return out
@@ -938,6 +967,9 @@ def main():
                "roofline": roofline(cres["flops"], cres["dec_ms"], peaks, peak_kind, cres["tc_used"],
                                     cres["clocks"], n_sm, DECODE_DRAM_BYTES["cif"]),
                "gpu_launches": cres["launches_per_step"] * 5, "psnr_db": cres["psnr"]}
+        if not args.no_tv:
+            cif["tv_recovery"] = tv_run(B, torch, dev, cres, cwl, cwl["iters"],
+                                        with_oracle=not args.no_cpu_baseline)
         if not args.no_cpu_baseline:
             _, _, cref = oracle_sample(cres["frames"], cwl, cwl["oracle_frames"])
             cif["parity_vs_oracle"] = {

@@ -106,7 +106,8 @@ int cs_ctx_destroy(cs_ctx* ctx);
 int cs_ctx_status(cs_ctx* ctx);
 /* cs_ctx_set_debug: test hooks for the failure path, consumed by the next
  * launch of the context's tensor-core decodes (CS_ENGINE_TC with N = 256 or
- * 1024, or CS_ENGINE_TC_STREAM).  CS_DEBUG_DROP_ARRIVAL makes one
+ * 1024, CS_ENGINE_TC_STREAM, or the tensor-core TV kernel of
+ * cs_decode_gop_tv).  CS_DEBUG_DROP_ARRIVAL makes one
  * warp of that launch withhold one barrier arrival, so that a device-side wait
  * runs out (after 1 s): the launch then drains, its outputs are incomplete and
  * cs_ctx_status reports CS_ETIMEDOUT; the context stays usable.  No GPU fault
@@ -182,9 +183,14 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
  * 1 / (8 beta + mu L) for r (L = the plan's Lipschitz constant) and one update
  * of each multiplier; params->iters iterations from zero.  beta and mu are the
  * penalties of the splitting and of the measurement constraint (0.125 and 1
- * suit 8-bit residuals).  FP32, plain per-block kernel (params->precision must
- * be CS_FP32, params->engine CS_ENGINE_AUTO or CS_ENGINE_PLAIN; lambda_rel is
- * not used).
+ * suit 8-bit residuals).  FP32-grade results; params->precision must be
+ * CS_FP32 and lambda_rel is not used.  Engines: CS_ENGINE_AUTO takes the
+ * tensor-core TV kernel (both Phi products per iteration on tcgen05, three fp16
+ * MMAs per K step, the state in the context's streaming-decode scratch) for
+ * 16 x 16 blocks with M <= 128 when the context has that scratch, else the
+ * plain per-block FP32 kernel; CS_ENGINE_TC demands the tensor-core kernel
+ * (CS_EINVAL for any other shape), CS_ENGINE_PLAIN the plain one;
+ * CS_ENGINE_TC_STREAM is CS_EINVAL.
  * Buffers and errors as cs_decode_gop; CS_EINVAL for beta or mu <= 0. */
 int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float mu,
                      const uint8_t* key_dev, const float* y_dev, float* frames_f32_dev,
