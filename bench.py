@@ -557,7 +557,9 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
     param_list = [params[m] for m in ms]
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
 
-    # our kernels per step: one encode and one PSNR per M, and the decode: one
+    # our kernels per step: the encode (tensor-core plans share launches of up to 4
+    # plans and 320 accumulator columns; plain-engine plans one each), one PSNR per
+    # M, and the decode: one
     # launch per call with no_batch, else one per (operand type, shared-memory
     # layout) group of the 16x16 tensor path (M16 <= 96 or <= 128), one per group
     # of the 32x32 cluster path (and its streaming tail), one per group of the
@@ -584,7 +586,17 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
                 if n_sm - 8 * 15 > 0 and tiles > 15 * 13:
                     groups.add(("tc8 tail",))
         return len(groups) + plain
-    launches_per_step = 2 * len(ms) + decode_launches()
+    def encode_launches():
+        if engine == B.CS_ENGINE_PLAIN:
+            return len(ms)
+        count, cols, k = 0, 0, 0
+        for m in ms:
+            m16 = (m + 15) // 16 * 16
+            if k == 0 or k == 4 or cols + m16 > 320:
+                count, cols, k = count + 1, 0, 0
+            cols, k = cols + m16, k + 1
+        return count
+    launches_per_step = encode_launches() + len(ms) + decode_launches()
 
     enc_ev, dec_ev, psnr_ev = [], [], []
 
@@ -595,8 +607,7 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
         if record:
             a0, a1 = ev_pair()
             a0.record(stream)
-        for m in ms:
-            B.cs_encode_gop(plans[m], params[m], frames_dev, y_dev[m], stream)
+        B.cs_encode_batch(ctx, plan_list, param_list, frames_dev, [y_dev[m] for m in ms], stream)
         if record:
             a1.record(stream)
             enc_ev.append((a0, a1))
@@ -639,6 +650,19 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
                 step_ms.append(e0.elapsed_time(e1))
         clock_info = clocks.summary()
 
+        # the encode launch's own duration: each launch is queued behind the L2 flush
+        # (a 256 MB fill that outlasts the host's enqueueing), so its events bracket
+        # the kernel alone, cold L2, with no host launch gap inside
+        enc_q = []
+        for _ in range(5):
+            flush.zero_()
+            q0, q1 = ev_pair()
+            q0.record(stream)
+            B.cs_encode_batch(ctx, plan_list, param_list, frames_dev, [y_dev[m] for m in ms], stream)
+            q1.record(stream)
+            enc_q.append((q0, q1))
+        torch.cuda.synchronize(dev)
+
         # end to end through the C ABI's host-buffer entry point: the clip in
         # from pinned host memory, encode, batched decode, PSNR, uint8 frames
         # and PSNRs out, all inside the timed region
@@ -673,11 +697,12 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
            "tuned": tuned, "plan_ms": plan_ms, "autotune_s": autotune_s, "step_ms": step_ms,
            "e2e_ms": e2e_ms, "h2d": h2d, "d2h": d2h, "clocks": clock_info,
            "launches_per_step": launches_per_step, "dec_ms": avg(dec_ev), "enc_ms": avg(enc_ev),
+           "enc_kernel_ms": avg(enc_q),
            "psnr_ms": avg(psnr_ev), "n_cs": n_cs, "nblk": nblk,
            "pixels_step": len(ms) * n_cs * h * w,
            "flops": sum(decode_flops(n_cs * nblk, m, n, iters) for m in ms),
            "psnr": {str(m): float(np.mean(psnr_dev[m].cpu().numpy())) for m in ms},
-           "enc_bytes": sum(frames.nbytes + 4 * n_cs * nblk * m for m in ms),
+           "enc_bytes": frames.nbytes + sum(4 * n_cs * nblk * m for m in ms),
            "psnr_bytes": len(ms) * n_cs * h * w * (1 + 4)}
     res["tc_used"] = engine == B.CS_ENGINE_TC or (
         engine == B.CS_ENGINE_AUTO and all(t["engine"] in (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM)
@@ -739,9 +764,13 @@ def hbm_kernels(res, peaks):
     def gbs(ms_, nbytes):
         return {"ms_per_step": ms_, "bytes_per_step": nbytes, "achieved_gbs": nbytes / (ms_ / 1e3) / 1e9,
                 "peak_gbs": peaks["hbm_gbs"], "frac": nbytes / (ms_ / 1e3) / 1e9 / peaks["hbm_gbs"]}
-    return {"encode": gbs(res["enc_ms"], res["enc_bytes"]), "psnr": gbs(res["psnr_ms"], res["psnr_bytes"]),
-            "note": "algorithmic bytes (each encode call reads the clip once and writes its y; "
-                    "frames re-read by later calls may hit L2)"}
+    enc = gbs(res["enc_kernel_ms"], res["enc_bytes"])
+    enc["ms_in_step"] = res["enc_ms"]
+    return {"encode": enc, "psnr": gbs(res["psnr_ms"], res["psnr_bytes"]),
+            "note": "algorithmic bytes: the step's one encode call (cs_encode_batch, every M in one "
+                    "launch) reads the clip once and writes every M's y. encode.ms_per_step is the "
+                    "launch's own duration (queued behind an L2 flush: cold L2, no host gap); "
+                    "ms_in_step is the same call timed inside the step (idle GPU before it)"}
 
 
 def tv_run(B, torch, dev, res, wl, iters, with_oracle):

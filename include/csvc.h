@@ -144,6 +144,15 @@ int cs_plan_lipschitz(const cs_plan* plan, double* lipschitz);
  * y_b = Phi r_b with FP32-grade products (exact residuals, FP32 accumulation). */
 int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_dev,
                   float* y_dev, cs_stream_t stream);
+/* cs_encode_batch: cs_encode_gop for n_plans plans (any M, one block size)
+ * over the same clip: params[i] must all describe the same clip (height,
+ * width, gop, n_gops, block), y_dev[i] is plan i's output.  The plans the
+ * tensor-core encode takes share one launch (several when their M add up to
+ * more than one launch holds), which reads the clip once; the results are
+ * bit-identical to one cs_encode_gop per plan.  Host arrays, device buffers;
+ * CS_EINVAL when the calls differ in their clip. */
+int cs_encode_batch(cs_ctx* ctx, int32_t n_plans, cs_plan* const* plans, const cs_params* params,
+                    const uint8_t* frames_dev, float* const* y_dev, cs_stream_t stream);
 
 /* ---- decode (Sec. 3.2, Eqs. 1-4) ------------------------------------------
  * key_dev: uint8 [n_gops][H][W] (the key frame of each GOP); y_dev as written

@@ -70,6 +70,8 @@ _SIGS = {
     "cs_plan_a": (ctypes.c_int, [_vp, ctypes.POINTER(_vp)]),
     "cs_plan_lipschitz": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "cs_encode_gop": (ctypes.c_int, [_vp, ctypes.POINTER(cs_params), _vp, _vp, _vp]),
+    "cs_encode_batch": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(cs_params),
+                                       _vp, ctypes.POINTER(_vp), _vp]),
     "cs_decode_gop": (ctypes.c_int, [_vp, ctypes.POINTER(cs_params), _vp, _vp, _vp, _vp, _vp]),
     "cs_decode_batch": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(_vp), ctypes.POINTER(cs_params),
                                        ctypes.POINTER(_vp), ctypes.POINTER(_vp),
@@ -207,6 +209,15 @@ def cs_plan_lipschitz(plan: int) -> float:
 def cs_encode_gop(plan: int, params: cs_params, frames_dev, y_dev, stream=None) -> None:
     _check(load().cs_encode_gop(plan, ctypes.byref(params), _ptr(frames_dev), _ptr(y_dev),
                                 _stream(stream)))
+
+
+def cs_encode_batch(ctx: int, plans, params, frames_dev, y_dev, stream=None) -> None:
+    """cs_encode_gop for several plans over one clip; sequences of equal length."""
+    n = len(plans)
+    pl = (_vp * n)(*plans)
+    pa = (cs_params * n)(*params)
+    ys = (_vp * n)(*[_ptr(y) for y in y_dev])
+    _check(load().cs_encode_batch(ctx, n, pl, pa, _ptr(frames_dev), ys, _stream(stream)))
 
 
 def cs_decode_gop(plan: int, params: cs_params, key_dev, y_dev, frames_f32_dev=None,

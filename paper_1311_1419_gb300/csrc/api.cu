@@ -429,12 +429,49 @@ int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_
     if (st) return st;
     if (gs.n_cs > 0 && (!frames_dev || !y_dev)) return fail(CS_EINVAL, "null buffer");
     if (params->engine < CS_ENGINE_AUTO || params->engine > CS_ENGINE_TC_STREAM) return fail(CS_EINVAL, "bad engine");
-    // a tensor-core encode where the plan has one (the 16 x 16 kernel with Phi on chip,
-    // else the general one that streams Phi), unless the plain engine is asked for
-    const bool plain = params->engine == CS_ENGINE_PLAIN;
-    cudaError_t e = !plain && encode_tc_supported(plan) ? launch_encode_tc(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
-                    : !plain && plan->phi_tcg           ? launch_encode_tcg(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
-                                                        : launch_encode(plan, gs, frames_dev, y_dev, (cudaStream_t)stream);
+    // the tensor-core encode where the plan has Phi images for it, unless the plain
+    // engine is asked for
+    const bool tc = params->engine != CS_ENGINE_PLAIN && encode_tcg_supported(plan);
+    cudaError_t e = tc ? launch_encode_tcg(plan, gs, frames_dev, y_dev, (cudaStream_t)stream)
+                       : launch_encode(plan, gs, frames_dev, y_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "encode launch");
+    return CS_OK;
+}
+
+int cs_encode_batch(cs_ctx* ctx, int32_t n_plans, cs_plan* const* plans, const cs_params* params,
+                    const uint8_t* frames_dev, float* const* y_dev, cs_stream_t stream) {
+    if (!ctx || n_plans < 0 || (n_plans > 0 && (!plans || !params || !y_dev)))
+        return fail(CS_EINVAL, "null argument");
+    if (n_plans == 0) return CS_OK;
+    std::vector<GopShape> gs(n_plans);
+    for (int i = 0; i < n_plans; ++i) {
+        if (!plans[i] || plans[i]->ctx != ctx) return fail(CS_EINVAL, "plan of another context");
+        const int st = make_shape(plans[i], &params[i], &gs[i]);
+        if (st) return st;
+        if (params[i].engine < CS_ENGINE_AUTO || params[i].engine > CS_ENGINE_TC_STREAM)
+            return fail(CS_EINVAL, "bad engine");
+        if (gs[i].h != gs[0].h || gs[i].w != gs[0].w || gs[i].g != gs[0].g || gs[i].n_gops != gs[0].n_gops ||
+            gs[i].b != gs[0].b)
+            return fail(CS_EINVAL, "every plan's call must describe the same clip and block size");
+        if (gs[i].n_cs > 0 && (!frames_dev || !y_dev[i])) return fail(CS_EINVAL, "null buffer");
+    }
+    CS_CUDA_TRY(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    // the plans the tensor-core encode takes share launches (the clip is read once
+    // per launch); the rest run on the plain kernel one by one
+    std::vector<const cs_plan*> tc_plans;
+    std::vector<float*> tc_y;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n_plans && e == cudaSuccess; ++i) {
+        if (params[i].engine != CS_ENGINE_PLAIN && encode_tcg_supported(plans[i])) {
+            tc_plans.push_back(plans[i]);
+            tc_y.push_back(y_dev[i]);
+        } else {
+            e = launch_encode(plans[i], gs[i], frames_dev, y_dev[i], s);
+        }
+    }
+    if (e == cudaSuccess && !tc_plans.empty())
+        e = launch_encode_tcg_multi(tc_plans.data(), tc_y.data(), (int)tc_plans.size(), gs[0], frames_dev, s);
     if (e != cudaSuccess) return cuda_fail(e, "encode launch");
     return CS_OK;
 }

@@ -1,7 +1,8 @@
 // cs_codec_host: the whole codec of one clip from and to host memory.
 //
 // The clip (key frames and CS frames, Sec. 3) is copied to the device once;
-// every plan measures it (Sec. 3.1, y = Phi r per block of every residual);
+// every plan measures it (Sec. 3.1, y = Phi r per block of every residual; the
+// plans of one block size in one encode launch that reads the clip once);
 // the measurements of all plans are recovered in one batched decode (Sec. 3.2,
 // Eqs. 1-4); every decoded CS frame is scored by PSNR against the original
 // (Sec. 4); the uint8 decoded frames and the PSNRs go back to the host.  The
@@ -92,7 +93,15 @@ extern "C" int cs_codec_host(cs_ctx* ctx, int32_t n_plans, cs_plan* const* plans
         f_p[i] = reinterpret_cast<float*>(base + off_f[i]);
         u_p[i] = base + off_u[i];
     }
-    for (int i = 0; st == CS_OK && i < n_plans; ++i)
+    // one pass over the clip for the plans of one block size, else plan by plan
+    bool one_b = true;
+    for (int i = 1; i < n_plans; ++i) one_b = one_b && gs[i].b == gs[0].b;
+    if (st == CS_OK && one_b) {
+        std::vector<float*> y_w(n_plans);
+        for (int i = 0; i < n_plans; ++i) y_w[i] = const_cast<float*>(y_p[i]);
+        st = cs_encode_batch(ctx, n_plans, plans, params, clip, y_w.data(), stream);
+    }
+    for (int i = 0; st == CS_OK && !one_b && i < n_plans; ++i)
         st = cs_encode_gop(plans[i], &params[i], clip, const_cast<float*>(y_p[i]), stream);
     if (st == CS_OK)
         st = cs_decode_batch(ctx, n_plans, plans, params, key_p.data(), y_p.data(), f_p.data(),

@@ -110,13 +110,14 @@ struct cs_plan {
     // lo, bf16 hi, bf16 lo); NULL when the shape has no tensor-core kernel
     uint8_t* a_tc = nullptr;
     int tc_ea = 0;            // log2 scale of A in the 16-bit operands
-    // fp16 hi / lo (then bf16 hi / lo) images of Phi * 2^tc_ephi for the
-    // tensor-core encode (16 x 16 blocks, M <= 128); NULL otherwise
+    // fp16 hi / lo (then bf16 hi / lo) images of Phi * 2^tc_ephi in the on-chip
+    // kernels' layout (16 x 16 blocks, M <= 128): the tensor-core encode's and TV
+    // decode's operand; NULL otherwise
     uint8_t* phi_tc = nullptr;
     int tc_ephi = 0;
-    // fp16 hi / lo images of Phi * 2^tc_ephi in 64-column K chunks for the general
-    // tensor-core encode (N = 64, 256, 1024, M <= 256, where the 16 x 16 one does
-    // not apply); NULL otherwise
+    // fp16 hi / lo images of Phi * 2^tc_ephi in 64-column K chunks for the
+    // tensor-core encode of every other shape (N = 64, 256, 1024, M <= 256); NULL
+    // otherwise
     uint8_t* phi_tcg = nullptr;
     int tc_ep = 0;            // log2 scale of the residual operand P
     // images of A * 2^tc_ea (same four types, m16 x N, 128-byte-swizzled atoms)
@@ -139,17 +140,18 @@ struct GopShape {
     int nbr, nbc, nblk;   // block rows, block cols, blocks per frame
     int n_cs;             // CS frames in the call = n_gops * (g - 1)
 };
-bool encode_tc_supported(const cs_plan* plan);
-cudaError_t launch_encode_tc(const cs_plan* plan, const GopShape& gs, const uint8_t* frames, float* y,
-                             cudaStream_t s);
 cudaError_t launch_encode(const cs_plan* plan, const GopShape& gs, const uint8_t* frames,
                           float* y, cudaStream_t s);
-// the general tensor-core encode (encode_tcg.cu)
+// the tensor-core encode (encode_tcg.cu): every block size, M <= 256, one or
+// several plans of the same N per launch
 bool encode_tcg_plan_supported(int n, int m);
+bool encode_tcg_supported(const cs_plan* plan);   // the plan has Phi images for it
 size_t encode_tcg_image_bytes(int n, int m);
 cudaError_t launch_phi_images_g(const float* phi, uint8_t* img, int n, int m, int e, cudaStream_t s);
 cudaError_t launch_encode_tcg(const cs_plan* plan, const GopShape& gs, const uint8_t* frames, float* y,
                               cudaStream_t s);
+cudaError_t launch_encode_tcg_multi(const cs_plan* const* plans, float* const* ys, int n_plans,
+                                    const GopShape& gs, const uint8_t* frames, cudaStream_t s);
 
 // decode (decode_plain.cu, decode_tc.cu)
 struct DecodeArgs {

@@ -77,6 +77,18 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool valid
                  "r"(valid ? 4 : 0)
                  : "memory");
 }
+// 8-byte asynchronous copy global -> shared; zero fill when !valid (src is then
+// not read).  dst and src 8-byte aligned.
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(valid ? 8 : 0)
+                 : "memory");
+}
+// Wait until at most N of this thread's committed cp.async groups are pending.
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() {
     asm volatile("cp.async.commit_group;" ::: "memory");
 }

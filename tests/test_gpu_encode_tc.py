@@ -1,7 +1,8 @@
-"""The tensor-core encodes against the FP64 oracle and against the SIMT encode:
-the 16x16 kernel (M <= 128, Phi on chip) and the general one (8x8, 16x16 with
-M > 128, 32x32; Phi streamed in 64-pixel K chunks): vector loads and the
-cropped-edge path, ragged last tiles, every M16 class, several GOPs."""
+"""The tensor-core encode against the FP64 oracle and against the SIMT encode,
+on every block size (8x8, 16x16 with M <= 128 on the on-chip kernels' Phi
+images, 16x16 with M > 128, 32x32; Phi streamed in 64-pixel K chunks): vector
+loads and the cropped-edge path, ragged last tiles, every M16 class, several
+GOPs."""
 import numpy as np
 import pytest
 
