@@ -148,9 +148,11 @@ int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_
  * over the same clip: params[i] must all describe the same clip (height,
  * width, gop, n_gops, block), y_dev[i] is plan i's output.  The plans the
  * tensor-core encode takes share one launch (several when their M add up to
- * more than one launch holds), which reads the clip once; the results are
- * bit-identical to one cs_encode_gop per plan.  Host arrays, device buffers;
- * CS_EINVAL when the calls differ in their clip. */
+ * more than one launch holds), which reads the clip once.  Each y is FP32-grade
+ * like cs_encode_gop's and equal to it up to FP32 rounding (the hi and lo
+ * products of a plan may be summed in another order when the launch is
+ * crowded); the same call always gives the same bytes.  Host arrays, device
+ * buffers; CS_EINVAL when the calls differ in their clip. */
 int cs_encode_batch(cs_ctx* ctx, int32_t n_plans, cs_plan* const* plans, const cs_params* params,
                     const uint8_t* frames_dev, float* const* y_dev, cs_stream_t stream);
 

@@ -5,24 +5,27 @@
 //
 // One GEMM across the blocks of the call per plan, Y_p [rows x M_p] = R [rows x
 // N] Phi_p^T, with R shared by the plans: residuals are integers in [-255, 255],
-// exact in fp16, and Phi * 2^e is split into fp16 hi + lo, so two MMAs per K
-// step give FP32-grade products.  A tile is 128 blocks (one per TMEM lane); K
-// runs in chunks of 64 pixels (two rows of a 32 x 32 block, four of a 16 x 16,
-// a whole 8 x 8 block).  Per CTA (one per SM) the work is a pipeline over its
-// chunks, with mbarrier hand-offs and no CTA-wide barrier per chunk:
-//   - warps 1 .. 16, residual bytes: every thread copies the current and key
-//     bytes of its own two 8-pixel items of a chunk with asynchronous 8-byte
-//     copies, D chunks ahead, into a ring in shared memory (no other thread
-//     reads them, so the copies need no barrier);
-//   - warps 1 .. 16, residual chunks: current - key (fp16, exact) into an
-//     S-stage ring of 128-byte-swizzled operands, one arrival per warp;
-//   - warp 0 (one thread): bulk-copies every plan's Phi chunk (hi and lo,
-//     contiguous in the images' K-chunk-major layout, resident in L2) S - 1
-//     chunks ahead into an S-stage ring, and issues each plan's MMAs into the
-//     plan's own accumulator columns;
-//   - warps 1 .. 16, after a tile's last chunk: y = D 2^-e through shared memory
-//     (the residual ring, idle then) in slices of 64 columns, so that rows of y
-//     are stored contiguously.
+// exact in fp16, and Phi * 2^e is split into fp16 hi + lo, which gives
+// FP32-grade products.  Where the accumulators fit, a plan's hi and lo images
+// form one B operand of 2 M16 rows (Y_hi and Y_lo side by side in tensor
+// memory, added at the end), so a K step is one MMA of N = 2 M16; otherwise
+// each is its own MMA.  A tile is 128 blocks (one per TMEM lane); K runs in
+// chunks of 64 pixels (two rows of a 32 x 32 block, four of a 16 x 16, a whole
+// 8 x 8 block).  Per CTA (one per SM) the work is a pipeline over its chunks,
+// with mbarrier hand-offs and no CTA-wide barrier per chunk:
+//   - warps 1 .. 16 (the converters): warp w owns TMEM lane quarter w % 4 (32
+//     blocks of the tile) and pixels 16 ((w - 1) / 4) .. + 15 of every chunk;
+//     each thread loads its block's current and key bytes four chunks ahead into
+//     registers, forms current - key as fp16 (exact) and stores it into a TMEM
+//     stage, the MMA's A operand;
+//   - warp 17 (one thread): bulk-copies every plan's Phi chunk (hi and lo,
+//     contiguous in the images' K-chunk-major layout, resident in L2) into an
+//     S-stage ring, as soon as the stage's last MMAs are done;
+//   - warp 0 (one thread): issues each plan's MMAs into the plan's accumulator
+//     columns;
+//   - the converters, after a tile's last chunk: y = D 2^-e through shared
+//     memory in slices of 64 columns, so that rows of y are stored
+//     contiguously.
 // Every mbarrier wait is bounded and reports through the context's error word.
 #include <cuda_fp16.h>
 
@@ -38,7 +41,9 @@ constexpr int kMaxEncPlans = 4;
 struct EncPlan {
     const uint8_t* img;   // Phi * 2^e: fp16 hi image then fp16 lo image, m16 x n each
     float* y;             // [rows][m]
-    int m, m16, col;      // measurements, rounded up to 16, first accumulator column
+    int m, m16;           // measurements, rounded up to 16
+    int col;              // first accumulator column (hi; lo at col + m16 in paired mode)
+    int phi_off;          // byte offset of the plan's hi chunk in a Phi stage (lo follows it)
     float scale;          // 2^-e
 };
 struct EncLaunch {
@@ -46,8 +51,11 @@ struct EncLaunch {
     GopShape gs;          // the clip (its m is not used)
     int* err;
     int n_plans;
-    int m16_total;        // accumulator columns of all plans
-    int vec;              // 8-byte frame loads are aligned and never cross the right edge
+    int m16_total;        // rows of all plans' images
+    int paired;           // hi and lo as one B operand of 2 m16 rows
+    int r_col;            // first TMEM column of the residual stages (32 columns each)
+    int ncols;            // TMEM columns allocated
+    int vec;              // 1: 8-byte frame loads, 2: 16-byte, 0: byte loads
     EncPlan p[kMaxEncPlans];
 };
 
@@ -55,39 +63,26 @@ namespace {
 
 using namespace tc;
 
-constexpr int kT = 512;                             // converter threads (16 warps)
 constexpr int kTile = 128;
 constexpr int kChunk = 64;                          // K per chunk: one 128-byte swizzle atom column
-constexpr int kItems = kTile * kChunk / 8;          // 8-pixel items of a chunk: 1024
-constexpr int kItemsPerThread = kItems / kT;        // 2
-constexpr uint32_t kRStage = kTile * kChunk * 2;    // fp16 residual operand of a chunk: 16 KB
-constexpr uint32_t kRawSlot = 2u * kItems * 8u;     // current then key bytes of a chunk: 16 KB
+constexpr int kConvWarps = 16;                      // warps 1 .. 16: four per TMEM lane quarter
+constexpr int kThreadsE = (2 + kConvWarps) * 32;    // + warp 0 (MMAs) and warp 17 (Phi copies)
+constexpr int kPhiWarp = kConvWarps + 1;
+constexpr int kDepth = 4;                           // chunks of frame bytes in flight per thread
 constexpr int kMaxM16 = 256;                        // per plan (one MMA's N)
 constexpr int kMaxM16Total = 320;                   // per launch
+constexpr uint32_t kYStage = kTile * 64 * 4;        // y staging: 128 rows x 64 columns
+constexpr uint32_t kBarConv = 1;                    // named barrier of the converter warps
 constexpr uint64_t kWaitNs = 1000000000ull;
 
 __host__ __device__ constexpr uint32_t phi_stage_bytes(int m16_total) {
     return 2u * (uint32_t)m16_total * kChunk * 2u;
 }
-__host__ __device__ constexpr uint32_t off_r(int s, int m16_total) { return (uint32_t)s * phi_stage_bytes(m16_total); }
-__host__ __device__ constexpr uint32_t off_raw(int s, int m16_total) {
-    return off_r(s, m16_total) + (uint32_t)s * kRStage;
-}
-__host__ __device__ constexpr uint32_t off_bar(int s, int d, int m16_total) {
-    return off_raw(s, m16_total) + (uint32_t)d * kRawSlot;
-}
-__host__ __device__ constexpr uint32_t smem_bytes(int s, int d, int m16_total) {
-    return off_bar(s, d, m16_total) + 256u + 1024u;
-}
+__host__ __device__ constexpr uint32_t off_y(int s, int m16_total) { return (uint32_t)s * phi_stage_bytes(m16_total); }
+__host__ __device__ constexpr uint32_t off_bar(int s, int m16_total) { return off_y(s, m16_total) + kYStage; }
+__host__ __device__ constexpr uint32_t smem_bytes(int s, int m16_total) { return off_bar(s, m16_total) + 256u + 1024u; }
 constexpr uint32_t kSmemMax = 232448;
-static_assert(smem_bytes(2, 2, kMaxM16Total) <= kSmemMax, "the widest launch fits");
-
-// Byte offset of pixels k .. k + 7 (k % 8 == 0, k < 64) of block row `row` in a
-// chunk operand (K-major, 16 row groups of 1 KB, 128-byte swizzle).
-__device__ __forceinline__ uint32_t rchunk_off(uint32_t row, uint32_t k) {
-    const uint32_t r = row & 7;
-    return (row >> 3) * 1024u + r * 128u + (((k >> 3) ^ r) << 4);
-}
+static_assert(smem_bytes(2, kMaxM16Total) <= kSmemMax, "the widest launch fits");
 
 __device__ __forceinline__ bool wait_e(uint64_t* bar, uint32_t parity, int* abort, int* err) {
     if (*(volatile int*)abort) return false;
@@ -97,140 +92,175 @@ __device__ __forceinline__ bool wait_e(uint64_t* bar, uint32_t parity, int* abor
     return false;
 }
 
-// Where a converter thread's items of a tile come from.  Thread t's items are
-// blocks b_i = t / 8 + 64 i of the tile (i = 0, 1), all at segment kseg = t % 8
-// of a chunk (block row rr = kseg / segs of the chunk's rows, 8-pixel segment sg
-// = kseg % segs), so per tile it keeps each block's byte offsets of its first
-// chunk in the current and key frames; chunk c adds c (64 / B) rows.
-struct ItemBase {
-    long long cur[kItemsPerThread], key[kItemsPerThread];
-    int fy[kItemsPerThread];   // frame row of the first chunk (>= H: outside; -1: no block)
-    int fx[kItemsPerThread];   // frame column of the segment
+// A converter thread's block of a tile: byte offsets of its first chunk's two
+// 8-pixel segments in the current frame (the key at key_off from them), the
+// frame rows of the two segments (-1: no block), and the frame column.
+struct Src {
+    long long off0, off1, key_d;
+    int fy0, fy1, fx;
 };
 
-__device__ __forceinline__ void item_bases(const EncLaunch& L, int tile, int rows, int t, ItemBase& ib) {
+// Thread (lane quarter q = block 32 q + lane of the tile, pixel group cg = 16
+// pixels of a chunk).  The 16 pixels: a half row of a 32 x 32 block, a row of a
+// 16 x 16 block, two rows of an 8 x 8 block.
+__device__ __forceinline__ void src_of(const EncLaunch& L, int tile, int rows, int b, int cg, Src& sr) {
     const GopShape& gs = L.gs;
-    const int bsz = gs.b, segs = bsz / 8;
-    const int kseg = t % (kChunk / 8), rr = kseg / segs, sg = kseg % segs;
+    const int bsz = gs.b;
+    const int row = tile * kTile + b;
+    sr.fy0 = sr.fy1 = -1;
+    sr.fx = 0;
+    sr.off0 = sr.off1 = sr.key_d = 0;
+    if (row >= rows) return;
+    const int ci = row / gs.nblk, blk = row - ci * gs.nblk;
+    const int gg = ci / (gs.g - 1), j = ci - gg * (gs.g - 1) + 1;
+    const int bi = blk / gs.nbc, bj = blk - bi * gs.nbc;
+    int r0, c0, r1, c1;
+    if (bsz == 32) { r0 = r1 = cg >> 1; c0 = 16 * (cg & 1); c1 = c0 + 8; }
+    else if (bsz == 16) { r0 = r1 = cg; c0 = 0; c1 = 8; }
+    else { r0 = 2 * cg; r1 = r0 + 1; c0 = c1 = 0; }
     const long long frame_px = (long long)gs.h * gs.w;
-#pragma unroll
-    for (int i = 0; i < kItemsPerThread; ++i) {
-        const int b = t / (kChunk / 8) + (kT / (kChunk / 8)) * i;
-        const int row = tile * kTile + b;
-        ib.fy[i] = -1;
-        ib.fx[i] = 0;
-        ib.cur[i] = ib.key[i] = 0;
-        if (row < rows) {
-            const int r32 = row;
-            const int ci = r32 / gs.nblk, blk = r32 - ci * gs.nblk;
-            const int gg = ci / (gs.g - 1), j = ci - gg * (gs.g - 1) + 1;
-            const int bi = blk / gs.nbc, bj = blk - bi * gs.nbc;
-            const int fy = bi * bsz + rr, fx = bj * bsz + 8 * sg;
-            ib.fy[i] = fy;
-            ib.fx[i] = fx;
-            ib.cur[i] = (long long)(gg * gs.g + j) * frame_px + (long long)fy * gs.w + fx;
-            ib.key[i] = (long long)(gg * gs.g) * frame_px + (long long)fy * gs.w + fx;
-        }
-    }
+    const long long cur = (long long)(gg * gs.g + j) * frame_px;
+    sr.fy0 = bi * bsz + r0;
+    sr.fy1 = bi * bsz + r1;
+    sr.fx = bj * bsz + c0;
+    sr.off0 = cur + (long long)sr.fy0 * gs.w + bj * bsz + c0;
+    sr.off1 = cur + (long long)sr.fy1 * gs.w + bj * bsz + c1;
+    sr.key_d = -(long long)j * frame_px;
 }
 
-// The residual bytes of this thread's items of chunk c (of the tile ib describes)
-// into a raw slot: item i at 8 (t + 512 i) (current frame) and 8192 + 8 (t + 512
-// i) (its key).  Items outside the frame or beyond the last block read as zero.
-__device__ __forceinline__ void load_raw(const EncLaunch& L, uint8_t* raw, const ItemBase& ib, int c, int t) {
+// The thread's 16 current and 16 key bytes of chunk c (zero outside the frame).
+__device__ __forceinline__ void load_bytes(const EncLaunch& L, const Src& sr, int c, uint4& cv, uint4& kv) {
     const GopShape& gs = L.gs;
     const int dy = c * (kChunk / gs.b);
+    const long long step = (long long)dy * gs.w;
+    const bool v0 = sr.fy0 >= 0 && sr.fy0 + dy < gs.h, v1 = sr.fy1 >= 0 && sr.fy1 + dy < gs.h;
+    cv = kv = make_uint4(0u, 0u, 0u, 0u);
+    const uint8_t* p0 = L.frames + sr.off0 + step;
+    const uint8_t* p1 = L.frames + sr.off1 + step;
+    if (L.vec == 2) {          // both segments in one 16-byte row piece
+        if (v0) {
+            cv = __ldg(reinterpret_cast<const uint4*>(p0));
+            kv = __ldg(reinterpret_cast<const uint4*>(p0 + sr.key_d));
+        }
+    } else if (L.vec == 1) {
+        if (v0) {
+            const uint2 a = __ldg(reinterpret_cast<const uint2*>(p0));
+            const uint2 k = __ldg(reinterpret_cast<const uint2*>(p0 + sr.key_d));
+            cv.x = a.x; cv.y = a.y; kv.x = k.x; kv.y = k.y;
+        }
+        if (v1) {
+            const uint2 a = __ldg(reinterpret_cast<const uint2*>(p1));
+            const uint2 k = __ldg(reinterpret_cast<const uint2*>(p1 + sr.key_d));
+            cv.z = a.x; cv.w = a.y; kv.z = k.x; kv.w = k.y;
+        }
+    } else {
+        // cropped right edge or unaligned rows: byte loads, zero beyond the frame
+        uint32_t cw[4] = {0u, 0u, 0u, 0u}, kw[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-    for (int i = 0; i < kItemsPerThread; ++i) {
-        const int item = t + kT * i;
-        uint8_t* dc = raw + 8 * item;
-        uint8_t* dk = raw + kItems * 8 + 8 * item;
-        const bool valid = ib.fy[i] >= 0 && ib.fy[i] + dy < gs.h;
-        const long long step = (long long)dy * gs.w;
-        const uint8_t* cur = valid ? L.frames + ib.cur[i] + step : L.frames;
-        const uint8_t* key = valid ? L.frames + ib.key[i] + step : L.frames;
-        if (L.vec) {
-            cp_async8(dc, cur, valid);
-            cp_async8(dk, key, valid);
-        } else {
-            // cropped right edge or unaligned rows: plain byte loads, zero beyond the frame
-#pragma unroll
-            for (int x = 0; x < 8; ++x) {
-                const bool in = valid && ib.fx[i] + x < gs.w;
-                dc[x] = in ? cur[x] : (uint8_t)0;
-                dk[x] = in ? key[x] : (uint8_t)0;
+        for (int x = 0; x < 16; ++x) {
+            const bool seg1 = x >= 8;
+            const int xx = x & 7;
+            const bool in = (seg1 ? v1 : v0) && sr.fx + (seg1 && gs.b >= 16 ? 8 : 0) + xx < gs.w;
+            const uint8_t* p = (seg1 ? p1 : p0) + xx;
+            if (in) {
+                cw[x >> 2] |= (uint32_t)p[0] << (8 * (x & 3));
+                kw[x >> 2] |= (uint32_t)p[sr.key_d] << (8 * (x & 3));
             }
         }
+        cv = make_uint4(cw[0], cw[1], cw[2], cw[3]);
+        kv = make_uint4(kw[0], kw[1], kw[2], kw[3]);
     }
 }
 
-// current - key of the thread's items into the fp16 residual operand.  A byte b
-// placed under the exponent byte 0x64 is the fp16 value 1024 + b, exactly; the
-// difference of two such values is cur - key, exactly (|cur - key| <= 255 <
-// 2^11), so a pixel pair costs two byte permutes and one half2 subtract.
-__device__ __forceinline__ void form_residual(const uint8_t* raw, uint8_t* rbuf, int t) {
+// current - key for 16 pixels as 8 fp16 pairs.  A byte b placed under the
+// exponent byte 0x64 is the fp16 value 1024 + b, exactly; the difference of two
+// such values is cur - key, exactly (|cur - key| <= 255 < 2^11).
+__device__ __forceinline__ void residual16(const uint4& cv, const uint4& kv, uint32_t (&r)[8]) {
+    const uint32_t cw[4] = {cv.x, cv.y, cv.z, cv.w}, kw[4] = {kv.x, kv.y, kv.z, kv.w};
 #pragma unroll
-    for (int i = 0; i < kItemsPerThread; ++i) {
-        const int item = t + kT * i;
-        const uint2 cv = *reinterpret_cast<const uint2*>(raw + 8 * item);
-        const uint2 kv = *reinterpret_cast<const uint2*>(raw + kItems * 8 + 8 * item);
-        const uint32_t cw[2] = {cv.x, cv.y}, kw[2] = {kv.x, kv.y};
-        uint4 pk;
-        uint32_t* w = reinterpret_cast<uint32_t*>(&pk);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            // bytes 2 (e & 1), 2 (e & 1) + 1 of the word, each under 0x64
-            const uint32_t sel = (e & 1) ? 0x4342u : 0x4140u;
-            const uint32_t ch = __byte_perm(cw[e >> 1], 0x64646464u, sel);
-            const uint32_t kh = __byte_perm(kw[e >> 1], 0x64646464u, sel);
-            const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&ch), *reinterpret_cast<const __half2*>(&kh));
-            w[e] = *reinterpret_cast<const uint32_t*>(&d);
-        }
-        const int b = item / (kChunk / 8), kseg = item % (kChunk / 8);
-        *reinterpret_cast<uint4*>(rbuf + rchunk_off((uint32_t)b, (uint32_t)(8 * kseg))) = pk;
+    for (int e = 0; e < 8; ++e) {
+        const uint32_t sel = (e & 1) ? 0x4342u : 0x4140u;
+        const uint32_t ch = __byte_perm(cw[e >> 1], 0x64646464u, sel);
+        const uint32_t kh = __byte_perm(kw[e >> 1], 0x64646464u, sel);
+        const __half2 d = __hsub2(*reinterpret_cast<const __half2*>(&ch), *reinterpret_cast<const __half2*>(&kh));
+        r[e] = *reinterpret_cast<const uint32_t*>(&d);
     }
 }
 
-// Thread 0: every plan's hi and lo chunk c into a Phi stage (plan q's hi chunk at
-// 256 col_q bytes, its lo chunk m16_q x 128 bytes after it).
+// Every plan's hi and lo chunk c into a Phi stage (plan q's hi chunk at
+// phi_off_q, its lo chunk m16_q x 128 bytes after it).
 __device__ __forceinline__ void load_phi(const EncLaunch& L, uint8_t* stage, uint64_t* full, int c) {
     mbar_arrive_expect_tx(full, phi_stage_bytes(L.m16_total));
     for (int q = 0; q < L.n_plans; ++q) {
         const EncPlan& P = L.p[q];
         const uint32_t cb = (uint32_t)P.m16 * kChunk * 2;                  // one chunk of one image
         const size_t img = (size_t)P.m16 * L.gs.n * 2;
-        uint8_t* dst = stage + 2u * (uint32_t)P.col * kChunk * 2u;
+        uint8_t* dst = stage + P.phi_off;
         bulk_g2s(dst, P.img + (size_t)c * cb, cb, full);
         bulk_g2s(dst + cb, P.img + img + (size_t)c * cb, cb, full);
     }
 }
 
-constexpr int kConvWarps = kT / 32;                 // warps 1 .. 16: residual chunks and y
-constexpr int kThreadsE = 32 + kT;                  // warp 0: Phi copies and MMAs
-constexpr uint32_t kBarConv = 1;                    // named barrier of the converter warps
+// After a tile's last chunk: y = D 2^-e (paired: D_hi + D_lo) through shared
+// memory, 64 columns at a time; row r's column x sits at [r][x ^ (r % 32)], so
+// that the TMEM-side writes (one row per lane) and the row-contiguous reads both
+// avoid bank conflicts.  Converter warp (q, h) reads lanes 32 q .. and 16
+// columns of each slice.
+__device__ __forceinline__ void write_y(const EncLaunch& L, float* ys, uint32_t tmem, int tile, int rows, int q,
+                                        int h, int warp, int lane, bool ok) {
+    const int r = 32 * q + lane;
+    const int live = min(kTile, rows - tile * kTile);
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * q) << 16);
+    for (int pi = 0; pi < L.n_plans; ++pi) {
+        const EncPlan& P = L.p[pi];
+        for (int s0 = 0; s0 < P.m16; s0 += 64) {
+#pragma unroll
+            for (int cc = 0; cc < 16; cc += 8) {
+                const int col = s0 + 16 * h + cc;
+                if (col < P.m16) {
+                    uint32_t d[8], dl[8];
+                    tmem_ld8(lane_base + (uint32_t)(P.col + col), d);
+                    if (L.paired) tmem_ld8(lane_base + (uint32_t)(P.col + P.m16 + col), dl);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const float v = __uint_as_float(d[i]) + (L.paired ? __uint_as_float(dl[i]) : 0.f);
+                        ys[r * 64 + ((16 * h + cc + i) ^ (r & 31))] = v * P.scale;
+                    }
+                }
+            }
+            named_sync(kBarConv, kConvWarps * 32);
+            // a warp stores whole row segments: rows w - 1, w + 15, ..., lanes along
+            // the slice's columns
+            const int width = min(64, P.m - s0);
+            float* yt = P.y + (size_t)tile * kTile * P.m + s0;
+            if (ok)
+                for (int rr = warp - 1; rr < live; rr += kConvWarps)
+                    for (int cl = lane; cl < width; cl += 32) yt[rr * P.m + cl] = ys[rr * 64 + (cl ^ (rr & 31))];
+            named_sync(kBarConv, kConvWarps * 32);
+        }
+    }
+}
 
-template <int S, int D>
-__global__ void __launch_bounds__(kThreadsE, 1) k_encode_tcg(const __grid_constant__ EncLaunch L) {
+template <int S>
+__global__ void __maxnreg__(96) k_encode_tcg(const __grid_constant__ EncLaunch L) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
     const int mt = L.m16_total;
     const uint32_t kPhiStage = phi_stage_bytes(mt);
-    uint8_t* phi_s = sm;
-    uint8_t* r_s = sm + off_r(S, mt);
-    uint8_t* raw_s = sm + off_raw(S, mt);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + off_bar(S, D, mt));
+    float* ys = reinterpret_cast<float*>(sm + off_y(S, mt));
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + off_bar(S, mt));
     uint64_t* phi_full = bar;              // [S]: the stage's Phi chunks have landed
-    uint64_t* r_full = bar + S;            // [S]: the converter warps have formed the stage's residual chunk
-    uint64_t* mma_done = bar + 2 * S;      // [S]: the stage's MMAs have read both its buffers
+    uint64_t* r_full = bar + S;            // [S]: the converters have stored the stage's residual chunk
+    uint64_t* mma_done = bar + 2 * S;      // [S]: the stage's MMAs are done (Phi and residual stage free)
     uint64_t* acc_full = bar + 3 * S;      // the tile's accumulators are complete
-    uint64_t* acc_empty = bar + 3 * S + 1; // the converter warps have read them out
+    uint64_t* acc_empty = bar + 3 * S + 1; // the converters have read them out
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 3 * S + 2);
     int* abort = reinterpret_cast<int*>(bar + 3 * S + 3);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nch = L.gs.n / kChunk;                      // 1, 4 or 16
+    const int nch = L.gs.n / kChunk;                        // 1, 4 or 16
     const int lg_nch = nch == 1 ? 0 : nch == 4 ? 2 : 4;
-    const uint32_t ncols = mt <= 32 ? 32u : mt <= 64 ? 64u : mt <= 128 ? 128u : mt <= 256 ? 256u : 512u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < S; ++s) {
             mbar_init(&phi_full[s], 1);
@@ -244,7 +274,7 @@ __global__ void __launch_bounds__(kThreadsE, 1) k_encode_tcg(const __grid_consta
     }
     if (warp == 0) {
         __syncwarp();
-        tmem_alloc(tmem_slot, ncols);
+        tmem_alloc(tmem_slot, (uint32_t)L.ncols);
         tmem_relinquish();
     }
     fence_before_sync();
@@ -258,18 +288,12 @@ __global__ void __launch_bounds__(kThreadsE, 1) k_encode_tcg(const __grid_consta
     auto tile_of = [&](int g) { return (int)blockIdx.x + (g >> lg_nch) * (int)gridDim.x; };
     if (warp == 0) {
         if (lane == 0) {
-            // ---- Phi copies, S - 1 chunks ahead, and every MMA ----
+            // ---- every MMA ----
             const uint32_t s_base = smem_u32(sm);
             bool ok = true;
-            int phi_last[S], mma_last[S];   // each stage's last copy and commit (for the drain)
+            int mma_last[S];
 #pragma unroll
-            for (int s = 0; s < S; ++s) phi_last[s] = mma_last[s] = -1;
-#pragma unroll
-            for (int g = 0; g < S - 1; ++g)
-                if (g < total) {
-                    load_phi(L, phi_s + (uint32_t)g * kPhiStage, &phi_full[g], g & (nch - 1));
-                    phi_last[g] = g;
-                }
+            for (int s = 0; s < S; ++s) mma_last[s] = -1;
             for (int g = 0; g < total; ++g) {
                 const int s = g % S, c = g & (nch - 1);
                 const uint32_t u = (uint32_t)(g / S);
@@ -279,128 +303,118 @@ __global__ void __launch_bounds__(kThreadsE, 1) k_encode_tcg(const __grid_consta
                 ok = wait_e(&r_full[s], u & 1, abort, L.err) && ok;
                 fence_after_sync();
                 if (ok) {
-                    const uint64_t da = desc_sw128(s_base + off_r(S, mt) + (uint32_t)s * kRStage, 16, 1024);
+                    const uint32_t a0 = tmem + (uint32_t)(L.r_col + 32 * s);
                     for (int q = 0; q < L.n_plans; ++q) {
                         const EncPlan& P = L.p[q];
-                        const uint32_t po = (uint32_t)s * kPhiStage + 2u * (uint32_t)P.col * kChunk * 2u;
+                        const uint32_t po = (uint32_t)s * kPhiStage + (uint32_t)P.phi_off;
                         const uint64_t dh = desc_sw128(s_base + po, 16, 1024);
-                        const uint64_t dl = desc_sw128(s_base + po + (uint32_t)P.m16 * kChunk * 2u, 16, 1024);
-                        const uint32_t id = idesc_f16(128, (uint32_t)P.m16, 0u, 0u, 0u);
+                        const uint32_t d = tmem + (uint32_t)P.col;
+                        if (L.paired) {
+                            // hi and lo rows as one B operand: D_hi, D_lo side by side
+                            const uint32_t id = idesc_f16(128, 2u * (uint32_t)P.m16, 0u, 0u, 0u);
 #pragma unroll
-                        for (uint32_t ks = 0; ks < kChunk / 16; ++ks) {
-                            mma_f16(tmem + (uint32_t)P.col, da + 2 * ks, dh + 2 * ks, id, (c > 0 || ks > 0) ? 1u : 0u);
-                            mma_f16(tmem + (uint32_t)P.col, da + 2 * ks, dl + 2 * ks, id, 1u);
+                            for (uint32_t ks = 0; ks < kChunk / 16; ++ks)
+                                mma_f16_tmem_a(d, a0 + 8 * ks, dh + 2 * ks, id, (c > 0 || ks > 0) ? 1u : 0u);
+                        } else {
+                            const uint64_t dl = desc_sw128(s_base + po + (uint32_t)P.m16 * kChunk * 2u, 16, 1024);
+                            const uint32_t id = idesc_f16(128, (uint32_t)P.m16, 0u, 0u, 0u);
+#pragma unroll
+                            for (uint32_t ks = 0; ks < kChunk / 16; ++ks) {
+                                mma_f16_tmem_a(d, a0 + 8 * ks, dh + 2 * ks, id, (c > 0 || ks > 0) ? 1u : 0u);
+                                mma_f16_tmem_a(d, a0 + 8 * ks, dl + 2 * ks, id, 1u);
+                            }
                         }
                     }
                     mma_commit(&mma_done[s]);
                     mma_last[s] = g;
                     if (c == nch - 1) mma_commit(acc_full);
                 }
-                // Phi for chunk g + S - 1, into the stage whose last reader was chunk g - 1
-                const int gn = g + S - 1;
-                if (gn < total) {
-                    const int sn = gn % S;
-                    if (gn >= S) ok = wait_e(&mma_done[sn], (uint32_t)((gn / S - 1) & 1), abort, L.err) && ok;
-                    if (ok) {
-                        load_phi(L, phi_s + (uint32_t)sn * kPhiStage, &phi_full[sn], gn & (nch - 1));
-                        phi_last[sn] = gn;
-                    }
+            }
+            // MMAs still in flight after a wait gave up: wait for them (bounded)
+#pragma unroll
+            for (int s = 0; s < S; ++s)
+                if (mma_last[s] >= 0) mbar_wait(&mma_done[s], (uint32_t)((mma_last[s] / S) & 1), kWaitNs);
+        }
+        __syncwarp();
+    } else if (warp == kPhiWarp) {
+        if (lane == 0) {
+            // ---- Phi chunks, S ahead: stage s once its previous MMAs are done ----
+            bool ok = true;
+            int phi_last[S];
+#pragma unroll
+            for (int s = 0; s < S; ++s) phi_last[s] = -1;
+            for (int g = 0; g < total && ok; ++g) {
+                const int s = g % S;
+                if (g >= S) ok = wait_e(&mma_done[s], (uint32_t)((g / S - 1) & 1), abort, L.err) && ok;
+                if (ok) {
+                    load_phi(L, sm + (uint32_t)s * kPhiStage, &phi_full[s], g & (nch - 1));
+                    phi_last[s] = g;
                 }
             }
-            // copies and MMAs still in flight after a wait gave up: wait for each
-            // stage's last ones (bounded; they have completed on the normal path)
+            // copies still in flight after a wait gave up: wait for them (bounded)
 #pragma unroll
-            for (int s = 0; s < S; ++s) {
+            for (int s = 0; s < S; ++s)
                 if (phi_last[s] >= 0) mbar_wait(&phi_full[s], (uint32_t)((phi_last[s] / S) & 1), kWaitNs);
-                if (mma_last[s] >= 0) mbar_wait(&mma_done[s], (uint32_t)((mma_last[s] / S) & 1), kWaitNs);
-            }
         }
         __syncwarp();
     } else {
-        // ---- residual chunks (D chunks of bytes in flight) and y ----
-        const int t = threadIdx.x - 32;
+        // ---- converters: residual chunks into tensor memory, then y ----
+        // warp (q, h): blocks 32 q + lane, pixel group h (16 pixels)
+        const int q = warp & 3, h = (warp - 1) >> 2;
+        const int b = 32 * q + lane;                       // the thread's block of every tile
+        const uint32_t r_lane = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L.r_col + 8 * h);
         bool ok = true;
-        ItemBase pf;                 // the item bases of the tile the prefetch is in
+        Src pf;                                            // the prefetch's tile
         int pf_tile = -1;
-        auto prefetch = [&](int gp, uint8_t* slot) {
+        uint4 cv[kDepth], kv[kDepth];                      // chunk g in slot g % kDepth
+        auto fetch = [&](int gp, uint4& c_, uint4& k_) {
             const int tp = tile_of(gp);
             if (tp != pf_tile) {
-                item_bases(L, tp, rows, t, pf);
+                src_of(L, tp, rows, b, h, pf);
                 pf_tile = tp;
             }
-            load_raw(L, slot, pf, gp & (nch - 1), t);
+            load_bytes(L, pf, gp & (nch - 1), c_, k_);
         };
 #pragma unroll
-        for (int g = 0; g < D; ++g) {
-            if (g < total) prefetch(g, raw_s + (uint32_t)g * kRawSlot);
-            cp_async_commit();
-        }
+        for (int j = 0; j < kDepth; ++j)
+            if (j < total) fetch(j, cv[j], kv[j]);
         uint32_t ph_acc = 0;
-        for (int g = 0; g < total; ++g) {
-            const int s = g % S, c = g & (nch - 1);
-            const uint32_t u = (uint32_t)(g / S);
-            uint8_t* raw = raw_s + (uint32_t)(g % D) * kRawSlot;
-            cp_async_wait_group<D - 1>();                   // this thread's bytes of chunk g
-            if (g >= S) ok = wait_e(&mma_done[s], (u - 1) & 1, abort, L.err) && ok;   // R stage s is free
-            form_residual(raw, r_s + (uint32_t)s * kRStage, t);
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&r_full[s]);
-            if (g + D < total) prefetch(g + D, raw);
-            cp_async_commit();
-            if (c == nch - 1) {
-                // y = D 2^-e through shared memory (the residual ring: every MMA of
-                // the tile has completed), 64 columns at a time; row r's column x
-                // sits at [r][x ^ (r % 32)], so that the TMEM-side writes (one row
-                // per lane) and the row-contiguous reads both avoid bank conflicts
-                ok = wait_e(acc_full, ph_acc, abort, L.err) && ok;
-                ph_acc ^= 1;
-                fence_after_sync();
-                const int tile = tile_of(g);
-                float* ys = reinterpret_cast<float*>(r_s);
-                // four warps per TMEM lane quarter, 16 columns of a slice each
-                const int q4 = warp & 3, qc = (warp - 1) >> 2;
-                const int r = 32 * q4 + lane;
-                const int live = min(kTile, rows - tile * kTile);
-                for (int q = 0; q < L.n_plans; ++q) {
-                    const EncPlan& P = L.p[q];
-                    for (int s0 = 0; s0 < P.m16; s0 += 64) {
+        for (int g0 = 0; g0 < total; g0 += kDepth) {
 #pragma unroll
-                        for (int cc = 0; cc < 16; cc += 8) {
-                            const int col = s0 + 16 * qc + cc;
-                            if (col < P.m16) {
-                                uint32_t d[8];
-                                tmem_ld8(tmem + ((uint32_t)(32 * q4) << 16) + (uint32_t)(P.col + col), d);
-                                tmem_wait_ld();
-#pragma unroll
-                                for (int i = 0; i < 8; ++i)
-                                    ys[r * 64 + ((16 * qc + cc + i) ^ (r & 31))] = __uint_as_float(d[i]) * P.scale;
-                            }
-                        }
-                        named_sync(kBarConv, kT);
-                        // a warp stores whole row segments: rows w, w + 16, ..., lanes
-                        // along the slice's columns
-                        const int width = min(64, P.m - s0);
-                        float* yt = P.y + (size_t)tile * kTile * P.m + s0;
-                        if (ok)
-                            for (int rr = warp - 1; rr < live; rr += kConvWarps)
-                                for (int cl = lane; cl < width; cl += 32)
-                                    yt[rr * P.m + cl] = ys[rr * 64 + (cl ^ (rr & 31))];
-                        named_sync(kBarConv, kT);
+            for (int j = 0; j < kDepth; ++j) {
+                const int g = g0 + j;
+                if (g < total) {
+                    const int s = g % S, c = g & (nch - 1);
+                    const uint32_t u = (uint32_t)(g / S);
+                    uint32_t r[8];
+                    residual16(cv[j], kv[j], r);
+                    if (g + kDepth < total) fetch(g + kDepth, cv[j], kv[j]);
+                    // the stage's previous MMAs are done before it is overwritten
+                    if (g >= S) ok = wait_e(&mma_done[s], (u - 1) & 1, abort, L.err) && ok;
+                    fence_after_sync();
+                    tmem_st8(r_lane + (uint32_t)(32 * s), r);
+                    tmem_wait_st();
+                    fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&r_full[s]);
+                    if (c == nch - 1) {
+                        ok = wait_e(acc_full, ph_acc, abort, L.err) && ok;
+                        ph_acc ^= 1;
+                        fence_after_sync();
+                        write_y(L, ys, tmem, tile_of(g), rows, q, h, warp, lane, ok);
+                        // this warp's accumulator reads are done: the next tile may overwrite them
+                        fence_before_sync();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(acc_empty);
                     }
                 }
-                // this warp's accumulator reads are done: the next tile may overwrite them
-                fence_before_sync();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(acc_empty);
             }
         }
-        cp_async_wait_all();
     }
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (warp == 0) tmem_dealloc(tmem, ncols);
+    if (warp == 0) tmem_dealloc(tmem, (uint32_t)L.ncols);
 }
 
 // The images of Phi * 2^e for this kernel: fp16 hi then fp16 lo, each m16 x n,
@@ -421,7 +435,7 @@ __global__ void k_phi_images_g(const float* __restrict__ phi, uint8_t* __restric
     *reinterpret_cast<__half*>(img + (size_t)m16 * n * 2 + off) = hl;
 }
 
-template <int S, int D>
+template <int S>
 cudaError_t launch_shape(const EncLaunch& L, int grid, cudaStream_t s) {
     // the shared-memory limit is raised to the device maximum once per shape and
     // device (a driver call per launch would cost microseconds of host time)
@@ -431,11 +445,11 @@ cudaError_t launch_shape(const EncLaunch& L, int grid, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(raised.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(k_encode_tcg<S, D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
+        e = cudaFuncSetAttribute(k_encode_tcg<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemMax);
         if (e != cudaSuccess) return e;
         raised.fetch_or(bit, std::memory_order_acq_rel);
     }
-    k_encode_tcg<S, D><<<grid, kThreadsE, smem_bytes(S, D, L.m16_total), s>>>(L);
+    k_encode_tcg<S><<<grid, kThreadsE, smem_bytes(S, L.m16_total), s>>>(L);
     return cudaGetLastError();
 }
 
@@ -470,10 +484,15 @@ cudaError_t launch_encode_tcg_multi(const cs_plan* const* plans, float* const* y
     const long long tiles = (rows + kTile - 1) / kTile;
     const int sms = plans[0]->ctx->sm_count;
     const int grid = (int)(tiles < sms ? tiles : sms);
-    // 8-byte frame loads when every block row segment starts on an 8-byte
-    // boundary and no block is cropped at the right edge
-    const int vec = gs.w % 8 == 0 && gs.w % gs.b == 0 && (reinterpret_cast<uintptr_t>(frames) & 7) == 0;
-    // consecutive plans whose accumulators fit one launch share it
+    // frame loads: 16 bytes when a thread's 16 pixels are one aligned row piece
+    // (16 x 16 and 32 x 32 blocks), else 8 bytes, when every segment starts on
+    // its boundary and no block is cropped at the right edge; else bytes
+    const uintptr_t fa = reinterpret_cast<uintptr_t>(frames);
+    const bool whole = gs.w % gs.b == 0;
+    const int vec = whole && gs.b >= 16 && gs.w % 16 == 0 && (fa & 15) == 0 ? 2
+                    : whole && gs.w % 8 == 0 && (fa & 7) == 0           ? 1
+                                                                         : 0;
+    // consecutive plans whose images fit one launch share it
     for (int i = 0; i < n_plans;) {
         EncLaunch L{};
         L.frames = frames;
@@ -481,6 +500,7 @@ cudaError_t launch_encode_tcg_multi(const cs_plan* const* plans, float* const* y
         L.err = plans[i]->ctx->err_dev;
         L.vec = vec;
         int mt = 0, k = 0;
+        bool pair_ok = true;
         while (i + k < n_plans && k < kMaxEncPlans) {
             const cs_plan* p = plans[i + k];
             const int m16 = m16_of_e(p->m);
@@ -490,19 +510,40 @@ cudaError_t launch_encode_tcg_multi(const cs_plan* const* plans, float* const* y
             P.y = ys[i + k];
             P.m = p->m;
             P.m16 = m16;
-            P.col = mt;
+            P.phi_off = 2 * mt * kChunk * 2;
             P.scale = ldexpf(1.f, -p->tc_ephi);
+            pair_ok = pair_ok && 2 * m16 <= kMaxM16;
             mt += m16;
             ++k;
         }
         L.n_plans = k;
         L.m16_total = mt;
-        // the deepest pipeline that fits
-        cudaError_t e;
-        if (smem_bytes(3, 4, mt) <= kSmemMax) e = launch_shape<3, 4>(L, grid, s);
-        else if (smem_bytes(2, 4, mt) <= kSmemMax) e = launch_shape<2, 4>(L, grid, s);
-        else if (smem_bytes(2, 3, mt) <= kSmemMax) e = launch_shape<2, 3>(L, grid, s);
-        else e = launch_shape<2, 2>(L, grid, s);
+        // the deepest Phi ring whose shared memory and tensor-memory columns fit,
+        // hi and lo paired where their accumulators fit beside the residual stages
+        int stages = 0;
+        for (int st : {4, 3, 2}) {
+            if (smem_bytes(st, mt) > kSmemMax) continue;
+            const bool paired = pair_ok && 2 * mt + 32 * st <= 512;
+            const int acc = paired ? 2 * mt : mt;
+            const int r_col = (acc + 31) / 32 * 32;
+            if (r_col + 32 * st > 512) continue;
+            stages = st;
+            L.paired = paired;
+            L.r_col = r_col;
+            int nc = 32;
+            while (nc < r_col + 32 * st) nc *= 2;
+            L.ncols = nc;
+            break;
+        }
+        if (!stages) return cudaErrorInvalidConfiguration;
+        int col = 0;
+        for (int q = 0; q < k; ++q) {
+            L.p[q].col = col;
+            col += L.paired ? 2 * L.p[q].m16 : L.p[q].m16;
+        }
+        const cudaError_t e = stages == 4 ? launch_shape<4>(L, grid, s)
+                              : stages == 3 ? launch_shape<3>(L, grid, s)
+                                            : launch_shape<2>(L, grid, s);
         if (e != cudaSuccess) return e;
         i += k;
     }

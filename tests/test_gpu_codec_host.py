@@ -1,7 +1,7 @@
-"""cs_codec_host: the whole codec of a clip from host memory (copy-in, encode
-under every plan, one batched decode, PSNR, copy-out) gives, bit for bit, what
-the device-pointer calls give, and matches the FP64 oracle; mismatched clip
-shapes are refused before anything is enqueued."""
+"""cs_codec_host: the whole codec of a clip from host memory (copy-in, one
+batched encode under every plan, one batched decode, PSNR, copy-out) gives, bit
+for bit, what the device-pointer calls give, and matches the FP64 oracle;
+mismatched clip shapes are refused before anything is enqueued."""
 import numpy as np
 import pytest
 
@@ -45,9 +45,10 @@ def test_codec_host_equals_device_path(B, h, w, gop, n_gops, b, ms, iters):
         keys = f_dev[::gop].contiguous()
         cs_idx = [t for t in range(gop * n_gops) if t % gop]
         cs_dev = f_dev[cs_idx].contiguous()
+        ys = [torch.empty((n_cs, nblk, m), dtype=torch.float32, device="cuda") for m in ms]
+        B.cs_encode_batch(ctx, plans, params, f_dev, ys)
         for i, m in enumerate(ms):
-            y = torch.empty((n_cs, nblk, m), dtype=torch.float32, device="cuda")
-            B.cs_encode_gop(plans[i], params[i], f_dev, y)
+            y = ys[i]
             of = torch.empty((n_cs, h, w), dtype=torch.float32, device="cuda")
             ou = torch.empty((n_cs, h, w), dtype=torch.uint8, device="cuda")
             B.cs_decode_gop(plans[i], params[i], keys, y, of, ou)

@@ -1,8 +1,10 @@
 """cs_encode_batch: several plans of one block size measure one clip in shared
-tensor-core launches (the clip read once per launch).  Each plan's y is
-bit-identical to its own cs_encode_gop and matches the FP64 oracle; plans whose
-accumulators exceed one launch split into several; a plain-engine plan runs on
-the SIMT encode beside them; calls that differ in their clip are refused."""
+tensor-core launches (the clip read once per launch).  Each plan's y matches its
+own cs_encode_gop to FP32 rounding (a launch with room sums a plan's hi and lo
+products in separate accumulators, a crowded one in one: the order of the sums
+differs) and the FP64 oracle; plans whose images exceed one launch split into
+several; a plain-engine plan runs on the SIMT encode beside them; calls that
+differ in their clip are refused."""
 import numpy as np
 import pytest
 
@@ -64,7 +66,8 @@ def test_batch_equals_single_calls_and_the_oracle(B, ctx, h, w, gop, n_f, b, ms)
     frames = scenes.surveillance_video(n_f, h, w, seed=9)
     yb, ys = _run(B, ctx, frames, gop, b, ms)
     for i, m in enumerate(ms):
-        assert np.array_equal(yb[i], ys[i]), "plan %d (M=%d) differs from its own call" % (i, m)
+        d = np.linalg.norm(yb[i] - ys[i]) / np.linalg.norm(ys[i])
+        assert d <= 1e-6, "plan %d (M=%d) differs from its own call: %.3g" % (i, m, d)
         ref = O.encode(O.Plan(b * b, m, 7 + i), frames, gop)
         err = np.linalg.norm(yb[i] - ref) / np.linalg.norm(ref)
         print("batch encode b=%d M=%d: rel-l2 %.3g" % (b, m, err))
@@ -77,7 +80,7 @@ def test_batch_with_a_plain_engine_plan(B, ctx):
     engines = [B.CS_ENGINE_AUTO, B.CS_ENGINE_PLAIN, B.CS_ENGINE_AUTO]
     yb, ys = _run(B, ctx, frames, 4, 16, ms, engines)
     for i, m in enumerate(ms):
-        assert np.array_equal(yb[i], ys[i])
+        assert np.linalg.norm(yb[i] - ys[i]) / np.linalg.norm(ys[i]) <= 1e-6
         ref = O.encode(O.Plan(256, m, 7 + i), frames, 4)
         assert np.linalg.norm(yb[i] - ref) / np.linalg.norm(ref) <= 1e-5
 
