@@ -70,7 +70,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the decode of one
 # step, from one ncu capture of that exact configuration (FP32-grade, batched);
 # reported as roofline.traffic for it only, null for anything else
-DECODE_DRAM_BYTES = {"cif": 62_840_000}
+DECODE_DRAM_BYTES = {"cif": 62_840_000, "720p": 24_975_000_000}
 FP32_LANES_PER_SM = 128
 
 
