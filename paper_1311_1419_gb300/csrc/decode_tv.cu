@@ -1,18 +1,20 @@
 // TV recovery of every measured block (Eq. 1 with the total variation, the
 // regulariser of the paper's TVAL3 decoder, Sec. 4), followed by the key
-// add-back of Eq. (4).  Per block, min ||D r||_1 s.t. Phi r = y by the
-// augmented Lagrangian / alternating-direction scheme (Li, Yin, Jiang, Zhang,
-// Comput. Optim. Appl. 2013): with the splitting w = D r (D the forward
-// differences along rows and columns, zero at the last column / row), each
-// iteration takes
+// add-back of Eq. (4).  Per block, min ||D r||_1 s.t. Phi r = y by the augmented
+// Lagrangian / alternating-direction scheme (Li, Yin, Jiang, Zhang, Comput.
+// Optim. Appl. 2013): with the splitting w = D r (D the forward differences
+// along rows and columns, zero at the last column / row), each iteration takes
 //   w   = shrink(D r - nu / beta, 1 / beta)
 //   r  -= alpha (D^T (beta (D r - w) - nu) + Phi^T (mu (Phi r - y) - lam))
 //   nu -= beta (D r - w),  lam -= mu (Phi r - y)
 // with alpha = 1 / (8 beta + mu L) (8 bounds ||D||^2, L the plan's Lipschitz
-// constant of Phi Phi^T), from r = nu = lam = 0, for a fixed count.  A CTA
-// recovers R blocks with their state in shared memory; the residual works in
-// the pixel domain, so the reconstruction is the add-back alone.  Phi is read
-// from global memory (L1/L2 resident), once per R blocks.
+// constant of Phi Phi^T), from r = nu = lam = 0, for a fixed count.  This file's
+// kernel is the plain one (SIMT FP32, every shape; 16 x 16 blocks with M <= 128
+// run on the tensor cores, decode_tc.cu).  It keeps q = nu + beta w instead of
+// nu and w: the difference term of the gradient is D^T (beta D r - q) and the
+// multiplier step is nu' = q - beta D r', so a block's state is r, r' (the next
+// iterate), q (2 N), y, lam and Phi r - y: 4 N + 3 M values, and a CTA recovers
+// R blocks (up to 12 of 32 x 32) sharing every load of Phi (read from L2).
 #include <math.h>
 
 #include "internal.h"
@@ -23,14 +25,13 @@ int make_shape(const cs_plan* plan, const cs_params* p, GopShape* gs);
 
 namespace {
 
-constexpr int kT = 256;
+constexpr int kT = 512;
 
 __device__ __forceinline__ float shrink(float v, float t) { return v - fminf(fmaxf(v, -t), t); }
 
-// R blocks per CTA share every load of Phi (the two Phi products are each
-// register-blocked: 4 rows of Phi against the R blocks' vectors per pass), and
-// each block's iteration is the one above.
-template <int R>
+// R blocks per CTA, JB pixels per thread in the Phi^T product (n = JB x 512 for
+// 32 x 32 blocks, else one pixel per thread).
+template <int R, int JB>
 __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
                                                  const float* __restrict__ yall,
                                                  const uint8_t* __restrict__ keys,
@@ -40,19 +41,17 @@ __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
     extern __shared__ float sm[];
     const int n = gs.n, m = gs.m, b = gs.b;
     const int mp = (m + 3) & ~3;                // rows of the M-vectors, 16-byte aligned
-    float* r = sm;                  // [R][N] residual blocks
-    float* dr = r + R * n;          // [R][2N] D r: row differences, then column differences
-    float* nu = dr + 2 * R * n;     // [R][2N] multiplier of D r = w
-    float* wv = nu + 2 * R * n;     // [R][2N] w
-    float* tv = wv + 2 * R * n;     // [R][2N] beta (D r - w) - nu
-    float* ys = sm + ((9 * R * n + 3) & ~3);    // [R][mp] y (zero beyond M)
-    float* lam = ys + R * mp;       // [R][mp] multiplier of Phi r = y
-    float* rho = lam + R * mp;      // [R][mp] Phi r - y, then mu rho - lam
+    float* ra = sm;                             // [R][N] r
+    float* rb = ra + R * n;                     // [R][N] the next r
+    float* qs = rb + R * n;                     // [R][2N] q: row differences, then column differences
+    float* ys = qs + 2 * R * n;                 // [R][mp] y (zero beyond M)
+    float* lam = ys + R * mp;                   // [R][mp] multiplier of Phi r = y
+    float* rho = lam + R * mp;                  // [R][mp] Phi r - y, then mu (Phi r - y) - lam
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long total = (long long)gs.n_cs * gs.nblk;
     const long long row0 = (long long)blockIdx.x * R;
-    for (int e = tid; e < R * n; e += kT) r[e] = 0.f;
-    for (int e = tid; e < 2 * R * n; e += kT) dr[e] = nu[e] = 0.f;
+    for (int e = tid; e < R * n; e += kT) ra[e] = 0.f;
+    for (int e = tid; e < 2 * R * n; e += kT) qs[e] = 0.f;
     for (int e = tid; e < R * mp; e += kT) {
         const int q = e / mp, i = e % mp;
         // blocks beyond the call's last measure nothing: their iterates stay 0
@@ -64,61 +63,76 @@ __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
     __syncthreads();
     const float ib = 1.f / beta;
     for (int k = 0; k < iters; ++k) {
-        // w-step and the difference-side term of the gradient
-        for (int e = tid; e < 2 * R * n; e += kT) {
-            const float w = shrink(dr[e] - nu[e] * ib, ib);
-            wv[e] = w;
-            tv[e] = beta * (dr[e] - w) - nu[e];
-        }
         for (int e = tid; e < R * mp; e += kT) rho[e] = mu * rho[e] - lam[e];
         __syncthreads();
-        // r-step: one gradient step of length alpha; D^T tv, then Phi^T rho, 4 rows of
-        // Phi per pass against every block's rho (rows m .. mp - 1 of rho are zero)
-        for (int j = tid; j < n; j += kT) {
-            const int pr = j / b, pc = j % b;
-            float g[R];
+        // r' = r - alpha (D^T (beta D r - q) + Phi^T P): the Phi^T P term for the
+        // thread's JB pixels of all R blocks, 4 rows of Phi per pass (rows >= m zero)
+        for (int j0 = tid; j0 < n; j0 += JB * kT) {
+            float g[JB][R];
 #pragma unroll
-            for (int q = 0; q < R; ++q) {
-                const float* t = tv + 2 * q * n;
-                float v = 0.f;
-                if (pc > 0) v += t[j - 1];
-                if (pc < b - 1) v -= t[j];
-                if (pr > 0) v += t[n + j - b];
-                if (pr < b - 1) v -= t[n + j];
-                g[q] = v;
-            }
+            for (int t = 0; t < JB; ++t)
+#pragma unroll
+                for (int q = 0; q < R; ++q) g[t][q] = 0.f;
             for (int i = 0; i < m; i += 4) {
-                float pv[4];
+                float pv[JB][4];
 #pragma unroll
-                for (int rr = 0; rr < 4; ++rr) pv[rr] = i + rr < m ? phi[(size_t)(i + rr) * n + j] : 0.f;
+                for (int t = 0; t < JB; ++t)
+#pragma unroll
+                    for (int rr = 0; rr < 4; ++rr)
+                        pv[t][rr] = (i + rr < m && j0 + t * kT < n) ? __ldg(phi + (size_t)(i + rr) * n + j0 + t * kT) : 0.f;
 #pragma unroll
                 for (int q = 0; q < R; ++q) {
-                    const float4 rv = *reinterpret_cast<const float4*>(rho + q * mp + i);
-                    g[q] = fmaf(pv[0], rv.x, g[q]);
-                    g[q] = fmaf(pv[1], rv.y, g[q]);
-                    g[q] = fmaf(pv[2], rv.z, g[q]);
-                    g[q] = fmaf(pv[3], rv.w, g[q]);
+                    const float4 pq = *reinterpret_cast<const float4*>(rho + q * mp + i);
+#pragma unroll
+                    for (int t = 0; t < JB; ++t) {
+                        g[t][q] = fmaf(pv[t][0], pq.x, g[t][q]);
+                        g[t][q] = fmaf(pv[t][1], pq.y, g[t][q]);
+                        g[t][q] = fmaf(pv[t][2], pq.z, g[t][q]);
+                        g[t][q] = fmaf(pv[t][3], pq.w, g[t][q]);
+                    }
                 }
             }
 #pragma unroll
-            for (int q = 0; q < R; ++q) r[q * n + j] -= alpha * g[q];
+            for (int t = 0; t < JB; ++t) {
+                const int j = j0 + t * kT;
+                if (j >= n) continue;
+                const int pr = j / b, pc = j % b;
+#pragma unroll
+                for (int q = 0; q < R; ++q) {
+                    const float* rq = ra + q * n;
+                    const float* q0 = qs + 2 * q * n;
+                    const float* q1 = q0 + n;
+                    const float rj = rq[j];
+                    // t_h and t_v at j and at the neighbours left and above
+                    const float th = pc < b - 1 ? beta * (rq[j + 1] - rj) - q0[j] : 0.f;
+                    const float tl = pc > 0 ? beta * (rj - rq[j - 1]) - q0[j - 1] : 0.f;
+                    const float tv = pr < b - 1 ? beta * (rq[j + b] - rj) - q1[j] : 0.f;
+                    const float tu = pr > 0 ? beta * (rj - rq[j - b]) - q1[j - b] : 0.f;
+                    rb[q * n + j] = rj - alpha * (tl - th + tu - tv + g[t][q]);
+                }
+            }
         }
         __syncthreads();
-        // D r at the new r
+        float* tmp = ra;
+        ra = rb;
+        rb = tmp;
+        // q' = nu' + beta w' with nu' = q - beta D r', w' = shrink(D r' - nu' / beta, 1 / beta)
         for (int e = tid; e < 2 * R * n; e += kT) {
             const int q = e / (2 * n), e2 = e % (2 * n);
-            const float* rq = r + q * n;
+            const float* rq = ra + q * n;
             const int j = e2 < n ? e2 : e2 - n;
             const int pr = j / b, pc = j % b;
-            float v = 0.f;
+            float d = 0.f;
             if (e2 < n) {
-                if (pc < b - 1) v = rq[j + 1] - rq[j];
+                if (pc < b - 1) d = rq[j + 1] - rq[j];
             } else {
-                if (pr < b - 1) v = rq[j + b] - rq[j];
+                if (pr < b - 1) d = rq[j + b] - rq[j];
             }
-            dr[e] = v;
+            const float nu = qs[e] - beta * d;
+            qs[e] = nu + beta * shrink(d - nu * ib, ib);
         }
-        // Phi r - y at the new r: a warp takes 4 rows of Phi against the R blocks
+        // Phi r' - y and lam -= mu (Phi r' - y): a warp takes 4 rows of Phi against
+        // the R blocks, its lanes 4 pixels at a time
         for (int i0 = warp * 4; i0 < m; i0 += (kT / 32) * 4) {
             float acc[4][R];
 #pragma unroll
@@ -126,16 +140,21 @@ __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
 #pragma unroll
                 for (int q = 0; q < R; ++q) acc[rr][q] = 0.f;
             const int nrow = m - i0 < 4 ? m - i0 : 4;
-            for (int col = lane; col < n; col += 32) {
-                float rv[R];
+            for (int c4 = lane; c4 < n / 4; c4 += 32) {
+                float4 pv[4];
 #pragma unroll
-                for (int q = 0; q < R; ++q) rv[q] = r[q * n + col];
+                for (int rr = 0; rr < 4; ++rr)
+                    pv[rr] = rr < nrow ? __ldg(reinterpret_cast<const float4*>(phi + (size_t)(i0 + rr) * n) + c4)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int rr = 0; rr < 4; ++rr) {
-                    if (rr < nrow) {
-                        const float pv = phi[(size_t)(i0 + rr) * n + col];
+                for (int q = 0; q < R; ++q) {
+                    const float4 rv = *reinterpret_cast<const float4*>(ra + q * n + 4 * c4);
 #pragma unroll
-                        for (int q = 0; q < R; ++q) acc[rr][q] = fmaf(pv, rv[q], acc[rr][q]);
+                    for (int rr = 0; rr < 4; ++rr) {
+                        acc[rr][q] = fmaf(pv[rr].x, rv.x, acc[rr][q]);
+                        acc[rr][q] = fmaf(pv[rr].y, rv.y, acc[rr][q]);
+                        acc[rr][q] = fmaf(pv[rr].z, rv.z, acc[rr][q]);
+                        acc[rr][q] = fmaf(pv[rr].w, rv.w, acc[rr][q]);
                     }
                 }
             }
@@ -145,14 +164,15 @@ __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
                 for (int q = 0; q < R; ++q) {
                     float v = acc[rr][q];
                     for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-                    if (lane == 0 && rr < nrow) rho[q * mp + i0 + rr] = v - ys[q * mp + i0 + rr];
+                    if (lane == 0 && rr < nrow) {
+                        const int e = q * mp + i0 + rr;
+                        const float rh = v - ys[e];
+                        rho[e] = rh;
+                        lam[e] -= mu * rh;
+                    }
                 }
             }
         }
-        __syncthreads();
-        // multipliers (each entry by the thread that reads it in the next w-step)
-        for (int e = tid; e < 2 * R * n; e += kT) nu[e] -= beta * (dr[e] - wv[e]);
-        for (int e = tid; e < R * mp; e += kT) lam[e] -= mu * rho[e];
         __syncthreads();
     }
     // add back the key (Eq. 4), crop
@@ -167,7 +187,7 @@ __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
         const int py = bi * b + j / b, px = bj * b + j % b;
         if (py >= gs.h || px >= gs.w) continue;
         const size_t off = (size_t)py * gs.w + px;
-        const float v = (float)keys[(size_t)g * frame_px + off] + r[e];
+        const float v = (float)keys[(size_t)g * frame_px + off] + ra[e];
         if (out_f32) out_f32[(size_t)c * frame_px + off] = v;
         if (out_u8) out_u8[(size_t)c * frame_px + off] = (uint8_t)fminf(fmaxf(rintf(v), 0.f), 255.f);
     }
@@ -175,22 +195,29 @@ __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
 
 size_t tv_smem(int n, int m, int nr) {
     const int mp = (m + 3) & ~3;
-    return (size_t)(((9 * nr * n + 3) & ~3) + 3 * nr * mp) * sizeof(float);
+    return (size_t)nr * (size_t)(4 * n + 3 * mp) * sizeof(float);
 }
 
-template <int R>
+template <int R, int JB>
 cudaError_t launch_tv(const float* phi, const float* y, const uint8_t* key, float* f32, uint8_t* u8,
                       const GopShape& gs, int iters, float beta, float mu, float alpha, cudaStream_t s) {
     const size_t smem = tv_smem(gs.n, gs.m, R);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_tv_plain<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tv_plain<R, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
     const long long rows = (long long)gs.n_cs * gs.nblk;
-    k_tv_plain<R><<<(unsigned)((rows + R - 1) / R), kT, smem, s>>>(phi, y, key, f32, u8, gs, iters, beta,
-                                                                    mu, alpha);
+    k_tv_plain<R, JB><<<(unsigned)((rows + R - 1) / R), kT, smem, s>>>(phi, y, key, f32, u8, gs, iters, beta,
+                                                                        mu, alpha);
     return cudaGetLastError();
+}
+
+template <int R>
+cudaError_t launch_tv_r(const float* phi, const float* y, const uint8_t* key, float* f32, uint8_t* u8,
+                        const GopShape& gs, int iters, float beta, float mu, float alpha, cudaStream_t s) {
+    return gs.n >= 1024 ? launch_tv<R, 2>(phi, y, key, f32, u8, gs, iters, beta, mu, alpha, s)
+                        : launch_tv<R, 1>(phi, y, key, f32, u8, gs, iters, beta, mu, alpha, s);
 }
 
 }  // namespace
@@ -226,20 +253,22 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
     if (params->engine == CS_ENGINE_TC)
         return fail(CS_EINVAL, "TV recovery's tensor-core kernel takes 16 x 16 blocks with M <= 128");
     if (tv_smem(gs.n, gs.m, 1) > 227 * 1024) return fail(CS_EINVAL, "block too large for the TV kernel");
-    // as many blocks per CTA (8, 4, 2 or 1) as keep the state under 100 KB, so that
-    // two CTAs share an SM
+    // as many blocks per CTA (12, 8, 4, 2 or 1) as fit the shared memory and still
+    // give every SM two CTAs' worth of work
     int nr = 1;
-    for (int r : {8, 4, 2})
-        if (tv_smem(gs.n, gs.m, r) <= 100 * 1024) {
+    for (int r : {12, 8, 4, 2})
+        if (tv_smem(gs.n, gs.m, r) <= 227 * 1024 && rows >= 2ll * r * plan->ctx->sm_count) {
             nr = r;
             break;
         }
     cudaError_t e;
+    const float* ph = plan->phi;
     switch (nr) {
-        case 8: e = launch_tv<8>(plan->phi, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
-        case 4: e = launch_tv<4>(plan->phi, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
-        case 2: e = launch_tv<2>(plan->phi, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
-        default: e = launch_tv<1>(plan->phi, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
+        case 12: e = launch_tv_r<12>(ph, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
+        case 8: e = launch_tv_r<8>(ph, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
+        case 4: e = launch_tv_r<4>(ph, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
+        case 2: e = launch_tv_r<2>(ph, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
+        default: e = launch_tv_r<1>(ph, y_dev, key_dev, frames_f32_dev, frames_u8_dev, gs, it, beta, mu, alpha, s); break;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cs_decode_gop_tv");
     return CS_OK;
