@@ -25,13 +25,12 @@ int make_shape(const cs_plan* plan, const cs_params* p, GopShape* gs);
 
 namespace {
 
-constexpr int kT = 512;
-
 __device__ __forceinline__ float shrink(float v, float t) { return v - fminf(fmaxf(v, -t), t); }
 
-// R blocks per CTA, JB pixels per thread in the Phi^T product (n = JB x 512 for
-// 32 x 32 blocks, else one pixel per thread).
-template <int R, int JB>
+// R blocks per CTA of kT threads, JB pixels per thread in the Phi^T product (n =
+// JB x kT for 32 x 32 blocks: 512 threads, 2 pixels each; else 256 threads, one
+// pixel each).
+template <int R, int JB, int kT>
 __global__ void __launch_bounds__(kT) k_tv_plain(const float* __restrict__ phi,
                                                  const float* __restrict__ yall,
                                                  const uint8_t* __restrict__ keys,
@@ -198,26 +197,26 @@ size_t tv_smem(int n, int m, int nr) {
     return (size_t)nr * (size_t)(4 * n + 3 * mp) * sizeof(float);
 }
 
-template <int R, int JB>
+template <int R, int JB, int kT>
 cudaError_t launch_tv(const float* phi, const float* y, const uint8_t* key, float* f32, uint8_t* u8,
                       const GopShape& gs, int iters, float beta, float mu, float alpha, cudaStream_t s) {
     const size_t smem = tv_smem(gs.n, gs.m, R);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_tv_plain<R, JB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tv_plain<R, JB, kT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
     const long long rows = (long long)gs.n_cs * gs.nblk;
-    k_tv_plain<R, JB><<<(unsigned)((rows + R - 1) / R), kT, smem, s>>>(phi, y, key, f32, u8, gs, iters, beta,
-                                                                        mu, alpha);
+    k_tv_plain<R, JB, kT><<<(unsigned)((rows + R - 1) / R), kT, smem, s>>>(phi, y, key, f32, u8, gs, iters,
+                                                                            beta, mu, alpha);
     return cudaGetLastError();
 }
 
 template <int R>
 cudaError_t launch_tv_r(const float* phi, const float* y, const uint8_t* key, float* f32, uint8_t* u8,
                         const GopShape& gs, int iters, float beta, float mu, float alpha, cudaStream_t s) {
-    return gs.n >= 1024 ? launch_tv<R, 2>(phi, y, key, f32, u8, gs, iters, beta, mu, alpha, s)
-                        : launch_tv<R, 1>(phi, y, key, f32, u8, gs, iters, beta, mu, alpha, s);
+    return gs.n >= 1024 ? launch_tv<R, 2, 512>(phi, y, key, f32, u8, gs, iters, beta, mu, alpha, s)
+                        : launch_tv<R, 1, 256>(phi, y, key, f32, u8, gs, iters, beta, mu, alpha, s);
 }
 
 }  // namespace
@@ -253,11 +252,13 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
     if (params->engine == CS_ENGINE_TC)
         return fail(CS_EINVAL, "TV recovery's tensor-core kernel takes 16 x 16 blocks with M <= 128");
     if (tv_smem(gs.n, gs.m, 1) > 227 * 1024) return fail(CS_EINVAL, "block too large for the TV kernel");
-    // as many blocks per CTA (12, 8, 4, 2 or 1) as fit the shared memory and still
-    // give every SM two CTAs' worth of work
+    // as many blocks per CTA (12 for 32 x 32 blocks, else up to 8: at 12 the
+    // 256-thread CTA's registers would allow only two per SM; then 4, 2 or 1) as
+    // fit the shared memory and still give every SM two CTAs' worth of work
     int nr = 1;
     for (int r : {12, 8, 4, 2})
-        if (tv_smem(gs.n, gs.m, r) <= 227 * 1024 && rows >= 2ll * r * plan->ctx->sm_count) {
+        if ((r < 12 || gs.n >= 1024) && tv_smem(gs.n, gs.m, r) <= 227 * 1024 &&
+            rows >= 2ll * r * plan->ctx->sm_count) {
             nr = r;
             break;
         }
