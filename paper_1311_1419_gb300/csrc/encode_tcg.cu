@@ -80,7 +80,10 @@ __host__ __device__ constexpr uint32_t phi_stage_bytes(int m16_total) {
 }
 __host__ __device__ constexpr uint32_t off_y(int s, int m16_total) { return (uint32_t)s * phi_stage_bytes(m16_total); }
 __host__ __device__ constexpr uint32_t off_bar(int s, int m16_total) { return off_y(s, m16_total) + kYStage; }
-__host__ __device__ constexpr uint32_t smem_bytes(int s, int m16_total) { return off_bar(s, m16_total) + 256u + 1024u; }
+// (at least 116 KB: one CTA per SM, so that no CTA waits for another's tensor memory)
+__host__ __device__ constexpr uint32_t smem_bytes(int s, int m16_total) {
+    return off_bar(s, m16_total) + 256u + 1024u > 116u * 1024u ? off_bar(s, m16_total) + 256u + 1024u : 116u * 1024u;
+}
 constexpr uint32_t kSmemMax = 232448;
 static_assert(smem_bytes(2, kMaxM16Total) <= kSmemMax, "the widest launch fits");
 
