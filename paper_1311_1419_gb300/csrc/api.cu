@@ -81,6 +81,8 @@ static size_t scratch_room(const cs_ctx* ctx) {
     return std::min(room, half > ctx->scratch_bytes ? half - ctx->scratch_bytes : (size_t)0);
 }
 
+size_t scratch_room_of(const cs_ctx* ctx) { return scratch_room(ctx); }
+
 // Validate a call's parameters against the plan and derive the GOP shape.
 int make_shape(const cs_plan* plan, const cs_params* p, GopShape* gs) {
     if (!plan || !p) return fail(CS_EINVAL, "null plan or params");
@@ -264,9 +266,11 @@ int cs_ctx_destroy(cs_ctx* ctx) {
     if (ctx->counters_dev) cudaFree(ctx->counters_dev);
     if (ctx->tc8_scratch) cudaFree(ctx->tc8_scratch);
     if (ctx->tcs_scratch) cudaFree(ctx->tcs_scratch);
+    if (ctx->tv_scratch) cudaFree(ctx->tv_scratch);
     slot_ring_destroy(&ctx->counter_ring);
     slot_ring_destroy(&ctx->tc8_ring);
     slot_ring_destroy(&ctx->tcs_ring);
+    slot_ring_destroy(&ctx->tv_ring);
     slot_ring_destroy(&ctx->stage_ring);
     if (ctx->stage) cudaFree(ctx->stage);
     delete ctx;
@@ -349,6 +353,12 @@ int cs_make_phi(cs_ctx* ctx, int32_t n, int32_t m, uint64_t seed, cs_plan** out)
             }
         }
         if (ranges[2] > 0.f) p->tc_ephi = (int)floor(log2(16384.0 / (double)ranges[2]));   // max |Phi| near 2^14
+        if (e == cudaSuccess && tcs && ranges[2] > 0.f) {
+            // the streaming TV decode's images of Phi (the streaming decode's layouts)
+            e = cudaMalloc(&p->phi_tcs, tcs_operand_bytes(n, m));
+            if (e == cudaSuccess) e = launch_tcs_images(p->phi, p->phi_tcs, n, m, p->tc_ephi, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        }
         if (e == cudaSuccess && tc_chip && n == 256 && ranges[2] > 0.f) {
             // the 16 x 16 tensor-core encode's Phi images
             e = cudaMalloc(&p->phi_tc, tc_operand_bytes(n, m));
@@ -398,6 +408,7 @@ int cs_plan_destroy(cs_plan* p) {
     if (p->dct) cudaFree(p->dct);
     if (p->a_tc) cudaFree(p->a_tc);
     if (p->a_tcs) cudaFree(p->a_tcs);
+    if (p->phi_tcs) cudaFree(p->phi_tcs);
     if (p->phi_tc) cudaFree(p->phi_tc);
     if (p->phi_tcg) cudaFree(p->phi_tcg);
     delete p;

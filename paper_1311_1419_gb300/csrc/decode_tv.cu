@@ -232,8 +232,6 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
         return fail(CS_EINVAL, "beta and mu must be finite and > 0");
     if (params->iters < 0 || params->iters > kMaxIters) return fail(CS_EINVAL, "iters out of range");
     if (params->precision != CS_FP32) return fail(CS_EINVAL, "TV recovery computes in FP32 only");
-    if (params->engine == CS_ENGINE_TC_STREAM)
-        return fail(CS_EINVAL, "TV recovery has no streaming tensor-core kernel");
     GopShape gs;
     int st = make_shape(plan, params, &gs);
     if (st) return st;
@@ -244,13 +242,25 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
     const float alpha = (float)(1.0 / (8.0 * (double)beta + (double)mu * plan->lipschitz));
     cudaStream_t s = (cudaStream_t)stream;
     const int it = params->iters;
-    if (params->engine != CS_ENGINE_PLAIN && tv_tc_supported(plan)) {
+    // the on-chip tensor-core kernel (16 x 16 blocks, M <= 128), else the streaming
+    // one, else (or when the budget leaves no room for the streaming state) the
+    // plain kernel; an explicit engine insists on its kernel
+    if ((params->engine == CS_ENGINE_AUTO || params->engine == CS_ENGINE_TC) && tv_tc_supported(plan)) {
         const cudaError_t e = launch_decode_tv_tc(plan, gs, it, beta, mu, alpha, key_dev, y_dev, frames_f32_dev,
                                                   frames_u8_dev, s);
         return e == cudaSuccess ? CS_OK : cuda_fail(e, "cs_decode_gop_tv");
     }
     if (params->engine == CS_ENGINE_TC)
-        return fail(CS_EINVAL, "TV recovery's tensor-core kernel takes 16 x 16 blocks with M <= 128");
+        return fail(CS_EINVAL, "TV recovery's on-chip tensor-core kernel takes 16 x 16 blocks with M <= 128");
+    if ((params->engine == CS_ENGINE_AUTO || params->engine == CS_ENGINE_TC_STREAM) && tv_tcs_supported(plan)) {
+        const cudaError_t e = launch_decode_tv_tcs(plan, gs, it, beta, mu, alpha, key_dev, y_dev, frames_f32_dev,
+                                                   frames_u8_dev, s);
+        if (e == cudaSuccess) return CS_OK;
+        if (e != cudaErrorMemoryAllocation || params->engine == CS_ENGINE_TC_STREAM)
+            return cuda_fail(e, "cs_decode_gop_tv");
+    }
+    if (params->engine == CS_ENGINE_TC_STREAM)
+        return fail(CS_EINVAL, "TV recovery's streaming tensor-core kernel takes N = 64, 256, 1024 with M <= 512");
     if (tv_smem(gs.n, gs.m, 1) > 227 * 1024) return fail(CS_EINVAL, "block too large for the TV kernel");
     // as many blocks per CTA (12 for 32 x 32 blocks, else up to 8: at 12 the
     // 256-thread CTA's registers would allow only two per SM; then 4, 2 or 1) as

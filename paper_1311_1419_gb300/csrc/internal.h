@@ -70,9 +70,12 @@ struct cs_ctx {
     // of (CTAs per SM x sm_count) per-CTA scratches (tcs_ring)
     uint8_t* tcs_scratch = nullptr;
     int tcs_slots = 0;
-    size_t scratch_bytes = 0;           // tc8_scratch + tcs_scratch
+    // state of the streaming TV decode (allocated on its first use): one per-launch
+    // area of sm_count per-CTA scratches (tv_ring)
+    uint8_t* tv_scratch = nullptr;
+    size_t scratch_bytes = 0;           // tc8_scratch + tcs_scratch + tv_scratch
     std::mutex launch_mu;               // held from slot_take to slot_done
-    csvc::SlotRing counter_ring, tc8_ring, tcs_ring;
+    csvc::SlotRing counter_ring, tc8_ring, tcs_ring, tv_ring;
     // device staging of cs_codec_host (grown on demand), one holder at a time
     std::mutex stage_mu;
     uint8_t* stage = nullptr;
@@ -123,6 +126,8 @@ struct cs_plan {
     // images of A * 2^tc_ea (same four types, m16 x N, 128-byte-swizzled atoms)
     // for the streaming tensor-core decode; NULL when it does not take the shape
     uint8_t* a_tcs = nullptr;
+    // the same images of Phi * 2^tc_ephi: the streaming TV decode's B operands
+    uint8_t* phi_tcs = nullptr;
 };
 
 namespace csvc {
@@ -188,6 +193,16 @@ bool tv_tc_supported(const cs_plan* plan);
 cudaError_t launch_decode_tv_tc(const cs_plan* plan, const GopShape& gs, int iters, float beta, float mu,
                                 float alpha, const uint8_t* key, const float* y, float* out_f32,
                                 uint8_t* out_u8, cudaStream_t s);
+// TV recovery on the tensor cores with streamed operands: N = 64, 256, 1024 with
+// M <= 512, state in the context's TV scratch (decode_tv_tcs.cu); on a budget that
+// has no room for that scratch the launch returns cudaErrorMemoryAllocation
+bool tv_tcs_supported(const cs_plan* plan);
+size_t tv_tcs_slot_bytes(int sm_count);
+cudaError_t launch_decode_tv_tcs(const cs_plan* plan, const GopShape& gs, int iters, float beta, float mu,
+                                 float alpha, const uint8_t* key, const float* y, float* out_f32,
+                                 uint8_t* out_u8, cudaStream_t s);
+// room left for decode scratch under the context's HBM budget (caller holds ctx->mu)
+size_t scratch_room_of(const cs_ctx* ctx);
 // 32 x 32 blocks (N = 1024): clusters of 8 CTAs (decode_tc8.cu)
 cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
 cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaStream_t s);

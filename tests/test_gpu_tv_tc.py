@@ -96,7 +96,9 @@ def test_tv_tensor_cores_zero_iterations_return_the_key(B, ctx):
 
 def test_tv_engine_rules(B, ctx):
     s = torch.cuda.current_stream()
-    for b, m, engine in [(8, 24, B.CS_ENGINE_TC), (16, 200, B.CS_ENGINE_TC), (16, 64, B.CS_ENGINE_TC_STREAM)]:
+    # the on-chip kernel takes 16 x 16 blocks with M <= 128 only; the streaming one
+    # N = 64, 256, 1024 only
+    for b, m, engine in [(8, 24, B.CS_ENGINE_TC), (16, 200, B.CS_ENGINE_TC), (4, 8, B.CS_ENGINE_TC_STREAM)]:
         plan = B.cs_make_phi(ctx, b * b, m, 1)
         try:
             p = B.make_params(64, 64, 2, b, m, iters=5, engine=engine)
