@@ -775,10 +775,11 @@ def hbm_kernels(res, peaks):
 
 def tv_run(B, torch, dev, res, wl, iters, with_oracle):
     """TV recovery (the paper's TVAL3 regulariser) of the clip at its largest M:
-    on the tensor-core TV kernel where the shape has one (16x16 blocks, M <= 128),
-    else on the plain per-block kernel, each timed once after a warm-up call; with
-    the tensor cores, the plain kernel is timed beside them on the same input.  The
-    oracle checks the first block row of the first CS frame."""
+    on the on-chip tensor-core TV kernel where the shape fits it (16x16 blocks,
+    M <= 128), else on the streaming tensor-core one (blocks of 64, 256 or 1024
+    pixels), else on the plain per-block kernel, each timed once after a warm-up
+    call; with the tensor cores, the plain kernel is timed beside them on the same
+    input.  The oracle checks the first block row of the first CS frame."""
     h, w, b = wl["height"], wl["width"], wl["block"]
     m = max(wl["ms"])
     n_cs, stream = res["n_cs"], res["stream"]
@@ -799,14 +800,18 @@ def tv_run(B, torch, dev, res, wl, iters, with_oracle):
         B.cs_ctx_status(res["ctx"])
         return out, a0.elapsed_time(a1)
 
-    try:
-        tv_out, tv_ms = timed(B.CS_ENGINE_TC)
-        kernel = "tensor-core TV kernel (k_tv_tc, FP32-grade split-fp16 products)"
-    except B.CsError as e:
-        if e.status != B.CS_EINVAL:
-            raise
-        tv_out, tv_ms = timed(B.CS_ENGINE_PLAIN)
-        kernel = "plain FP32 TV kernel (k_tv_plain; the tensor-core one takes 16x16 blocks, M <= 128)"
+    tv_out = None
+    for engine, kernel in [
+            (B.CS_ENGINE_TC, "on-chip tensor-core TV kernel (k_tv_tc, FP32-grade split-fp16 products)"),
+            (B.CS_ENGINE_TC_STREAM, "streaming tensor-core TV kernel (k_tv_tcs, FP32-grade split-fp16 "
+                                    "products, Phi images streamed from L2)"),
+            (B.CS_ENGINE_PLAIN, "plain FP32 TV kernel (k_tv_plain)")]:
+        try:
+            tv_out, tv_ms = timed(engine)
+            break
+        except B.CsError as e:
+            if e.status != B.CS_EINVAL or engine == B.CS_ENGINE_PLAIN:
+                raise
     tv_psnr = torch.empty(n_cs, dtype=torch.float64, device=dev)
     B.cs_psnr(res["cs_dev"], tv_out, n_cs, h, w, tv_psnr, stream)
     torch.cuda.synchronize(dev)
@@ -815,7 +820,7 @@ def tv_run(B, torch, dev, res, wl, iters, with_oracle):
            "decode_ms": tv_ms, "mpixel_per_s": n_cs * h * w / (tv_ms / 1e3) / 1e6,
            "achieved_tflops": flops / (tv_ms / 1e3) / 1e12,
            "psnr_db": float(np.mean(tv_psnr.cpu().numpy()))}
-    if kernel.startswith("tensor"):
+    if "tensor-core" in kernel:
         plain_out, plain_ms = timed(B.CS_ENGINE_PLAIN)
         keys = res["keys_dev"].repeat_interleave(wl["gop"] - 1, dim=0).to(torch.float64)
         d = (tv_out.to(torch.float64) - plain_out.to(torch.float64)).norm()

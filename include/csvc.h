@@ -195,13 +195,19 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
  * of each multiplier; params->iters iterations from zero.  beta and mu are the
  * penalties of the splitting and of the measurement constraint (0.125 and 1
  * suit 8-bit residuals).  FP32-grade results; params->precision must be
- * CS_FP32 and lambda_rel is not used.  Engines: CS_ENGINE_AUTO takes the
- * tensor-core TV kernel (both Phi products per iteration on tcgen05, three fp16
- * MMAs per K step, the state in the context's streaming-decode scratch) for
- * 16 x 16 blocks with M <= 128 when the context has that scratch, else the
- * plain per-block FP32 kernel; CS_ENGINE_TC demands the tensor-core kernel
- * (CS_EINVAL for any other shape), CS_ENGINE_PLAIN the plain one;
- * CS_ENGINE_TC_STREAM is CS_EINVAL.
+ * CS_FP32 and lambda_rel is not used.  Engines (both tensor-core kernels put
+ * the two Phi products of an iteration on tcgen05, three fp16 MMAs per K step):
+ * - CS_ENGINE_TC: the on-chip kernel (Phi resident in shared memory, the
+ *   multiplier state in the context's streaming-decode scratch); 16 x 16
+ *   blocks with M <= 128 only, CS_EINVAL for any other shape;
+ * - CS_ENGINE_TC_STREAM: the streaming kernel (Phi streamed from L2, the
+ *   iterate and multipliers in a per-SM state area of about 4.3 MB that the
+ *   context allocates on first use, within its scratch budget); N = 64, 256 or
+ *   1024 with M <= 512, CS_EINVAL for any other shape, CS_ENOMEM when the
+ *   state area cannot be had;
+ * - CS_ENGINE_AUTO: the on-chip kernel where it applies, else the streaming
+ *   one, else (or when the state area cannot be had) the plain kernel;
+ * - CS_ENGINE_PLAIN: the plain per-block FP32 kernel.
  * Buffers and errors as cs_decode_gop; CS_EINVAL for beta or mu <= 0. */
 int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float mu,
                      const uint8_t* key_dev, const float* y_dev, float* frames_f32_dev,

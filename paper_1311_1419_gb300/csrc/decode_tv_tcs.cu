@@ -93,6 +93,7 @@ struct TvsLaunch {
     uint8_t* scratch;       // gridDim.x areas of scr_layout(n, m16).total bytes
     size_t scr_stride;
     int n_tiles;
+    int drop_arrival;       // test hook: CTA 0 withholds one warp's first P-ready arrival
     TvsJob job;
 };
 
@@ -166,8 +167,7 @@ __device__ __forceinline__ void copy_role_v(const TvsLaunch& L, MiscV* ms, uint8
     const uint8_t* p_hi = scr + sl.p_img;
     const uint8_t* p_lo = p_hi + (size_t)p_slices_v(m16) * kTBytes;
     uint32_t st = 0, pc = 0, zc = 0;
-    uint32_t last_par[kStages] = {};
-    bool issued[kStages] = {};
+    uint32_t last_par = 0, issued = 0;   // per stage, one bit each
     bool ok = true;
     for (;;) {
         const int tile = fetch_tile_v(L, ms);
@@ -207,8 +207,8 @@ __device__ __forceinline__ void copy_role_v(const TvsLaunch& L, MiscV* ms, uint8
                                          &ms->full[s]);
                             }
                         }
-                        last_par[s] = par;
-                        issued[s] = true;
+                        last_par = (last_par & ~(1u << s)) | (par << s);
+                        issued |= 1u << s;
                     }
                     __syncwarp();
                     ++st;
@@ -220,7 +220,7 @@ __device__ __forceinline__ void copy_role_v(const TvsLaunch& L, MiscV* ms, uint8
     if (lane == 0) {
         // copies whose consumer gave up may still be in flight (bounded)
         for (int s = 0; s < kStages; ++s)
-            if (issued[s]) mbar_wait(&ms->full[s], last_par[s], kWaitNs);
+            if ((issued >> s) & 1u) mbar_wait(&ms->full[s], (last_par >> s) & 1u, kWaitNs);
     }
     __syncwarp();
 }
@@ -298,26 +298,27 @@ __device__ __forceinline__ void acc_release_v(MiscV* ms, uint32_t acc, int lane)
     if (lane == 0) mbar_arrive(&ms->acc_empty[acc & 1]);
 }
 // The epilogue's global writes of an operand image are complete: let the copy warp read it.
-__device__ __forceinline__ void signal_copy_v(uint64_t* bar, int lane) {
+__device__ __forceinline__ void signal_copy_v(uint64_t* bar, int lane, bool withhold = false) {
     fence_proxy_async_global();
     __syncwarp();
-    if (lane == 0) mbar_arrive(bar);
+    if (lane == 0 && !withhold) mbar_arrive(bar);
 }
 
 // P for measurements i0 .. i0 + w4 - 1 of block blk (U from accumulator columns
 // starting at ucol, none at k = 0): rho = U su - y, P = mu rho - lam at k = 0 (lam =
 // 0, U = 0), else 2 mu rho - lam_{k-1}, lam_k = lam_{k-1} - mu rho; P sp as fp16
 // hi / lo into the P image.
-__device__ __forceinline__ void residual_v(const TvsJob& J, uint8_t* p_hi, uint8_t* p_lo, const float4* y4,
-                                           float4* lam4, uint32_t ucol, int i0, int w4, int blk, int k) {
+__device__ __forceinline__ void residual_v(const TvsJob& J, uint8_t* __restrict__ p_hi, uint8_t* __restrict__ p_lo,
+                                           const float4* __restrict__ y4, float4* __restrict__ lam4, uint32_t ucol,
+                                           int i0, int w4, int blk, int k, bool live) {
     const float mu = J.mu, cmu = k == 0 ? mu : 2.f * mu;
-    const bool use_u = k > 0, read_lam = k > 1, write_lam = k > 0 && k + 1 < J.iters;
+    const bool use_u = k > 0, read_lam = live && k > 1, write_lam = live && k > 0 && k + 1 < J.iters;
     for (int cc = 0; cc < w4; cc += 4) {
         const int i = i0 + cc;
         uint32_t u[4] = {0u, 0u, 0u, 0u};
         if (use_u) tmem_ld4(ucol + (uint32_t)cc, u);
         const size_t vi = (size_t)(i / 4) * kTile + blk;
-        const float4 yv = y4[vi];
+        const float4 yv = live ? y4[vi] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 lv = read_lam ? lam4[vi] : make_float4(0.f, 0.f, 0.f, 0.f);
         if (use_u) tmem_wait_ld();
         const float yy[4] = {yv.x, yv.y, yv.z, yv.w};
@@ -325,7 +326,7 @@ __device__ __forceinline__ void residual_v(const TvsJob& J, uint8_t* p_hi, uint8
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const float rho = __uint_as_float(u[e]) * J.su - yy[e];
-            p[e] = (cmu * rho - l[e]) * J.sp;
+            p[e] = live ? (cmu * rho - l[e]) * J.sp : 0.f;
             l[e] -= mu * rho;
         }
         if (write_lam) lam4[vi] = make_float4(l[0], l[1], l[2], l[3]);
@@ -337,72 +338,119 @@ __device__ __forceinline__ void residual_v(const TvsJob& J, uint8_t* p_hi, uint8
     }
 }
 
-// The r step (with the fused w-step) for pixel rows p0 .. p0 + nrows - 1 of block
-// blk: r_k, q_{k-1} from (rc, qc), r_{k+1}, q_k into (rn, qn) and the R image; G from
-// accumulator columns gcol + (pixel - pix0).  k = 0 (first): r = q = 0.
-__device__ __forceinline__ void r_step_v(const TvsJob& J, const float4* rc, const float4* qc, float4* rn, float4* qn,
-                                         uint8_t* r_hi, uint8_t* r_lo, uint32_t gcol, int pix0, int p0, int nrows,
-                                         int blk, bool first) {
+// One row of four pixels (p, 4 c4 .. 4 c4 + 3) of the r step with the fused w-step:
+// r[0..3] the row's r_k and r[4] its right neighbour's, rd the row below, qh / qv
+// the row's q_{k-1}, tu the t_v of the pixels above (0 on a block's first row), g
+// the accumulator's G; th_carry carries t_h from the pixel on the left.  Writes
+// q_k (qhn, qvn), r_{k+1} (rnew) and the row's t_v (the next row's tu).
+__device__ __forceinline__ void tv_row4(const float r[5], const float rd[4], const float qh[4], const float qv[4],
+                                        const float tu[4], const uint32_t g[4], int p, int c4, int b, float beta,
+                                        float ib, float alpha, float sg, float& th_carry, float qhn[4],
+                                        float qvn[4], float rnew[4], float tv[4]) {
+    float tl = th_carry;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int pc = 4 * c4 + e;
+        const float dh = pc < b - 1 ? r[e + 1] - r[e] : 0.f;
+        const float nh = qh[e] - beta * dh;
+        qhn[e] = nh + beta * shrink_v(dh - nh * ib, ib);
+        const float th = pc < b - 1 ? beta * dh - qhn[e] : 0.f;
+        const float dv = p < b - 1 ? rd[e] - r[e] : 0.f;
+        const float nv = qv[e] - beta * dv;
+        qvn[e] = nv + beta * shrink_v(dv - nv * ib, ib);
+        tv[e] = p < b - 1 ? beta * dv - qvn[e] : 0.f;
+        const float dt = (pc > 0 ? tl : 0.f) - th + tu[e] - tv[e];
+        rnew[e] = r[e] - alpha * fmaf(__uint_as_float(g[e]), sg, dt);
+        tl = th;
+    }
+    th_carry = tl;
+}
+
+// The row's results: q_k and r_{k+1} into (qn, rn) at float4 index vi (a live lane
+// only), r_{k+1} as fp16 hi / lo into the R image.
+__device__ __forceinline__ void tv_store4(float4* __restrict__ rn, float4* __restrict__ qn,
+                                          uint8_t* __restrict__ r_hi, uint8_t* __restrict__ r_lo, size_t vi,
+                                          size_t plane4, int blk, int j, bool live, const float qhn[4],
+                                          const float qvn[4], const float rnew[4]) {
+    if (live) {
+        qn[vi] = make_float4(qhn[0], qhn[1], qhn[2], qhn[3]);
+        qn[vi + plane4] = make_float4(qvn[0], qvn[1], qvn[2], qvn[3]);
+        rn[vi] = make_float4(rnew[0], rnew[1], rnew[2], rnew[3]);
+    }
+    const uint32_t h0 = pack2h(rnew[0], rnew[1]), h1 = pack2h(rnew[2], rnew[3]);
+    const float2 d0 = unpack2h(h0), d1 = unpack2h(h1);
+    const uint32_t off = sw64_offset((uint32_t)blk, (uint32_t)j, kTile / 8);
+    *reinterpret_cast<uint2*>(r_hi + off) = make_uint2(h0, h1);
+    *reinterpret_cast<uint2*>(r_lo + off) =
+        make_uint2(pack2h(rnew[0] - d0.x, rnew[1] - d0.y), pack2h(rnew[2] - d1.x, rnew[3] - d1.y));
+}
+
+// The r step (with the fused w-step) for pixel rows p0 .. p0 + nrows - 1 (nrows
+// even) of block blk: r_k, q_{k-1} from (rc, qc), r_{k+1}, q_k into (rn, qn) and the
+// R image; G from accumulator columns gcol + (pixel - pix0).  k = 0 (first): r = q =
+// 0.  Rows go in pairs, so that one wait covers both rows' loads and the second row
+// takes its neighbours above (r, q_v and t_v) from the first.  A lane with no block
+// (live false) moves no state and writes zeros into the R image.
+__device__ __forceinline__ void r_step_v(const TvsJob& J, const float4* __restrict__ rc,
+                                         const float4* __restrict__ qc, float4* __restrict__ rn,
+                                         float4* __restrict__ qn, uint8_t* __restrict__ r_hi,
+                                         uint8_t* __restrict__ r_lo, uint32_t gcol, int pix0, int p0, int nrows,
+                                         int blk, bool first, bool live) {
     const int n = J.n, b = J.gs.b, nq = b / 4;
     const float beta = J.beta, ib = 1.f / beta, alpha = J.alpha, sg = J.sg;
     const float* rcf = reinterpret_cast<const float*>(rc);
-    for (int p = p0; p < p0 + nrows; ++p) {
-        float th_carry = 0.f;
+    const size_t row4 = (size_t)nq * kTile, plane4 = (size_t)(n / 4) * kTile;
+    const bool ld = !first && live;
+    for (int p = p0; p < p0 + nrows; p += 2) {
+        float thc0 = 0.f, thc1 = 0.f;
         for (int c4 = 0; c4 < nq; ++c4) {
             const int j = p * b + 4 * c4;
-            uint32_t g[4];
-            tmem_ld4(gcol + (uint32_t)(j - pix0), g);
-            float4 R0 = make_float4(0.f, 0.f, 0.f, 0.f), Rn = R0, Ru = R0, Qh = R0, Qv = R0, Qu = R0;
-            float rright = 0.f;
-            if (!first) {
-                const size_t vi = (size_t)(j / 4) * kTile + blk;
+            const size_t vi = (size_t)(j / 4) * kTile + blk;
+            uint32_t g0[4], g1[4];
+            tmem_ld4(gcol + (uint32_t)(j - pix0), g0);
+            tmem_ld4(gcol + (uint32_t)(j + b - pix0), g1);
+            const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+            float4 Ru = z, R0 = z, R1 = z, Rd = z, Qu = z, Qh0 = z, Qv0 = z, Qh1 = z, Qv1 = z;
+            float rr0 = 0.f, rr1 = 0.f;
+            if (ld) {
                 R0 = rc[vi];
-                Rn = p < b - 1 ? rc[vi + (size_t)(b / 4) * kTile] : R0;
-                Ru = p > 0 ? rc[vi - (size_t)(b / 4) * kTile] : R0;
-                rright = c4 + 1 < nq ? rcf[((size_t)((j + 4) / 4) * kTile + blk) * 4] : 0.f;
-                Qh = qc[vi];
-                Qv = qc[vi + (size_t)(n / 4) * kTile];
-                Qu = p > 0 ? qc[vi + (size_t)(n / 4) * kTile - (size_t)(b / 4) * kTile] : Qu;
+                R1 = rc[vi + row4];
+                Ru = p > 0 ? rc[vi - row4] : R0;
+                Rd = p + 2 < b ? rc[vi + 2 * row4] : R1;
+                if (c4 + 1 < nq) {
+                    rr0 = rcf[(vi + kTile) * 4];
+                    rr1 = rcf[(vi + row4 + kTile) * 4];
+                }
+                Qh0 = qc[vi];
+                Qv0 = qc[vi + plane4];
+                Qh1 = qc[vi + row4];
+                Qv1 = qc[vi + plane4 + row4];
+                if (p > 0) Qu = qc[vi + plane4 - row4];
             }
             tmem_wait_ld();
-            const float r[5] = {R0.x, R0.y, R0.z, R0.w, rright};
-            const float rnv[4] = {Rn.x, Rn.y, Rn.z, Rn.w}, ruv[4] = {Ru.x, Ru.y, Ru.z, Ru.w};
-            const float qh[4] = {Qh.x, Qh.y, Qh.z, Qh.w}, qv[4] = {Qv.x, Qv.y, Qv.z, Qv.w};
+            const float r0[5] = {R0.x, R0.y, R0.z, R0.w, rr0}, r1[5] = {R1.x, R1.y, R1.z, R1.w, rr1};
+            const float ru[4] = {Ru.x, Ru.y, Ru.z, Ru.w}, rd[4] = {Rd.x, Rd.y, Rd.z, Rd.w};
             const float qu[4] = {Qu.x, Qu.y, Qu.z, Qu.w};
-            float qhn[4], qvn[4], rnew[4];
-            float tl = th_carry;
+            const float qh0[4] = {Qh0.x, Qh0.y, Qh0.z, Qh0.w}, qv0[4] = {Qv0.x, Qv0.y, Qv0.z, Qv0.w};
+            const float qh1[4] = {Qh1.x, Qh1.y, Qh1.z, Qh1.w}, qv1[4] = {Qv1.x, Qv1.y, Qv1.z, Qv1.w};
+            float tu[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int pc = 4 * c4 + e;
-                const float dh = pc < b - 1 ? r[e + 1] - r[e] : 0.f;
-                const float nh = qh[e] - beta * dh;
-                qhn[e] = nh + beta * shrink_v(dh - nh * ib, ib);
-                const float th = pc < b - 1 ? beta * dh - qhn[e] : 0.f;
-                const float dv = p < b - 1 ? rnv[e] - r[e] : 0.f;
-                const float nv = qv[e] - beta * dv;
-                qvn[e] = nv + beta * shrink_v(dv - nv * ib, ib);
-                const float tv = p < b - 1 ? beta * dv - qvn[e] : 0.f;
-                float tu = 0.f;
-                if (p > 0) {   // t_v of the pixel above, from its r_k and q_{k-1}
-                    const float du = r[e] - ruv[e];
+            for (int e = 0; e < 4; ++e) {   // t_v of the pixels above row p, from their r_k and q_{k-1}
+                tu[e] = 0.f;
+                if (p > 0) {
+                    const float du = r0[e] - ru[e];
                     const float nu = qu[e] - beta * du;
-                    tu = beta * du - (nu + beta * shrink_v(du - nu * ib, ib));
+                    tu[e] = beta * du - (nu + beta * shrink_v(du - nu * ib, ib));
                 }
-                const float dt = (pc > 0 ? tl : 0.f) - th + tu - tv;
-                rnew[e] = r[e] - alpha * fmaf(__uint_as_float(g[e]), sg, dt);
-                tl = th;
             }
-            th_carry = tl;
-            const size_t vi = (size_t)(j / 4) * kTile + blk;
-            qn[vi] = make_float4(qhn[0], qhn[1], qhn[2], qhn[3]);
-            qn[vi + (size_t)(n / 4) * kTile] = make_float4(qvn[0], qvn[1], qvn[2], qvn[3]);
-            rn[vi] = make_float4(rnew[0], rnew[1], rnew[2], rnew[3]);
-            const uint32_t h0 = pack2h(rnew[0], rnew[1]), h1 = pack2h(rnew[2], rnew[3]);
-            const float2 d0 = unpack2h(h0), d1 = unpack2h(h1);
-            const uint32_t off = sw64_offset((uint32_t)blk, (uint32_t)j, kTile / 8);
-            *reinterpret_cast<uint2*>(r_hi + off) = make_uint2(h0, h1);
-            *reinterpret_cast<uint2*>(r_lo + off) =
-                make_uint2(pack2h(rnew[0] - d0.x, rnew[1] - d0.y), pack2h(rnew[2] - d1.x, rnew[3] - d1.y));
+            float qhn[4], qvn[4], rnew[4], tv[4];
+            tv_row4(r0, r1, qh0, qv0, tu, g0, p, c4, b, beta, ib, alpha, sg, thc0, qhn, qvn, rnew, tv);
+            if (!live) rnew[0] = rnew[1] = rnew[2] = rnew[3] = 0.f;
+            tv_store4(rn, qn, r_hi, r_lo, vi, plane4, blk, j, live, qhn, qvn, rnew);
+            float tv1[4];
+            tv_row4(r1, rd, qh1, qv1, tv, g1, p + 1, c4, b, beta, ib, alpha, sg, thc1, qhn, qvn, rnew, tv1);
+            if (!live) rnew[0] = rnew[1] = rnew[2] = rnew[3] = 0.f;
+            tv_store4(rn, qn, r_hi, r_lo, vi + row4, plane4, blk, j + b, live, qhn, qvn, rnew);
         }
     }
 }
@@ -426,14 +474,16 @@ __device__ __forceinline__ void epi_role_v(const TvsLaunch& L, MiscV* ms, uint32
     float4* lam4 = reinterpret_cast<float4*>(scr + sl.lam4);
     const int nc = g2_width_v(n), nch2 = n / nc, pw = nc / kColGroups;   // pixels per column group and chunk
     uint32_t acc = 0;
+    bool first_tile = true;
     for (;;) {
         const int tile = fetch_tile_v(L, ms);
         if (tile < 0) break;
         cta_sync_v();   // B
         const long long tile_row0 = (long long)tile * kTile;
+        const long long rows_left = J.rows - tile_row0;
+        const bool live = blk < rows_left;   // the last tile's lanes beyond its blocks move no state
         if (K > 0) {
-            {   // the tile's y, read once (coalesced), [m16 / 4][128] float4, zero beyond M and the last block
-                const long long rows_left = J.rows - tile_row0;
+            {   // the tile's y, read once (coalesced), [m16 / 4][128] float4, zero beyond M and the tile's blocks
                 float* yf = reinterpret_cast<float*>(y4);
                 const float* src = J.y + tile_row0 * gs.m;
                 for (int e = et; e < kTile * m16; e += kEpiThreads) {
@@ -446,29 +496,31 @@ __device__ __forceinline__ void epi_role_v(const TvsLaunch& L, MiscV* ms, uint32
             }
             for (int c = 0; c < g1_chunks_v(m16); ++c) {   // P_0 = -mu y
                 const int w4 = g1_width_v(m16, c) / kColGroups;
-                residual_v(J, p_hi, p_lo, y4, lam4, 0u, g1_base_v(m16, c) + cg * w4, w4, blk, 0);
+                residual_v(J, p_hi, p_lo, y4, lam4, 0u, g1_base_v(m16, c) + cg * w4, w4, blk, 0, live);
             }
-            signal_copy_v(&ms->p_ready, lane);
+            // (the test hook withholds one warp's first arrival in CTA 0)
+            signal_copy_v(&ms->p_ready, lane, L.drop_arrival && blockIdx.x == 0 && ew == 1 && first_tile);
             for (int k = 0; k < K; ++k) {
                 if (k > 0) {
                     for (int c = 0; c < g1_chunks_v(m16); ++c, ++acc) {
                         acc_wait_v(L, ms, acc);
                         const int w4 = g1_width_v(m16, c) / kColGroups;
                         residual_v(J, p_hi, p_lo, y4, lam4, lane_addr + (acc & 1) * kChunk + (uint32_t)(cg * w4),
-                                   g1_base_v(m16, c) + cg * w4, w4, blk, k);
+                                   g1_base_v(m16, c) + cg * w4, w4, blk, k, live);
                         acc_release_v(ms, acc, lane);
                     }
                     signal_copy_v(&ms->p_ready, lane);
                 }
-                const float4* rc = reinterpret_cast<const float4*>(scr + sl.r[k & 1]);
-                const float4* qc = reinterpret_cast<const float4*>(scr + sl.q[k & 1]);
-                float4* rn = reinterpret_cast<float4*>(scr + sl.r[(k + 1) & 1]);
-                float4* qn = reinterpret_cast<float4*>(scr + sl.q[(k + 1) & 1]);
+                const bool odd = k & 1;   // (selects: a runtime index would put the layout in local memory)
+                const float4* rc = reinterpret_cast<const float4*>(scr + (odd ? sl.r[1] : sl.r[0]));
+                const float4* qc = reinterpret_cast<const float4*>(scr + (odd ? sl.q[1] : sl.q[0]));
+                float4* rn = reinterpret_cast<float4*>(scr + (odd ? sl.r[0] : sl.r[1]));
+                float4* qn = reinterpret_cast<float4*>(scr + (odd ? sl.q[0] : sl.q[1]));
                 for (int jc = 0; jc < nch2; ++jc, ++acc) {
                     acc_wait_v(L, ms, acc);
                     const int pix0 = jc * nc + cg * pw;
                     r_step_v(J, rc, qc, rn, qn, r_hi, r_lo, lane_addr + (acc & 1) * kChunk + (uint32_t)(cg * pw),
-                             pix0, pix0 / b, pw / b, blk, k == 0);
+                             pix0, pix0 / b, pw / b, blk, k == 0, live);
                     acc_release_v(ms, acc, lane);
                 }
                 if (k + 1 < K) signal_copy_v(&ms->z_ready, lane);
@@ -479,8 +531,8 @@ __device__ __forceinline__ void epi_role_v(const TvsLaunch& L, MiscV* ms, uint32
         }
         // r^K plus the key (Eq. 4), crop; the thread's pixels of every chunk
         const long long row = tile_row0 + blk;
-        const float4* rK = reinterpret_cast<const float4*>(scr + sl.r[K & 1]);
-        if (row < J.rows) {
+        const float4* rK = reinterpret_cast<const float4*>(scr + ((K & 1) ? sl.r[1] : sl.r[0]));
+        if (live) {
             const int c_idx = (int)(row / gs.nblk), bl = (int)(row % gs.nblk);
             const int g_key = c_idx / (gs.g - 1);
             const int bi = bl / gs.nbc, bj = bl % gs.nbc;
@@ -501,6 +553,7 @@ __device__ __forceinline__ void epi_role_v(const TvsLaunch& L, MiscV* ms, uint32
                 }
             }
         }
+        first_tile = false;
         cta_sync_v();   // C
     }
 }
@@ -577,11 +630,10 @@ cudaError_t launch_decode_tv_tcs(const cs_plan* plan, const GopShape& gs, int it
     TvsLaunch L{};
     L.err = ctx->err_dev;
     TvsJob& J = L.job;
-    const int m16 = m16_of_v(plan->m), m32 = (plan->m + 31) / 32 * 32;
+    const int m16 = m16_of_v(plan->m);
     const size_t img1 = (size_t)m16 * plan->n * 2;
     J.a1_img = plan->phi_tcs;                       // fp16 hi, then fp16 lo
     J.a2_img = plan->phi_tcs + 4 * img1;
-    (void)m32;
     J.y = y;
     J.keys = key;
     J.out_f32 = out_f32;
@@ -601,6 +653,7 @@ cudaError_t launch_decode_tv_tcs(const cs_plan* plan, const GopShape& gs, int it
     J.mu = mu;
     J.alpha = alpha;
     L.n_tiles = (int)((J.rows + kTile - 1) / kTile);
+    const int grid = L.n_tiles < ctx->sm_count ? L.n_tiles : ctx->sm_count;
     L.scr_stride = scr_layout(J.n, m16).total;
     cudaError_t e = cudaFuncSetAttribute((const void*)k_tv_tcs, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSmemBytes);
@@ -612,8 +665,8 @@ cudaError_t launch_decode_tv_tcs(const cs_plan* plan, const GopShape& gs, int it
     if (e != cudaSuccess) return e;
     L.tile_counter = ctx->counters_dev + cslot;
     L.scratch = ctx->tv_scratch;
+    L.drop_arrival = ctx->debug_flags.exchange(0) & CS_DEBUG_DROP_ARRIVAL;
     e = cudaMemsetAsync(L.tile_counter, 0, sizeof(int), s);
-    const int grid = L.n_tiles < ctx->sm_count ? L.n_tiles : ctx->sm_count;
     if (e == cudaSuccess) {
         k_tv_tcs<<<grid, kThreads, kSmemBytes, s>>>(L);
         e = cudaGetLastError();

@@ -1,8 +1,11 @@
 """TV recovery on the tensor cores with streamed operands (k_tv_tcs: 8x8, 16x16
 with M > 128, 32x32; M <= 512) against the FP64 oracle's TV augmented-Lagrangian
-decode and against the plain FP32 kernel: two tiles with a ragged last one,
-cropped edge blocks, a GEMM1 in two column chunks (M16 > 256), iteration counts
-0 .. 3, other penalties, and CS_ENGINE_TC_STREAM equal to the automatic choice."""
+decode and against the plain FP32 kernel: ragged last tiles, more tiles than
+SMs, cropped edge blocks, a GEMM1 in two column chunks
+(M16 > 256), iteration counts 0 .. 3, other penalties, CS_ENGINE_TC_STREAM equal
+to the automatic choice, and the bounded-wait failure path."""
+import time
+
 import numpy as np
 import pytest
 
@@ -49,7 +52,8 @@ def _decode(B, ctx, frames, gop, n_gops, b, m, iters, engine, beta=0.125, mu=1.0
 
 @pytest.mark.parametrize("h,w,gop,n_gops,b,m,iters,beta,mu", [
     (96, 160, 6, 2, 32, 102, 60, 0.125, 1.0),    # 32x32: 150 blocks, 2 tiles (last 22)
-    (40, 56, 3, 2, 8, 24, 100, 0.125, 1.0),      # 8x8, cropped edges, two GOPs
+    (40, 56, 3, 2, 8, 24, 100, 0.125, 1.0),      # 8x8, cropped edges, two GOPs, 140 blocks: 2 tiles
+    (72, 104, 2, 1, 8, 30, 40, 0.125, 1.0),      # 8x8, 117 blocks: one tile, ragged
     (80, 112, 3, 1, 16, 200, 50, 0.125, 1.0),    # 16x16 with M > 128
     (64, 96, 3, 1, 32, 300, 30, 0.125, 1.0),     # 32x32, M16 = 304: GEMM1 in two column chunks
     (64, 128, 3, 1, 32, 60, 3, 0.125, 1.0),      # third iteration reads the stored lambda
@@ -91,3 +95,52 @@ def test_streaming_tv_zero_iterations_return_the_key(B, ctx):
     got, u8 = _decode(B, ctx, frames, 3, 1, 32, 51, 0, B.CS_ENGINE_TC_STREAM)
     assert np.array_equal(got, np.repeat(frames[:1].astype(np.float64), 2, axis=0))
     assert np.array_equal(u8, np.repeat(frames[:1], 2, axis=0))
+
+
+def test_streaming_tv_more_tiles_than_sms(B, ctx):
+    # 4 CS frames of 70 x 70 blocks of 8 x 8: 19600 blocks, 154 tiles, more than one
+    # round of the persistent grid on any GB300; the plain kernel is the check
+    frames = scenes.surveillance_video(6, 560, 556, seed=21)
+    tcs, u8 = _decode(B, ctx, frames, 3, 2, 8, 20, 40, B.CS_ENGINE_TC_STREAM, seed=21)
+    plain, _ = _decode(B, ctx, frames, 3, 2, 8, 20, 40, B.CS_ENGINE_PLAIN, seed=21)
+    keys = np.repeat(frames[::3].astype(np.float64), 2, axis=0)
+    rel = np.linalg.norm(tcs - plain) / np.linalg.norm(plain - keys)
+    worst = np.abs(tcs - plain).max()
+    print("TV tcs vs plain, 19600 blocks: residual rel-l2 %.3g, max |diff| %.3g" % (rel, worst))
+    assert np.isfinite(tcs).all()
+    assert rel <= 1e-4 and worst <= 0.05
+    assert np.array_equal(u8, np.clip(np.rint(tcs), 0, 255).astype(np.uint8))
+
+
+def test_streaming_tv_withheld_arrival_times_out_and_recovers(B):
+    c = B.cs_ctx_create(0)
+    plan = B.cs_make_phi(c, 1024, 60, 5)
+    try:
+        h, w = 64, 128
+        frames = scenes.surveillance_video(2, h, w, seed=5)
+        p = B.make_params(h, w, 2, 32, 60, iters=20, engine=B.CS_ENGINE_TC_STREAM)
+        s = torch.cuda.current_stream()
+        f = torch.from_numpy(frames).cuda()
+        y = torch.empty((1, 8, 60), dtype=torch.float32, device="cuda")
+        B.cs_encode_gop(plan, p, f, y, s)
+        ref = torch.empty((1, h, w), dtype=torch.float32, device="cuda")
+        B.cs_decode_gop_tv(plan, p, f[:1], y, ref, None, s)
+        B.cs_ctx_status(c)
+
+        B.cs_ctx_set_debug(c, B.CS_DEBUG_DROP_ARRIVAL)
+        out = torch.full((1, h, w), -1.0, dtype=torch.float32, device="cuda")
+        t0 = time.time()
+        B.cs_decode_gop_tv(plan, p, f[:1], y, out, None, s)
+        with pytest.raises(B.CsError) as ei:
+            B.cs_ctx_status(c)
+        assert ei.value.status == B.CS_ETIMEDOUT
+        assert time.time() - t0 < 30
+        B.cs_ctx_status(c)
+
+        again = torch.empty((1, h, w), dtype=torch.float32, device="cuda")
+        B.cs_decode_gop_tv(plan, p, f[:1], y, again, None, s)
+        B.cs_ctx_status(c)
+        assert np.array_equal(again.cpu().numpy(), ref.cpu().numpy())
+    finally:
+        B.cs_plan_destroy(plan)
+        B.cs_ctx_destroy(c)
