@@ -563,7 +563,8 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
     # launch per call with no_batch, else one per (operand type, shared-memory
     # layout) group of the 16x16 tensor path (M16 <= 96 or <= 128), one per group
     # of the 32x32 cluster path (and its streaming tail), one per group of the
-    # streaming path, one per plain-kernel job (FP32: one operand type)
+    # streaming path, one per group of the chunked path, one per plain-kernel job
+    # (FP32: one operand type)
     def decode_launches():
         if no_batch:
             return len(ms)
@@ -575,6 +576,8 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
                 plain += 1
             elif eng == B.CS_ENGINE_TC_STREAM:
                 groups.add(("tcs",))
+            elif eng == B.CS_ENGINE_TC_CHUNK:
+                groups.add(("tcz",))
             elif n == 256:
                 groups.add(("tc", m16 <= 96))
             else:
@@ -704,9 +707,9 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
            "psnr": {str(m): float(np.mean(psnr_dev[m].cpu().numpy())) for m in ms},
            "enc_bytes": frames.nbytes + sum(4 * n_cs * nblk * m for m in ms),
            "psnr_bytes": len(ms) * n_cs * h * w * (1 + 4)}
-    res["tc_used"] = engine == B.CS_ENGINE_TC or (
-        engine == B.CS_ENGINE_AUTO and all(t["engine"] in (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM)
-                                           for t in tuned.values()))
+    tc_engines = (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM, B.CS_ENGINE_TC_CHUNK)
+    res["tc_used"] = engine in tc_engines or (
+        engine == B.CS_ENGINE_AUTO and all(t["engine"] in tc_engines for t in tuned.values()))
     res["mixed"], res["mixed_out"] = {}, {}
     if want_mixed and res["tc_used"]:
         # the same batched decode with mixed precision: bulk products in one 16-bit
@@ -892,7 +895,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--engine", choices=["auto", "plain", "tc", "tcs"], default="auto")
+    ap.add_argument("--engine", choices=["auto", "plain", "tc", "tcs", "tcz"], default="auto")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD,
                     help="720p (default): 32x32 blocks, M = 102; cif: the CIF M-sweep; "
                          "mixed64: the heterogeneous batch")
@@ -966,7 +969,7 @@ def main():
         return
 
     engine = {"auto": B.CS_ENGINE_AUTO, "plain": B.CS_ENGINE_PLAIN, "tc": B.CS_ENGINE_TC,
-              "tcs": B.CS_ENGINE_TC_STREAM}[args.engine]
+              "tcs": B.CS_ENGINE_TC_STREAM, "tcz": B.CS_ENGINE_TC_CHUNK}[args.engine]
     res = codec_run(wl, B, torch, dev, world, barrier, args.steps, args.warmup, engine,
                     want_e2e=not args.no_e2e, want_mixed=not args.no_mixed, no_batch=args.no_batch)
     total_ms = max_over_ranks(sum(res["step_ms"]), world, dev)

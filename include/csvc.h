@@ -64,13 +64,18 @@ typedef struct cs_plan cs_plan;
 #define CS_FP16 3          /* FP16 A and iterate (scaled), FP32-grade tail iterations */
 
 /* decode kernel (cs_params.engine) */
-#define CS_ENGINE_AUTO 0   /* CS_ENGINE_TC if the shape allows it, else CS_ENGINE_TC_STREAM, else plain */
+#define CS_ENGINE_AUTO 0   /* the autotuned engine of the (N, M) (cs_autotune), else CS_ENGINE_TC
+                            * if the shape allows it, else CS_ENGINE_TC_STREAM, else plain */
 #define CS_ENGINE_PLAIN 1  /* one CTA per block, FP32 SIMT: the plain baseline */
 #define CS_ENGINE_TC 2     /* persistent tcgen05 kernel with the iterates on chip: N = 256 or
                             * 1024 with M <= 128; CS_EINVAL for any other shape */
 #define CS_ENGINE_TC_STREAM 3  /* persistent tcgen05 kernel with A streamed from L2 and the
                                 * iterates in global memory: N = 64, 256 or 1024 with
                                 * M <= 512; CS_EINVAL for any other shape */
+#define CS_ENGINE_TC_CHUNK 4   /* persistent tcgen05 kernel with A streamed from L2, GEMM1 in
+                                * 128-coefficient chunks from tensor memory and only the last
+                                * two iterates s in global memory: N = 256 or 1024 with
+                                * M <= 128; CS_EINVAL for any other shape */
 
 /* Codec parameters of one encode/decode call (Sec. 3.1: "GOP size and
  * measurement matrix size" are the encoder's configuration). */
@@ -217,19 +222,22 @@ int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float beta, float m
  * the candidates on the device: the on-chip tensor-core kernel where the
  * shape has one (16 x 16 and 32 x 32 blocks, M <= 128), the streaming
  * tensor-core kernel where it has one (8 x 8, 16 x 16 and 32 x 32 blocks,
- * M <= 512), and the plain FP32 kernel at 64,
+ * M <= 512), the chunked one where it has one (16 x 16 and 32 x 32 blocks,
+ * M <= 128), and the plain FP32 kernel at 64,
  * 128, 256, 512 and 1024 threads per CTA with 1, 2, 4, 8 or 16 (up to 512
  * threads) measured blocks per CTA (the blocks of a CTA share each load of A;
  * shapes whose shared memory exceeds 200 KB are skipped; after its default shape
  * the plain sweep stops when that is more than 4x slower than a tensor-core
  * kernel of the shape).  Each runs a synthetic call (random
- * measurements, zero key, up to 19456 blocks, 8 iterations, FP32); the
- * fastest is recorded in ctx for this (N, M) and used from then on by FP32
- * decodes whose engine is CS_ENGINE_AUTO (an explicit engine still wins;
- * mixed precision always takes a tensor-core kernel).  Synchronises the
+ * measurements, zero key, two tiles of 128 blocks per SM up to 40 M pixels,
+ * 16 iterations, FP32: the throughput of a call that fills the GPU); the
+ * fastest is recorded in ctx for this (N, M) and used from then on by
+ * decodes whose engine is CS_ENGINE_AUTO (an explicit engine still wins; mixed
+ * precision takes the recorded engine when it is a tensor-core kernel, else the
+ * default order, which always gives it a tensor-core kernel).  Synchronises the
  * device: call it before serving or before capturing decodes into a CUDA
  * graph.  Outputs (each may be NULL): the chosen engine (CS_ENGINE_TC,
- * CS_ENGINE_TC_STREAM or CS_ENGINE_PLAIN), the plain kernel's threads and
+ * CS_ENGINE_TC_STREAM, CS_ENGINE_TC_CHUNK or CS_ENGINE_PLAIN), the plain kernel's threads and
  * blocks per CTA (0 for the tensor-core kernels) and the measured time per
  * block per iteration in ns.
  * The paper has no counterpart (its decoder is a MATLAB solver). */

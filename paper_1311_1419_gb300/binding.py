@@ -28,7 +28,7 @@ CS_ENOTFOUND = -6
 CS_ENODEV = -7
 
 CS_FP32, CS_BF16, CS_BF16X2, CS_FP16 = 0, 1, 2, 3
-CS_ENGINE_AUTO, CS_ENGINE_PLAIN, CS_ENGINE_TC, CS_ENGINE_TC_STREAM = 0, 1, 2, 3
+CS_ENGINE_AUTO, CS_ENGINE_PLAIN, CS_ENGINE_TC, CS_ENGINE_TC_STREAM, CS_ENGINE_TC_CHUNK = 0, 1, 2, 3, 4
 
 
 class CsError(RuntimeError):

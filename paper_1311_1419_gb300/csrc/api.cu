@@ -115,7 +115,7 @@ int check_decode_params(const cs_params* p) {
     if (!(p->lambda_rel >= 0.f) || !isfinite(p->lambda_rel))
         return fail(CS_EINVAL, "lambda_rel must be finite and >= 0");
     if (p->precision < CS_FP32 || p->precision > CS_FP16) return fail(CS_EINVAL, "bad precision");
-    if (p->engine < CS_ENGINE_AUTO || p->engine > CS_ENGINE_TC_STREAM) return fail(CS_EINVAL, "bad engine");
+    if (p->engine < CS_ENGINE_AUTO || p->engine > CS_ENGINE_TC_CHUNK) return fail(CS_EINVAL, "bad engine");
     return CS_OK;
 }
 
@@ -146,6 +146,9 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
     int eng = params->engine;
     const bool tc_ok = tc_supported(plan, params->precision);
     const bool tcs_ok = tcs_supported(plan);
+    const bool tcz_ok = tcz_supported(plan);
+    if (eng == CS_ENGINE_TC_CHUNK && !tcz_ok)
+        return fail(CS_EINVAL, "chunked tensor-core decode does not support this (N, M)");
     if (eng == CS_ENGINE_TC && !tc_ok)
         return fail(CS_EINVAL, "on-chip tensor-core decode does not support this (N, M)");
     if (eng == CS_ENGINE_TC_STREAM && !tcs_ok)
@@ -154,7 +157,9 @@ int prepare_decode(cs_plan* plan, const cs_params* params, const uint8_t* key, c
         std::lock_guard<std::mutex> lock(plan->ctx->tune_mu);
         auto it = plan->ctx->tuned.find({plan->n, plan->m});
         if (it != plan->ctx->tuned.end()) {
-            if (eng == CS_ENGINE_AUTO && params->precision == CS_FP32) eng = it->second[0];
+            // (the plain kernel computes in FP32 only: mixed precision keeps the default order then)
+            if (eng == CS_ENGINE_AUTO && (params->precision == CS_FP32 || it->second[0] != CS_ENGINE_PLAIN))
+                eng = it->second[0];
             d->plain_threads = it->second[1];
             d->plain_blocks = it->second[2];
         }
@@ -181,6 +186,7 @@ int decode_enqueue(cs_plan* plan, const cs_params* params, const uint8_t* key, c
     if (st) return st;
     cudaError_t e = engine == CS_ENGINE_TC          ? launch_decode_tc(d, stream)
                     : engine == CS_ENGINE_TC_STREAM ? launch_decode_tcs(d, stream)
+                    : engine == CS_ENGINE_TC_CHUNK  ? launch_decode_tcz(d, stream)
                                                     : launch_decode_plain(d, stream);
     if (e != cudaSuccess) return cuda_fail(e, "decode launch");
     return CS_OK;
@@ -439,7 +445,7 @@ int cs_encode_gop(cs_plan* plan, const cs_params* params, const uint8_t* frames_
     int st = make_shape(plan, params, &gs);
     if (st) return st;
     if (gs.n_cs > 0 && (!frames_dev || !y_dev)) return fail(CS_EINVAL, "null buffer");
-    if (params->engine < CS_ENGINE_AUTO || params->engine > CS_ENGINE_TC_STREAM) return fail(CS_EINVAL, "bad engine");
+    if (params->engine < CS_ENGINE_AUTO || params->engine > CS_ENGINE_TC_CHUNK) return fail(CS_EINVAL, "bad engine");
     // the tensor-core encode where the plan has Phi images for it, unless the plain
     // engine is asked for
     const bool tc = params->engine != CS_ENGINE_PLAIN && encode_tcg_supported(plan);
@@ -459,7 +465,7 @@ int cs_encode_batch(cs_ctx* ctx, int32_t n_plans, cs_plan* const* plans, const c
         if (!plans[i] || plans[i]->ctx != ctx) return fail(CS_EINVAL, "plan of another context");
         const int st = make_shape(plans[i], &params[i], &gs[i]);
         if (st) return st;
-        if (params[i].engine < CS_ENGINE_AUTO || params[i].engine > CS_ENGINE_TC_STREAM)
+        if (params[i].engine < CS_ENGINE_AUTO || params[i].engine > CS_ENGINE_TC_CHUNK)
             return fail(CS_EINVAL, "bad engine");
         if (gs[i].h != gs[0].h || gs[i].w != gs[0].w || gs[i].g != gs[0].g || gs[i].n_gops != gs[0].n_gops ||
             gs[i].b != gs[0].b)
@@ -499,7 +505,7 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
                     cs_stream_t stream) {
     if (!ctx || n_jobs < 0 || (n_jobs > 0 && (!plans || !params || !key_dev || !y_dev)))
         return fail(CS_EINVAL, "null argument");
-    std::vector<DecodeArgs> tc_jobs, tcs_jobs, plain_jobs;
+    std::vector<DecodeArgs> tc_jobs, tcs_jobs, tcz_jobs, plain_jobs;
     tc_jobs.reserve(n_jobs);
     for (int i = 0; i < n_jobs; ++i) {
         if (!plans[i] || plans[i]->ctx != ctx) return fail(CS_EINVAL, "plan of another context");
@@ -509,7 +515,11 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
                                 frames_f32_dev ? frames_f32_dev[i] : nullptr,
                                 frames_u8_dev ? frames_u8_dev[i] : nullptr, &d, &engine);
         if (st) return fail(st, std::string("job ") + std::to_string(i) + ": " + cs_last_error());
-        (engine == CS_ENGINE_TC ? tc_jobs : engine == CS_ENGINE_TC_STREAM ? tcs_jobs : plain_jobs).push_back(d);
+        (engine == CS_ENGINE_TC          ? tc_jobs
+         : engine == CS_ENGINE_TC_STREAM ? tcs_jobs
+         : engine == CS_ENGINE_TC_CHUNK  ? tcz_jobs
+                                         : plain_jobs)
+            .push_back(d);
     }
     cudaError_t e = cudaSuccess;
     cudaStream_t s = (cudaStream_t)stream;
@@ -533,6 +543,8 @@ int cs_decode_batch(cs_ctx* ctx, int32_t n_jobs, cs_plan* const* plans, const cs
     } else if (!tcs_jobs.empty()) {
         e = launch_decode_tcs_batch(tcs_jobs.data(), (int)tcs_jobs.size(), s);
     }
+    // the chunked kernel's launch takes every SM: after the others on s
+    if (e == cudaSuccess && !tcz_jobs.empty()) e = launch_decode_tcz_batch(tcz_jobs.data(), (int)tcz_jobs.size(), s);
     for (size_t i = 0; e == cudaSuccess && i < plain_jobs.size(); ++i)
         e = launch_decode_plain(plain_jobs[i], s);
     if (e != cudaSuccess) return cuda_fail(e, "batched decode launch");

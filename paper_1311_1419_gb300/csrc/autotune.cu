@@ -47,7 +47,9 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
     CS_CUDA_TRY(cudaSetDevice(ctx->device));
     const int b = plan->b, n = plan->n, m = plan->m;
     const int cols = 64;
-    long long rows = std::min<long long>(152ll * 128, (5ll << 20) / n);   // <= 5 M pixels out
+    // two tiles of 128 blocks per SM (the throughput of a call that fills the GPU;
+    // a kernel that gives a tile one SM needs it), at most 40 M pixels out
+    long long rows = std::min<long long>(2ll * ctx->sm_count * 128, (40ll << 20) / n);
     rows = std::max<long long>(cols, rows / cols * cols);
     GopShape gs;
     gs.b = b;
@@ -68,6 +70,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
     std::vector<Candidate> cands;
     if (tc_supported(plan, CS_FP32)) cands.push_back({CS_ENGINE_TC, 0, 0});
     if (tcs_supported(plan)) cands.push_back({CS_ENGINE_TC_STREAM, 0, 0});
+    if (tcz_supported(plan)) cands.push_back({CS_ENGINE_TC_CHUNK, 0, 0});
     const size_t n_tc = cands.size();
     int t_def = 0, r_def = 0;
     plain_default_shape(n, m, &t_def, &r_def);
@@ -94,7 +97,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
         e = cudaMemcpyAsync(y, y_host.data(), y_host.size() * sizeof(float), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(key, 0, px, s);
 
-    const int iters = 8;
+    const int iters = 16;
     Candidate best{0, 0, 0};
     float best_ms = -1.f, plain_default_ms = 0.f;
     for (size_t i = 0; e == cudaSuccess && i < cands.size(); ++i) {
@@ -117,6 +120,7 @@ extern "C" int cs_autotune(cs_ctx* ctx, cs_plan* plan, int32_t* engine, int32_t*
         auto launch = [&]() {
             return cands[i].engine == CS_ENGINE_TC          ? launch_decode_tc(d, s)
                    : cands[i].engine == CS_ENGINE_TC_STREAM ? launch_decode_tcs(d, s)
+                   : cands[i].engine == CS_ENGINE_TC_CHUNK  ? launch_decode_tcz(d, s)
                                                             : launch_decode_plain(d, s);
         };
         e = launch();   // warm-up (and first-launch attribute set-up)

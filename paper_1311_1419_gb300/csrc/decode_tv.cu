@@ -245,6 +245,7 @@ extern "C" int cs_decode_gop_tv(cs_plan* plan, const cs_params* params, float be
     // the on-chip tensor-core kernel (16 x 16 blocks, M <= 128), else the streaming
     // one, else (or when the budget leaves no room for the streaming state) the
     // plain kernel; an explicit engine insists on its kernel
+    if (params->engine == CS_ENGINE_TC_CHUNK) return fail(CS_EINVAL, "TV recovery has no chunked tensor-core kernel");
     if ((params->engine == CS_ENGINE_AUTO || params->engine == CS_ENGINE_TC) && tv_tc_supported(plan)) {
         const cudaError_t e = launch_decode_tv_tc(plan, gs, it, beta, mu, alpha, key_dev, y_dev, frames_f32_dev,
                                                   frames_u8_dev, s);

@@ -218,6 +218,12 @@ cudaError_t launch_decode_tcs(const DecodeArgs& d, cudaStream_t s);
 cudaError_t launch_decode_tcs_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s,
                                     int max_ctas = 0);
 int tcs_ctas_per_sm();
+// N in {256, 1024}, M <= 128: A streamed, GEMM1 per 128-coefficient chunk from tensor
+// memory, s^{k-1} and s^{k-2} in a slot of the streaming decode's scratch (decode_tcz.cu)
+bool tcz_plan_supported(int n, int m);
+bool tcz_supported(const cs_plan* plan);
+cudaError_t launch_decode_tcz(const DecodeArgs& d, cudaStream_t s);
+cudaError_t launch_decode_tcz_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
 // fork streams of a context: 0 .. 2 the on-chip kernel's extra groups, 3 the batched
 // streaming launch, 4 the streaming tail of cluster-kernel jobs, 5 (the device's
 // highest stream priority) the cluster kernel when it has tails beside it

@@ -48,12 +48,12 @@ def test_autotuned_decode_matches_oracle(B, ctx, h, w, gop, b, m, iters):
     frames, plan, p, key, y = _case(B, ctx, h, w, gop, b, m, iters, seed=5)
     try:
         eng, thr, blk, ns = B.cs_autotune(ctx, plan)
-        assert eng in (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM, B.CS_ENGINE_PLAIN) and ns > 0
+        assert eng in (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM, B.CS_ENGINE_TC_CHUNK, B.CS_ENGINE_PLAIN) and ns > 0
         if eng == B.CS_ENGINE_PLAIN:
             assert thr in (64, 128, 256, 512, 1024) and blk in (1, 2, 4, 8, 16)
         else:
             assert thr == 0 and blk == 0
-            if eng == B.CS_ENGINE_TC:
+            if eng in (B.CS_ENGINE_TC, B.CS_ENGINE_TC_CHUNK):
                 assert b in (16, 32) and m <= 128
         print("N=%d M=%d: engine %d threads %d blocks/CTA %d, %.2f ns per block-iteration"
               % (b * b, m, eng, thr, blk, ns))
