@@ -68,9 +68,15 @@ WORKLOADS["mixed64"] = {
 DEFAULT_WORKLOAD = "720p"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the decode of one
-# step, from one ncu capture of that exact configuration (FP32-grade, batched);
-# reported as roofline.traffic for it only, null for anything else
-DECODE_DRAM_BYTES = {"cif": 62_840_000, "720p": 24_975_000_000}
+# step, from one ncu capture of that exact configuration (FP32-grade, batched) on
+# the engine it ran (2 = on-chip tensor cores, 4 = chunked); reported as
+# roofline.traffic when the step's decode ran on that engine, null otherwise
+DECODE_DRAM_BYTES = {"cif": (2, 62_840_000), "720p": (4, 293_170_000_000)}
+
+
+def decode_traffic(workload, res):
+    engine, nbytes = DECODE_DRAM_BYTES.get(workload, (None, None))
+    return nbytes if res["engines"] == [engine] else None
 FP32_LANES_PER_SM = 128
 
 
@@ -365,26 +371,29 @@ def run_reference(args, wl, frames):
 
 
 def mixed_launches(jobs, clusters=15, kappa=13) -> int:
-    """Kernels one cs_decode_batch of the mix launches: one per group of up to 48
-    jobs of each tensor-core kernel (16x16 on chip by shared-memory layout, 32x32
-    cluster, streaming; one operand type here), one for the streaming tail of the
-    cluster jobs when one of them has more tiles than clusters x kappa (the
-    library's rule; 15 clusters of 8 are co-resident on this part), and one per
-    plain-kernel job."""
+    """Kernels one cs_decode_batch of the mix launches, from each job's engine
+    (j["engine"]: 1 plain, 2 on chip, 3 streaming, 4 chunked): one per group of up
+    to 48 jobs of each tensor-core kernel (16x16 on chip by shared-memory layout,
+    32x32 cluster, streaming, chunked; one operand type here), one for the
+    streaming tail of the cluster jobs when one of them has more tiles than
+    clusters x kappa (the library's rule; 15 clusters of 8 are co-resident on this
+    part), and one per plain-kernel job."""
     groups = {}
     for j in jobs:
-        b, m = j["p"].block, j["p"].m
+        b, m, eng = j["p"].block, j["p"].m, j["engine"]
         m16 = (m + 15) // 16 * 16
-        if not j["tc"]:
+        if eng == 1:
             key = ("plain", len(groups))
-        elif b == 16 and m <= 128:
+        elif eng == 4:
+            key = ("tcz",)
+        elif eng == 3:
+            key = ("tcs",)
+        elif b == 16:
             key = ("tc", m16 <= 96)
-        elif b == 32 and m <= 128:
+        else:
             key = ("tc8",)
             if -(-j.get("blocks", 0) // 128) > clusters * kappa:
                 groups[("tc8 tail",)] = 1
-        else:
-            key = ("tcs",)
         groups[key] = groups.get(key, 0) + 1
     return sum(-(-c // 48) for c in groups.values())
 
@@ -456,6 +465,14 @@ def run_mixed64(args, wl, B, torch, dev, steps, warmup, with_oracle=True):
             key = (j["p"].block, j["p"].m)
             if key not in tuned:
                 tuned[key] = B.cs_autotune(ctx, j["plan"])
+            # the library's rule for CS_ENGINE_AUTO: the tuned engine, except that a
+            # mixed-precision job whose tuned engine is the (FP32-only) plain kernel
+            # takes the on-chip tensor-core kernel, else the streaming one
+            eng = tuned[key][0]
+            if j["p"].precision != B.CS_FP32 and eng == B.CS_ENGINE_PLAIN:
+                b, m = key
+                eng = B.CS_ENGINE_TC if (b in (16, 32) and m <= 128) else B.CS_ENGINE_TC_STREAM
+            j["engine"] = eng
         setup_s = time.perf_counter() - t0
         args_ = ([j["plan"] for j in jobs], [j["p"] for j in jobs], [j["key"] for j in jobs],
                  [j["y"] for j in jobs], [j["out"] for j in jobs])
@@ -707,6 +724,7 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
            "psnr": {str(m): float(np.mean(psnr_dev[m].cpu().numpy())) for m in ms},
            "enc_bytes": frames.nbytes + sum(4 * n_cs * nblk * m for m in ms),
            "psnr_bytes": len(ms) * n_cs * h * w * (1 + 4)}
+    res["engines"] = sorted({engine if engine != B.CS_ENGINE_AUTO else tuned[str(m)]["engine"] for m in ms})
     tc_engines = (B.CS_ENGINE_TC, B.CS_ENGINE_TC_STREAM, B.CS_ENGINE_TC_CHUNK)
     res["tc_used"] = engine in tc_engines or (
         engine == B.CS_ENGINE_AUTO and all(t["engine"] in tc_engines for t in tuned.values()))
@@ -977,7 +995,7 @@ def main():
     value = job_throughput(world, res["pixels_step"], args.steps, total_ms) / 1e6
     e2e_value = job_throughput(world, res["pixels_step"], args.steps, e2e_total) / 1e6
     all_fp32 = all(p.precision == B.CS_FP32 for p in res["params"].values())
-    traffic = DECODE_DRAM_BYTES.get(args.workload) if (
+    traffic = decode_traffic(args.workload, res) if (
         res["tc_used"] and all_fp32 and not args.no_batch and not args.only_m and not args.frames) else None
     roof = roofline(res["flops"], res["dec_ms"], peaks, peak_kind, res["tc_used"], res["clocks"],
                     n_sm, traffic)
@@ -1002,7 +1020,7 @@ def main():
                "unit": "Mpixel/s", "ms_per_step": sum(cres["step_ms"]) / 5,
                "decode_ms_per_step": cres["dec_ms"], "decode_gflop_per_step": cres["flops"] / 1e9,
                "roofline": roofline(cres["flops"], cres["dec_ms"], peaks, peak_kind, cres["tc_used"],
-                                    cres["clocks"], n_sm, DECODE_DRAM_BYTES["cif"]),
+                                    cres["clocks"], n_sm, decode_traffic("cif", cres)),
                "gpu_launches": cres["launches_per_step"] * 5, "psnr_db": cres["psnr"]}
         if not args.no_tv:
             cif["tv_recovery"] = tv_run(B, torch, dev, cres, cwl, cwl["iters"],
