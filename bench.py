@@ -60,7 +60,7 @@ WORKLOADS = {
 WORKLOADS["mixed64"] = {
     "workload": "64 GOPs (seeds 0..63) of QCIF/CIF/720p, 8x8/16x16/32x32 blocks, M/N uniform in "
                 "5%..50%, GOP uniform in 4..32, FISTA 300 iters, synthetic surveillance scenes; "
-                "split-BF16 on the tensor-core kernels (on-chip or streaming), FP32 on the plain "
+                "split-BF16 on the tensor-core kernels (on-chip, streaming or chunked), FP32 on the plain "
                 "kernel for any shape they do not cover; one cs_decode_batch captured in a CUDA graph",
     "metric": "recovered Mpixel/s at fixed iters (64 heterogeneous GOPs, one graph-captured batch)",
     "iters": 300, "lambda_rel": 0.01, "seed": 0, "jobs": 64,
