@@ -370,13 +370,15 @@ def run_reference(args, wl, frames):
     print(json.dumps(line), flush=True)
 
 
-def mixed_launches(jobs, clusters=15, kappa=13) -> int:
+def mixed_launches(jobs, clusters=15, kappa=13, n_sm=152) -> int:
     """Kernels one cs_decode_batch of the mix launches, from each job's engine
     (j["engine"]: 1 plain, 2 on chip, 3 streaming, 4 chunked): one per group of up
     to 48 jobs of each tensor-core kernel (16x16 on chip by shared-memory layout,
     32x32 cluster, streaming, chunked; one operand type here), one for the
     streaming tail of the cluster jobs when one of them has more tiles than
-    clusters x kappa (the library's rule; 15 clusters of 8 are co-resident on this
+    clusters x kappa, one for the cluster-kernel heads of the chunked 32x32 jobs
+    whose last round of tiles is short (more tiles than SMs, at most 4 x clusters
+    left over) (the library's rules; 15 clusters of 8 are co-resident on this
     part), and one per plain-kernel job."""
     groups = {}
     for j in jobs:
@@ -386,6 +388,9 @@ def mixed_launches(jobs, clusters=15, kappa=13) -> int:
             key = ("plain", len(groups))
         elif eng == 4:
             key = ("tcz",)
+            t = -(-j.get("blocks", 0) // 128)
+            if b == 32 and t > n_sm and 0 < t % n_sm <= 4 * clusters:
+                groups[("tc8 head",)] = groups.get(("tc8 head",), 0) + 1
         elif eng == 3:
             key = ("tcs",)
         elif b == 16:
@@ -506,7 +511,7 @@ def run_mixed64(args, wl, B, torch, dev, steps, warmup, with_oracle=True):
             "workload": wl["workload"], "jobs": len(jobs),
             "tensor_core_jobs": sum(j["tc"] for j in jobs), "pixels_per_step": pixels,
             "tensor_core_pixel_share": tc_pix / pixels, "gflop_per_step": gflop,
-            "achieved_tflops": gflop / ms, "gpu_launches": mixed_launches(jobs) * steps,
+            "achieved_tflops": gflop / ms, "gpu_launches": mixed_launches(jobs, n_sm=torch.cuda.get_device_properties(dev).multi_processor_count) * steps,
             "clocks": clocks.summary(), "setup_s": setup_s, "autotuned_shapes": len(tuned),
         }
         if with_oracle:
@@ -595,6 +600,11 @@ def codec_run(wl, B, torch, dev, world, barrier, steps, warmup, engine, want_e2e
                 groups.add(("tcs",))
             elif eng == B.CS_ENGINE_TC_CHUNK:
                 groups.add(("tcz",))
+                # the library hands a short last round of a 32x32 job to the cluster
+                # kernel (more tiles than SMs, at most 4 x 15 clusters left over)
+                tiles = -(-(n_cs * nblk) // 128)
+                if n == 1024 and tiles > n_sm and 0 < tiles % n_sm <= 4 * 15:
+                    groups.add(("tc8 head",))
             elif n == 256:
                 groups.add(("tc", m16 <= 96))
             else:

@@ -783,6 +783,11 @@ static cudaError_t launch_group8(const DecodeArgs* const* jobs, int n_jobs, bool
     return slot_done(&ctx->tc8_ring, slot, s);
 }
 
+int tc8_clusters(bool bf) {
+    int c = 0;
+    return co_resident_clusters(bf, &c) == cudaSuccess ? c : 0;
+}
+
 static double job_cost8(const DecodeArgs& d) {
     return (double)((long long)d.gs.n_cs * d.gs.nblk) * (double)d.iters * (double)m16_of8(d.plan->m);
 }
@@ -797,9 +802,14 @@ static double job_cost8(const DecodeArgs& d) {
 // bits in any batch.
 constexpr int kTcsTileRatio = 13;
 
+// (a job's blocks end at row_end when it is set: a range handed over by another kernel)
+static long long job_end8(const DecodeArgs& d) {
+    return d.row_end < 0 ? (long long)d.gs.n_cs * d.gs.nblk : d.row_end;
+}
+
 static long long tail_rows(const DecodeArgs& d, int clusters, int idle_ctas) {
     if (idle_ctas <= 0 || !tcs_supported(d.plan)) return 0;
-    const long long total = (long long)d.gs.n_cs * d.gs.nblk;
+    const long long total = job_end8(d);
     const long long tiles = (total + kTile - 1) / kTile;
     const long long one_round = (long long)clusters * kTcsTileRatio;
     const long long rounds = tiles / (one_round + idle_ctas);
@@ -826,7 +836,7 @@ cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStre
         for (DecodeArgs& d : head[bf]) {
             const long long t = tail_rows(d, clusters, idle_ctas);
             if (t <= 0) continue;
-            const long long total = (long long)d.gs.n_cs * d.gs.nblk;
+            const long long total = job_end8(d);
             DecodeArgs dt = d;
             dt.row_begin = total - t;
             dt.row_end = total;

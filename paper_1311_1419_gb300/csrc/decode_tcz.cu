@@ -414,17 +414,33 @@ __device__ __forceinline__ float gmax_z(uint32_t gaddr, float mx) {
     return mx;
 }
 
+// The thread's s^{k-1} (a) and s^{k-2} (c) for 16 coefficients at float4 index v0 ..
+// (each 128 float4 apart): zero where iteration k has none (k < 1, k < 2).
+__device__ __forceinline__ void load_s_z(const float4* __restrict__ s1, const float4* __restrict__ s2, size_t v0,
+                                         int k, float4 (&a)[4], float4 (&c)[4]) {
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        a[v] = k >= 1 ? s1[v0 + (size_t)v * kTile] : make_float4(0.f, 0.f, 0.f, 0.f);
+        c[v] = k >= 2 ? s2[v0 + (size_t)v * kTile] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
 // The step for the thread's 32 coefficients of one chunk, 16 at a time (G from
 // accumulator columns gaddr ..; the coefficients' s values at float4 index v0 ..
 // v0 + 7, each 128 float4 apart): z^k = s^{k-1} + beta_{k-1} (s^{k-1} - s^{k-2})
 // (0 at k = 0), s^k = soft(z^k - g / L, tau) written over s^{k-2}, and, when
 // want_z, z^{k+1} = s^k + beta_k (s^k - s^{k-1}) as hi / lo pairs into the Z chunk's
 // columns zcol .. of tensor memory, once GEMM1 has finished with the previous
-// chunk (z_empty).
+// chunk (z_empty).  The first 16 coefficients' s values arrive loaded in (pa, pc);
+// when nk >= 0 the step leaves there the first 16 of the next chunk's (iteration
+// nk, index nv0 in n1 / n2), so that their loads overlap the hand-over between
+// chunks.
 template <bool BF>
 __device__ __forceinline__ void step_z(const TczJob& J, const TczLaunch& L, MiscZ* ms, const float4* __restrict__ s1,
                                        float4* __restrict__ s2, size_t v0, uint32_t gaddr, uint32_t zcol, int k,
-                                       float tau, bool want_z, uint32_t& zw) {
+                                       float tau, bool want_z, uint32_t& zw, float4 (&pa)[4], float4 (&pc)[4],
+                                       const float4* __restrict__ n1, const float4* __restrict__ n2, size_t nv0,
+                                       int nk) {
     const float2 ginv2 = make_float2(-J.sg * J.inv_l, -J.sg * J.inv_l);
     const float bk = L.beta[k], bkm1 = k > 0 ? L.beta[k - 1] : 0.f;
     const float2 b2 = make_float2(bk, bk), bm2 = make_float2(bkm1, bkm1);
@@ -433,19 +449,13 @@ __device__ __forceinline__ void step_z(const TczJob& J, const TczLaunch& L, Misc
         uint32_t g[2][8];
         tmem_ld8(gaddr + 16 * h, g[0]);
         tmem_ld8(gaddr + 16 * h + 8, g[1]);
-        float4 a[4], c[4];   // s^{k-1}, s^{k-2}
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            const size_t vi = v0 + (size_t)(4 * h + v) * kTile;
-            a[v] = k >= 1 ? s1[vi] : make_float4(0.f, 0.f, 0.f, 0.f);
-            c[v] = k >= 2 ? s2[vi] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
+        if (h == 1) load_s_z(s1, s2, v0 + 4 * kTile, k, pa, pc);
         tmem_wait_ld();
         uint32_t zh[8], zl[8];
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const float2 a2[2] = {make_float2(a[v].x, a[v].y), make_float2(a[v].z, a[v].w)};
-            const float2 c2[2] = {make_float2(c[v].x, c[v].y), make_float2(c[v].z, c[v].w)};
+            const float2 a2[2] = {make_float2(pa[v].x, pa[v].y), make_float2(pa[v].z, pa[v].w)};
+            const float2 c2[2] = {make_float2(pc[v].x, pc[v].y), make_float2(pc[v].z, pc[v].w)};
             float2 sk[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
@@ -461,6 +471,7 @@ __device__ __forceinline__ void step_z(const TczJob& J, const TczLaunch& L, Misc
             }
             s2[v0 + (size_t)(4 * h + v) * kTile] = make_float4(sk[0].x, sk[0].y, sk[1].x, sk[1].y);
         }
+        if (h == 1 && nk >= 0) load_s_z(n1, n2, nv0, nk, pa, pc);
         if (want_z) {
             if (h == 0) {
                 // GEMM1 of the previous chunk has read the Z columns
@@ -541,18 +552,25 @@ __device__ __forceinline__ void epi_role_z(const TczLaunch& L, MiscZ* ms, uint8_
             atomicMax(&ms->colmax[r], __float_as_uint(mx * J.sg));
             named_sync(kBarEpi, kEpiThreads);
             const float tau = J.lambda_rel * __uint_as_float(ms->colmax[r]) * J.inv_l;
+            // the thread's first s index of chunk c; s^k goes over s^{k-2}: even k into
+            // buf0, odd k into buf1
+            auto vidx = [&](int c) { return (size_t)(c * (kCc / 4) + cg * (kPerThread / 4)) * kTile + r; };
+            float4 pa[4], pc[4];   // the next chunk's first 16 s^{k-1} and s^{k-2}: none at k = 0
+#pragma unroll
+            for (int v = 0; v < 4; ++v) pa[v] = pc[v] = make_float4(0.f, 0.f, 0.f, 0.f);
             for (int k = 0; k < K; ++k) {
                 const bool want_z = k + 1 < K;
-                // s^k goes over s^{k-2}: even k into buf0, odd k into buf1
                 const float4* s1 = (k & 1) ? buf0 : buf1;
                 float4* s2 = (k & 1) ? buf1 : buf0;
                 for (int c = 0; c < nch; ++c, ++acc) {
                     wait_z(ms, &ms->acc_full[acc & 1], (acc >> 1) & 1, L.err);
                     fence_after_sync();
-                    const size_t v0 = (size_t)(c * (kCc / 4) + cg * (kPerThread / 4)) * kTile + r;
-                    step_z<BF>(J, L, ms, s1, s2, v0,
+                    // the next chunk: c + 1 of this iteration, else chunk 0 of the next one
+                    const int kn = c + 1 < nch ? k : k + 1, cn = c + 1 < nch ? c + 1 : 0;
+                    step_z<BF>(J, L, ms, s1, s2, vidx(c),
                                lane_addr + kColG + (acc & 1) * kCc + (uint32_t)(kPerThread * cg),
-                               lane_addr + (uint32_t)(kPerThread / 2 * cg), k, tau, want_z, zw);
+                               lane_addr + (uint32_t)(kPerThread / 2 * cg), k, tau, want_z, zw, pa, pc,
+                               (kn & 1) ? buf0 : buf1, (kn & 1) ? buf1 : buf0, vidx(cn), kn < K ? kn : -1);
                     fence_before_sync();
                     __syncwarp();
                     if (lane == 0) {
@@ -752,12 +770,46 @@ cudaError_t launch_group_z(const DecodeArgs* const* jobs, int n_jobs, bool bf, c
 
 }  // namespace
 
+// A 32 x 32 job with more tiles than SMs leaves a last round of (tiles mod SMs)
+// tiles on as many SMs, which takes as long as a full round.  When that remainder is
+// at most four rounds of the cluster kernel's co-resident clusters (a tile-iteration
+// there takes about a fifth of one here, on eight SMs), the cluster kernel decodes
+// the job's first `remainder` tiles and this kernel the rest in whole rounds, one
+// after the other on the call's stream.  The split depends on the job and the
+// device alone, so a job decodes to the same bits in any batch.
+static long long cluster_head_rows(const DecodeArgs& d) {
+    if (d.plan->n != 1024 || d.row_begin != 0 || !tc_supported(d.plan, d.precision)) return 0;
+    const long long tiles = (job_rows_z(d) + kTile - 1) / kTile;
+    const int sm = d.plan->ctx->sm_count;
+    const long long rem = tiles % sm;
+    if (tiles <= sm || rem == 0) return 0;
+    const int clusters = tc8_clusters(d.precision == CS_BF16 || d.precision == CS_BF16X2);
+    return rem <= 4ll * clusters ? rem * kTile : 0;
+}
+
 cudaError_t launch_decode_tcz_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s) {
-    std::vector<const DecodeArgs*> groups[2];
+    std::vector<DecodeArgs> own, heads;
+    own.reserve(n_jobs);
     for (int i = 0; i < n_jobs; ++i) {
         if (job_rows_z(jobs[i]) <= 0) continue;
-        const bool bf = jobs[i].precision == CS_BF16 || jobs[i].precision == CS_BF16X2;
-        groups[bf ? 1 : 0].push_back(&jobs[i]);
+        const long long h = cluster_head_rows(jobs[i]);
+        DecodeArgs d = jobs[i];
+        if (h > 0) {
+            DecodeArgs dh = d;
+            dh.row_end = h;
+            heads.push_back(dh);
+            d.row_begin = h;
+        }
+        own.push_back(d);
+    }
+    if (!heads.empty()) {
+        const cudaError_t e = launch_decode_tc8_batch(heads.data(), (int)heads.size(), s);
+        if (e != cudaSuccess) return e;
+    }
+    std::vector<const DecodeArgs*> groups[2];
+    for (const DecodeArgs& d : own) {
+        const bool bf = d.precision == CS_BF16 || d.precision == CS_BF16X2;
+        groups[bf ? 1 : 0].push_back(&d);
     }
     for (int bf = 0; bf < 2; ++bf) {
         std::vector<const DecodeArgs*>& g = groups[bf];

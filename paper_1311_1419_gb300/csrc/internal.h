@@ -205,6 +205,7 @@ cudaError_t launch_decode_tv_tcs(const cs_plan* plan, const GopShape& gs, int it
 size_t scratch_room_of(const cs_ctx* ctx);
 // 32 x 32 blocks (N = 1024): clusters of 8 CTAs (decode_tc8.cu)
 cudaError_t launch_decode_tc8_batch(const DecodeArgs* jobs, int n_jobs, cudaStream_t s);
+int tc8_clusters(bool bf);   // clusters of the cluster kernel co-resident on the device (0: none)
 cudaError_t launch_tc8_images(const float* a, uint8_t* img, int m, int ea, cudaStream_t s);
 size_t tc8_slot_bytes(int sm_count);   // one per-launch area of the cluster decode
 // any N in {64, 256, 1024}, M <= 512, iterates in global memory (decode_tcs.cu)

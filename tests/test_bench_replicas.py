@@ -55,22 +55,29 @@ def test_one_rank_needs_no_process_group():
 
 
 def test_mixed_launch_count():
-    """The mixed bench's launch count: one launch per group of up to 48 jobs of each
+    """The mixed bench's launch count, from each job's engine (1 plain, 2 on chip,
+    3 streaming, 4 chunked): one launch per group of up to 48 jobs of each
     tensor-core kernel (16x16 on chip by shared-memory layout, 32x32 cluster,
-    streaming) and one per plain-kernel job."""
+    streaming, chunked) and one per plain-kernel job."""
     import bench
 
     class P:
         def __init__(self, block, m):
             self.block, self.m = block, m
 
-    def job(b, m, tc=True):
-        return {"p": P(b, m), "tc": tc}
-    jobs = ([job(16, 40)] * 50 + [job(16, 128)] + [job(32, 102)] * 3 + [job(32, 300)] * 2 +
-            [job(8, 16)] + [job(16, 40, tc=False)] * 2)
+    def job(b, m, engine):
+        return {"p": P(b, m), "engine": engine}
+    jobs = ([job(16, 40, 2)] * 50 + [job(16, 128, 2)] + [job(32, 102, 2)] * 3 + [job(32, 300, 3)] * 2 +
+            [job(8, 16, 3)] + [job(16, 40, 1)] * 2)
     # on chip: 50 jobs of M16 <= 96 (2 launches) + 1 of M16 = 128; cluster: 1;
     # streaming: 3 (32x32 M > 128, 8x8) in 1; plain: 2
     assert bench.mixed_launches(jobs) == 2 + 1 + 1 + 1 + 2
     # a cluster job of more than 15 x 13 tiles adds the streaming tail's launch
-    big = dict(job(32, 102), blocks=196 * 128)
+    big = dict(job(32, 102, 2), blocks=196 * 128)
     assert bench.mixed_launches(jobs + [big]) == 2 + 1 + 1 + 1 + 2 + 1
+    # chunked jobs of any block size share one launch per 48
+    assert bench.mixed_launches(jobs + [job(32, 102, 4)] * 49 + [job(16, 64, 4)]) == 2 + 1 + 1 + 1 + 2 + 2
+    # a chunked 32x32 job of 647 tiles (39 left over on 152 SMs) adds the cluster head's
+    # launch; one of 216 tiles (64 left over) does not
+    assert bench.mixed_launches(jobs + [dict(job(32, 102, 4), blocks=82800)]) == 2 + 1 + 1 + 1 + 2 + 1 + 1
+    assert bench.mixed_launches(jobs + [dict(job(32, 102, 4), blocks=27600)]) == 2 + 1 + 1 + 1 + 2 + 1

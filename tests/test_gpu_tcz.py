@@ -126,6 +126,27 @@ def test_tcz_more_tiles_than_sms_agrees_with_the_streaming_kernel(B, ctx):
     assert rel <= 1e-4
 
 
+def test_tcz_short_last_round_goes_to_the_cluster_kernel(B, ctx):
+    # three 720p GOPs of 16 frames: 41400 blocks, 324 tiles.  On 152 SMs with 15
+    # co-resident clusters of 8 the last round would hold 20 tiles: the cluster kernel
+    # decodes the first 20 tiles instead (bit for bit its own decode of them, which the
+    # on-chip engine gives for those rows too) and this kernel the other 304 in two
+    # whole rounds; everything matches the streaming kernel
+    h, w, gop, n_gops, b, m, iters = 720, 1280, 16, 3, 32, 102, 12
+    _, tcz, _ = _run(B, ctx, h, w, gop, b, m, iters, seed=25, n_gops=n_gops)
+    _, tc, _ = _run(B, ctx, h, w, gop, b, m, iters, seed=25, n_gops=n_gops, engine=B.CS_ENGINE_TC)
+    frames, tcs, _ = _run(B, ctx, h, w, gop, b, m, iters, seed=25, n_gops=n_gops, engine=B.CS_ENGINE_TC_STREAM)
+    keys = np.repeat(frames[::gop].astype(np.float64), gop - 1, axis=0)
+    rel = np.linalg.norm(tcz - tcs) / np.linalg.norm(tcs - keys)
+    print("tcz (with a cluster head) vs tcs, 41400 blocks: residual rel-l2 %.3g" % rel)
+    assert np.isfinite(tcz).all() and rel <= 1e-4
+    if torch.cuda.get_device_properties(0).multi_processor_count == 152:
+        # rows 0 .. 2559: CS frames 0 and 1 whole (920 blocks each)
+        assert np.array_equal(tcz[:2].astype(np.float32).view(np.uint32), tc[:2].astype(np.float32).view(np.uint32))
+        # and the chunked kernel's rows differ from the cluster kernel's in the last bits
+        assert not np.array_equal(tcz[5:], tc[5:])
+
+
 def test_tcz_in_a_batch_equals_alone(B, ctx):
     # two chunked jobs of different N and M in one cs_decode_batch (one launch) give
     # the bits each gives alone
