@@ -69,9 +69,11 @@ DEFAULT_WORKLOAD = "720p"
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the decode of one
 # step, from one ncu capture of that exact configuration (FP32-grade, batched) on
-# the engine it ran (2 = on-chip tensor cores, 4 = chunked); reported as
-# roofline.traffic when the step's decode ran on that engine, null otherwise
-DECODE_DRAM_BYTES = {"cif": (2, 62_840_000), "720p": (4, 293_170_000_000)}
+# the engine it ran (2 = on-chip tensor cores; 4 = chunked, whose 720p decode is
+# one cluster-kernel launch for the first 39 tiles and one chunked launch for the
+# other 608); reported as roofline.traffic when the step's decode ran on that
+# engine, null otherwise
+DECODE_DRAM_BYTES = {"cif": (2, 62_840_000), "720p": (4, 294_277_000_000)}
 
 
 def decode_traffic(workload, res):
