@@ -19,7 +19,7 @@
 // beta_{k-1} (s^{k-1} - s^{k-2}) in FP32 from the two previous iterates, which
 // stay in global memory (the new s^k is written over s^{k-2}): 8 bytes read and
 // 4 written per coefficient and iteration.  P stays in shared memory; only the
-// slices of A's two images stream, through a six-stage ring fed by a copy warp.
+// slices of A's two images stream, through a four-stage ring fed by a copy warp.
 // Tensor memory: two 128-column G accumulators (the step of chunk c overlaps
 // GEMM2 of chunk c + 1), U (M16 columns) and the Z chunk's hi and lo halves.
 // Mixed precision: a split product uses three MMAs (hi.hi + lo.hi + hi.lo), a
@@ -51,7 +51,7 @@ constexpr int kPerThread = kCc / kColGroups;  // coefficients of a chunk per epi
 constexpr int kSliceK = 32;                 // K per ring slot: one 64-byte swizzle atom
 constexpr uint32_t kHalfBytes = 8192;       // one slice of A, hi or lo: 32 x 128 or M16 x 32 fp16
 constexpr uint32_t kStageBytes = 2 * kHalfBytes;
-constexpr int kStages = 6;
+constexpr int kStages = 4;
 constexpr uint32_t kTBytes = kTile * 64;    // one 32-wide K slice of P (8 KB)
 constexpr uint32_t kPBytes = (kMaxM16z / kSliceK) * kTBytes;   // P hi (or lo): 32 KB
 constexpr uint32_t kOffP = kStages * kStageBytes;              // P hi, then P lo
