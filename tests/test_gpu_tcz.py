@@ -2,8 +2,9 @@
 GEMM1 in 128-coefficient chunks from tensor memory, s^{k-1} and s^{k-2} in
 global memory) against the FP64 oracle: 16 x 16 and 32 x 32 blocks, M from one
 16-row step to 128 (partial last K slices), ragged tiles, cropped edges, two
-GOPs, iteration counts 0 .. 3, mixed precision, more tiles than SMs, inside a
-batch, the engine rules and the bounded-wait failure path."""
+GOPs, iteration counts 0 .. 3, mixed precision, more tiles than SMs, a short last
+round handed to the cluster kernel (also inside a CUDA graph), inside a batch (one
+and both operand types), the engine rules and the bounded-wait failure path."""
 import time
 
 import numpy as np
@@ -170,6 +171,67 @@ def test_tcz_in_a_batch_equals_alone(B, ctx):
         B.cs_ctx_status(ctx)
         for a, o in zip(alone, outs):
             assert np.array_equal(a.cpu().numpy().view(np.uint32), o.cpu().numpy().view(np.uint32))
+    finally:
+        for p in plans:
+            B.cs_plan_destroy(p)
+
+
+def test_tcz_with_a_cluster_head_replays_from_a_cuda_graph(B, ctx):
+    # three 720p GOPs (324 tiles): on 152 SMs the first 20 tiles go to the cluster
+    # kernel and the rest to this kernel; the captured call replays to the eager bits
+    h, w, gop, n_gops, b, m, iters = 720, 1280, 16, 3, 32, 102, 6
+    frames = scenes.surveillance_video(gop * n_gops, h, w, seed=26)
+    plan = B.cs_make_phi(ctx, b * b, m, 26)
+    try:
+        p = B.make_params(h, w, gop, b, m, iters=iters, n_gops=n_gops, engine=B.CS_ENGINE_TC_CHUNK)
+        keys, y = _inputs(B, plan, frames, gop, n_gops, b, m, p)
+        eager = torch.zeros((y.shape[0], h, w), dtype=torch.float32, device="cuda")
+        B.cs_decode_gop(plan, p, keys, y, eager, None, torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        B.cs_ctx_status(ctx)
+        graphed = torch.zeros_like(eager)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side, capture_error_mode="thread_local"):
+                B.cs_decode_gop(plan, p, keys, y, graphed, None, side)
+        torch.cuda.current_stream().wait_stream(side)
+        for rep in range(2):
+            graphed.fill_(float("nan"))
+            g.replay()
+            torch.cuda.synchronize()
+            B.cs_ctx_status(ctx)
+            assert np.array_equal(eager.cpu().numpy().view(np.uint32), graphed.cpu().numpy().view(np.uint32)), rep
+    finally:
+        B.cs_plan_destroy(plan)
+
+
+def test_tcz_batch_of_both_operand_types_equals_alone(B, ctx):
+    # FP32-grade (fp16 operands) and split-BF16 chunked jobs in one cs_decode_batch:
+    # one launch per operand type, each job's bits as alone
+    cams = [(96, 160, 3, 32, 102, 20, 41, 0, 0), (96, 128, 4, 32, 64, 20, 42, 2, 0),
+            (144, 176, 3, 16, 77, 20, 43, 1, 8), (80, 112, 3, 16, 40, 20, 44, 0, 0)]
+    plans, params, keys, ys, alone = [], [], [], [], []
+    try:
+        for h, w, gop, b, m, iters, seed, prec, tail in cams:
+            frames = scenes.surveillance_video(gop, h, w, seed=seed)
+            plan = B.cs_make_phi(ctx, b * b, m, seed)
+            plans.append(plan)
+            p = B.make_params(h, w, gop, b, m, iters=iters, precision=prec, fp32_tail_iters=tail,
+                              engine=B.CS_ENGINE_TC_CHUNK)
+            params.append(p)
+            k, y = _inputs(B, plan, frames, gop, 1, b, m, p)
+            keys.append(k)
+            ys.append(y)
+            o = torch.empty((gop - 1, h, w), dtype=torch.float32, device="cuda")
+            B.cs_decode_gop(plan, p, k, y, o, None, torch.cuda.current_stream())
+            alone.append(o)
+        outs = [torch.full_like(o, float("nan")) for o in alone]
+        B.cs_decode_batch(ctx, plans, params, keys, ys, outs, None, torch.cuda.current_stream())
+        B.cs_ctx_status(ctx)
+        for i, (a, o) in enumerate(zip(alone, outs)):
+            assert np.array_equal(a.cpu().numpy().view(np.uint32), o.cpu().numpy().view(np.uint32)), i
     finally:
         for p in plans:
             B.cs_plan_destroy(p)
