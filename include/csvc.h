@@ -111,8 +111,8 @@ int cs_ctx_destroy(cs_ctx* ctx);
 int cs_ctx_status(cs_ctx* ctx);
 /* cs_ctx_set_debug: test hooks for the failure path, consumed by the next
  * launch of the context's tensor-core decodes (CS_ENGINE_TC with N = 256 or
- * 1024, CS_ENGINE_TC_STREAM, or the tensor-core TV kernel of
- * cs_decode_gop_tv).  CS_DEBUG_DROP_ARRIVAL makes one
+ * 1024, CS_ENGINE_TC_STREAM, CS_ENGINE_TC_CHUNK, or either tensor-core TV
+ * kernel of cs_decode_gop_tv).  CS_DEBUG_DROP_ARRIVAL makes one
  * warp of that launch withhold one barrier arrival, so that a device-side wait
  * runs out (after 1 s): the launch then drains, its outputs are incomplete and
  * cs_ctx_status reports CS_ETIMEDOUT; the context stays usable.  No GPU fault
@@ -169,7 +169,12 @@ int cs_encode_batch(cs_ctx* ctx, int32_t n_plans, cs_plan* const* plans, const c
  *   z^{k+1} = s^k + ((t_k - 1)/t_{k+1})(s^k - s^{k-1}),
  * then F'_t = F_key + Psi s^K cropped to H x W.  frames_f32_dev: float32
  * [n_gops*(G-1)][H][W] or NULL; frames_u8_dev: uint8, same shape, clamp of
- * round-half-even, or NULL (at least one must be non-NULL). */
+ * round-half-even, or NULL (at least one must be non-NULL).
+ * CS_ENGINE_TC_CHUNK: a call of 32 x 32 blocks with more 128-block tiles than the
+ * device has SMs, whose last round would hold at most four rounds of the
+ * CS_ENGINE_TC kernel's co-resident clusters, has its first (tiles mod SMs)
+ * tiles decoded by that kernel and the rest by the chunked one, one after the
+ * other on the stream; the split depends on the call and the device only. */
 int cs_decode_gop(cs_plan* plan, const cs_params* params, const uint8_t* key_dev,
                   const float* y_dev, float* frames_f32_dev, uint8_t* frames_u8_dev,
                   cs_stream_t stream);
