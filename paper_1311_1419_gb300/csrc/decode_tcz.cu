@@ -19,7 +19,7 @@
 // beta_{k-1} (s^{k-1} - s^{k-2}) in FP32 from the two previous iterates, which
 // stay in global memory (the new s^k is written over s^{k-2}): 8 bytes read and
 // 4 written per coefficient and iteration.  P stays in shared memory; only the
-// slices of A's two images stream, through a four-stage ring fed by a copy warp.
+// slices of A's two images stream, through a six-stage ring fed by a copy warp.
 // Tensor memory: two 128-column G accumulators (the step of chunk c overlaps
 // GEMM2 of chunk c + 1), U (M16 columns) and the Z chunk's hi and lo halves.
 // Mixed precision: a split product uses three MMAs (hi.hi + lo.hi + hi.lo), a
@@ -51,7 +51,7 @@ constexpr int kPerThread = kCc / kColGroups;  // coefficients of a chunk per epi
 constexpr int kSliceK = 32;                 // K per ring slot: one 64-byte swizzle atom
 constexpr uint32_t kHalfBytes = 8192;       // one slice of A, hi or lo: 32 x 128 or M16 x 32 fp16
 constexpr uint32_t kStageBytes = 2 * kHalfBytes;
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr uint32_t kTBytes = kTile * 64;    // one 32-wide K slice of P (8 KB)
 constexpr uint32_t kPBytes = (kMaxM16z / kSliceK) * kTBytes;   // P hi (or lo): 32 KB
 constexpr uint32_t kOffP = kStages * kStageBytes;              // P hi, then P lo
@@ -60,7 +60,11 @@ constexpr uint32_t kOffMisc = kOffC + 4096;
 constexpr uint32_t kSmemBytes = kOffMisc + 2048 + 1024;        // + alignment slack
 constexpr uint32_t kColG = 0;               // two G accumulators of 128 columns
 constexpr uint32_t kColU = 256;             // U: M16 <= 128 columns
-constexpr uint32_t kColZHi = 384, kColZLo = 448;   // the Z chunk: 128 fp16 pairs-of-columns each
+// the Z chunk in two halves: half h holds coefficients 32 j + 16 h .. 32 j + 16 h + 15 of
+// the chunk (j = 0 .. 3), hi then lo, 32 columns each
+constexpr uint32_t kColZ = 384;
+__host__ __device__ constexpr uint32_t zcol_hi(int h) { return kColZ + 64u * (uint32_t)h; }
+__host__ __device__ constexpr uint32_t zcol_lo(int h) { return kColZ + 64u * (uint32_t)h + 32u; }
 // per-CTA scratch: two s buffers (N floats per block, [N / 4][128 blocks] float4),
 // then the tile's y ([M16 / 4][128] float4)
 constexpr size_t kScrS = (size_t)1024 * kTile * 4;
@@ -106,7 +110,7 @@ namespace {
 struct MiscZ {
     uint64_t full[kStages], empty[kStages];
     uint64_t acc_full[2], acc_empty[2];
-    uint64_t z_full, z_empty, u_full, p_ready, drain;
+    uint64_t z_full[2], z_empty[2], u_full, p_ready, drain;
     uint32_t tmem_base;
     int abort;
     int next_tile;
@@ -238,10 +242,12 @@ __device__ __forceinline__ void copy_role_z(const TczLaunch& L, MiscZ* ms, uint8
 }
 
 // Warp 0: issues every MMA (lane 0).  GEMM2 of a chunk goes into the next of the
-// two G accumulators; GEMM1 of a chunk adds into U once the epilogue has put the
-// chunk's Z into tensor memory (z_full) and frees it again (z_empty); the last
-// chunk's GEMM1 also completes U (u_full).  GEMM1 of z^{k+1} is split (or not)
-// as iteration k + 1's products are.
+// two G accumulators.  GEMM1 of a chunk adds into U in two halves: the first K
+// step of every 32-coefficient slice once the epilogue has put the chunk's half-A Z
+// into tensor memory (z_full[0]), then the second once half B is there (z_full[1]);
+// each half frees its Z columns again (z_empty[h]).  A slice serves both halves, so
+// its ring stage is released after half B.  The last chunk's GEMM1 also completes U
+// (u_full).  GEMM1 of z^{k+1} is split (or not) as iteration k + 1's products are.
 template <bool BF>
 __device__ __forceinline__ void mma_role_z(const TczLaunch& L, MiscZ* ms, uint8_t* sm, uint32_t tbase, int lane) {
     const uint32_t s_base = smem_u32(sm);
@@ -292,39 +298,42 @@ __device__ __forceinline__ void mma_role_z(const TczLaunch& L, MiscZ* ms, uint8_
             __syncwarp();
             ++acc;
         };
-        auto gemm1 = [&](int c, bool split, bool last) {
-            ok = wait_z(ms, &ms->z_full, zt & 1, L.err) && ok;
+        uint32_t g1_stage[kCc / kSliceK];   // the ring stages of the chunk's GEMM1 slices
+        auto gemm1 = [&](int c, int h, bool split, bool last) {
+            ok = wait_z(ms, &ms->z_full[h], zt & 1, L.err) && ok;
             fence_after_sync();
-#pragma unroll 1
+#pragma unroll
             for (int ks = 0; ks < kCc / kSliceK; ++ks) {
-                const uint32_t s = st % kStages, par = (st / kStages) & 1;
-                ok = wait_z(ms, &ms->full[s], par, L.err) && ok;
-                fence_after_sync();
+                if (h == 0) {   // the slices arrive for half A and stay for half B
+                    const uint32_t s = st % kStages, par = (st / kStages) & 1;
+                    ok = wait_z(ms, &ms->full[s], par, L.err) && ok;
+                    fence_after_sync();
+                    g1_stage[ks] = s;
+                    ++st;
+                }
                 if (ok && lane == 0) {
+                    const uint32_t s = g1_stage[ks];
                     const uint32_t stg = s_base + s * kStageBytes;
                     const uint64_t b_hi = desc_sw64(stg, 16, 512);   // K-major: M16 rows of 32 columns
                     const uint64_t b_lo = desc_sw64(stg + kHalfBytes, 16, 512);
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const uint32_t zc = (uint32_t)(16 * ks + 8 * kk);   // 16 coefficients = 8 columns
-                        const uint32_t bo = (uint32_t)kk * 2u;
-                        const uint32_t accum = (c > 0 || ks > 0 || kk > 0) ? 1u : 0u;
-                        mma_f16_tmem_a(tbase + kColU, tbase + kColZHi + zc, b_hi + bo, id1, accum);
-                        if (split) {
-                            mma_f16_tmem_a(tbase + kColU, tbase + kColZLo + zc, b_hi + bo, id1, 1u);
-                            mma_f16_tmem_a(tbase + kColU, tbase + kColZHi + zc, b_lo + bo, id1, 1u);
-                        }
+                    const uint32_t zc = (uint32_t)(8 * ks);           // 16 coefficients = 8 columns
+                    const uint32_t bo = (uint32_t)h * 2u;             // the slice's K step h
+                    const uint32_t accum = (c > 0 || ks > 0 || h > 0) ? 1u : 0u;
+                    mma_f16_tmem_a(tbase + kColU, tbase + zcol_hi(h) + zc, b_hi + bo, id1, accum);
+                    if (split) {
+                        mma_f16_tmem_a(tbase + kColU, tbase + zcol_lo(h) + zc, b_hi + bo, id1, 1u);
+                        mma_f16_tmem_a(tbase + kColU, tbase + zcol_hi(h) + zc, b_lo + bo, id1, 1u);
                     }
-                    mma_commit(&ms->empty[s]);
+                    if (h == 1) mma_commit(&ms->empty[s]);
                 }
                 __syncwarp();
-                ++st;
             }
             if (ok && lane == 0) {
-                mma_commit(&ms->z_empty);
-                if (last) mma_commit(&ms->u_full);
+                mma_commit(&ms->z_empty[h]);
+                if (last && h == 1) mma_commit(&ms->u_full);
             }
             __syncwarp();
-            ++zt;
+            if (h == 1) ++zt;
         };
         if (K > 0) {
             ok = wait_z(ms, &ms->p_ready, pc & 1, L.err) && ok;   // P_0 = -y
@@ -338,9 +347,15 @@ __device__ __forceinline__ void mma_role_z(const TczLaunch& L, MiscZ* ms, uint8_
                 }
                 for (int c = 0; c < nch; ++c) {
                     gemm2(split);
-                    if (want_z && c > 0) gemm1(c - 1, zsplit, false);
+                    if (want_z && c > 0) {
+                        gemm1(c - 1, 0, zsplit, false);
+                        gemm1(c - 1, 1, zsplit, false);
+                    }
                 }
-                if (want_z) gemm1(nch - 1, zsplit, true);
+                if (want_z) {
+                    gemm1(nch - 1, 0, zsplit, true);
+                    gemm1(nch - 1, 1, zsplit, true);
+                }
             }
         }
         cta_sync_z();   // C
@@ -429,16 +444,18 @@ __device__ __forceinline__ void load_s_z(const float4* __restrict__ s1, const fl
 // accumulator columns gaddr ..; the coefficients' s values at float4 index v0 ..
 // v0 + 7, each 128 float4 apart): z^k = s^{k-1} + beta_{k-1} (s^{k-1} - s^{k-2})
 // (0 at k = 0), s^k = soft(z^k - g / L, tau) written over s^{k-2}, and, when
-// want_z, z^{k+1} = s^k + beta_k (s^k - s^{k-1}) as hi / lo pairs into the Z chunk's
-// columns zcol .. of tensor memory, once GEMM1 has finished with the previous
-// chunk (z_empty).  The first 16 coefficients' s values arrive loaded in (pa, pc);
+// want_z, z^{k+1} = s^k + beta_k (s^k - s^{k-1}) as hi / lo pairs into tensor
+// memory: 16 coefficients h into Z half h at column zoff of its hi and lo parts,
+// once GEMM1 has finished with that half of the previous chunk (z_empty[h]), each
+// half announced at once (z_full[h]) so that its GEMM1 runs beside the rest of the
+// step.  The first 16 coefficients' s values arrive loaded in (pa, pc);
 // when nk >= 0 the step leaves there the first 16 of the next chunk's (iteration
 // nk, index nv0 in n1 / n2), so that their loads overlap the hand-over between
 // chunks.
 template <bool BF>
 __device__ __forceinline__ void step_z(const TczJob& J, const TczLaunch& L, MiscZ* ms, const float4* __restrict__ s1,
-                                       float4* __restrict__ s2, size_t v0, uint32_t gaddr, uint32_t zcol, int k,
-                                       float tau, bool want_z, uint32_t& zw, float4 (&pa)[4], float4 (&pc)[4],
+                                       float4* __restrict__ s2, size_t v0, uint32_t gaddr, uint32_t zoff, int k,
+                                       float tau, bool want_z, uint32_t& zw, int lane, float4 (&pa)[4], float4 (&pc)[4],
                                        const float4* __restrict__ n1, const float4* __restrict__ n2, size_t nv0,
                                        int nk) {
     const float2 ginv2 = make_float2(-J.sg * J.inv_l, -J.sg * J.inv_l);
@@ -473,19 +490,18 @@ __device__ __forceinline__ void step_z(const TczJob& J, const TczLaunch& L, Misc
         }
         if (h == 1 && nk >= 0) load_s_z(n1, n2, nv0, nk, pa, pc);
         if (want_z) {
-            if (h == 0) {
-                // GEMM1 of the previous chunk has read the Z columns
-                wait_z(ms, &ms->z_empty, (zw & 1) ^ 1, L.err);
-                fence_after_sync();
-            }
-            tmem_st8(zcol + kColZHi + 8 * h, zh);
-            tmem_st8(zcol + kColZLo + 8 * h, zl);
+            // GEMM1 of the previous chunk has read this half's Z columns
+            wait_z(ms, &ms->z_empty[h], (zw & 1) ^ 1, L.err);
+            fence_after_sync();
+            tmem_st8(zoff + zcol_hi(h), zh);
+            tmem_st8(zoff + zcol_lo(h), zl);
+            tmem_wait_st();
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ms->z_full[h]);
         }
     }
-    if (want_z) {
-        tmem_wait_st();
-        ++zw;
-    }
+    if (want_z) ++zw;
 }
 
 // Warps 2 .. 17.
@@ -569,14 +585,11 @@ __device__ __forceinline__ void epi_role_z(const TczLaunch& L, MiscZ* ms, uint8_
                     const int kn = c + 1 < nch ? k : k + 1, cn = c + 1 < nch ? c + 1 : 0;
                     step_z<BF>(J, L, ms, s1, s2, vidx(c),
                                lane_addr + kColG + (acc & 1) * kCc + (uint32_t)(kPerThread * cg),
-                               lane_addr + (uint32_t)(kPerThread / 2 * cg), k, tau, want_z, zw, pa, pc,
+                               lane_addr + (uint32_t)(8 * cg), k, tau, want_z, zw, lane, pa, pc,
                                (kn & 1) ? buf0 : buf1, (kn & 1) ? buf1 : buf0, vidx(cn), kn < K ? kn : -1);
                     fence_before_sync();
                     __syncwarp();
-                    if (lane == 0) {
-                        if (want_z) mbar_arrive(&ms->z_full);
-                        mbar_arrive(&ms->acc_empty[acc & 1]);
-                    }
+                    if (lane == 0) mbar_arrive(&ms->acc_empty[acc & 1]);
                 }
                 if (want_z) {
                     // U of z^{k+1} is complete: P for iteration k + 1
@@ -653,8 +666,10 @@ __global__ void __maxnreg__(96) k_fista_tcz(const __grid_constant__ TczLaunch L)
                 mbar_init(&ms->acc_full[a], 1);
                 mbar_init(&ms->acc_empty[a], kEpiWarps);
             }
-            mbar_init(&ms->z_full, kEpiWarps);
-            mbar_init(&ms->z_empty, 1);
+            for (int h = 0; h < 2; ++h) {
+                mbar_init(&ms->z_full[h], kEpiWarps);
+                mbar_init(&ms->z_empty[h], 1);
+            }
             mbar_init(&ms->u_full, 1);
             mbar_init(&ms->p_ready, kEpiWarps);
             mbar_init(&ms->drain, 1);
