@@ -538,7 +538,7 @@ __device__ __forceinline__ void epi_update(const TcsJob& J, uint8_t* __restrict_
         }
         const size_t si = s_index4(jc, cg, c0 / 4, r, nc);
 #pragma unroll
-        for (int v = 0; v < 4; ++v) in.sp[v] = s4[si + (size_t)v * kTile];
+        for (int v = 0; v < 4; ++v) in.sp[v] = ld_stream4(s4 + si + (size_t)v * kTile);   // past L1
     };
     for (int c0 = 0; c0 < w; c0 += 16) {
         uint32_t g[2][8];

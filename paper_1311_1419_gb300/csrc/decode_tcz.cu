@@ -430,13 +430,14 @@ __device__ __forceinline__ float gmax_z(uint32_t gaddr, float mx) {
 }
 
 // The thread's s^{k-1} (a) and s^{k-2} (c) for 16 coefficients at float4 index v0 ..
-// (each 128 float4 apart): zero where iteration k has none (k < 1, k < 2).
+// (each 128 float4 apart): zero where iteration k has none (k < 1, k < 2).  The
+// loads skip L1, which keeps y's rows there.
 __device__ __forceinline__ void load_s_z(const float4* __restrict__ s1, const float4* __restrict__ s2, size_t v0,
                                          int k, float4 (&a)[4], float4 (&c)[4]) {
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-        a[v] = k >= 1 ? s1[v0 + (size_t)v * kTile] : make_float4(0.f, 0.f, 0.f, 0.f);
-        c[v] = k >= 2 ? s2[v0 + (size_t)v * kTile] : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[v] = k >= 1 ? ld_stream4(s1 + v0 + (size_t)v * kTile) : make_float4(0.f, 0.f, 0.f, 0.f);
+        c[v] = k >= 2 ? ld_stream4(s2 + v0 + (size_t)v * kTile) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 }
 

@@ -227,6 +227,16 @@ __device__ __forceinline__ void tmem_wait_st() {
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
+// ---- streamed global loads ----------------------------------------------------
+// A 16-byte load that does not allocate in L1: iterate state read once per pass
+// leaves L1 to the operands that are read again (y).
+__device__ __forceinline__ float4 ld_stream4(const float4* p) {
+    float4 v;
+    asm volatile("ld.global.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "l"(p) : "memory");
+    return v;
+}
+
 // ---- packed FP32 pairs (sm_100+ f32x2 arithmetic, round to nearest) ------------
 __device__ __forceinline__ unsigned long long f2_bits(float2 v) {
     return *reinterpret_cast<unsigned long long*>(&v);
