@@ -3,8 +3,9 @@ GEMM1 in 128-coefficient chunks from tensor memory, s^{k-1} and s^{k-2} in
 global memory) against the FP64 oracle: 16 x 16 and 32 x 32 blocks, M from one
 16-row step to 128 (partial last K slices), ragged tiles, cropped edges, two
 GOPs, iteration counts 0 .. 3, mixed precision, more tiles than SMs, a short last
-round handed to the cluster kernel (also inside a CUDA graph), inside a batch (one
-and both operand types), the engine rules and the bounded-wait failure path."""
+round handed to the cluster kernel (also inside a CUDA graph), the full 720p clip
+at K = 300 on sampled blocks, inside a batch (one and both operand types), the
+engine rules and the bounded-wait failure path."""
 import time
 
 import numpy as np
@@ -297,3 +298,47 @@ def test_tcz_withheld_arrival_times_out_and_recovers(B):
     finally:
         B.cs_plan_destroy(plan)
         B.cs_ctx_destroy(c)
+
+
+def test_tcz_full_720p_clip_sampled_blocks_match_the_oracle(B, ctx):
+    """The 720p workload as the bench decodes it (96 frames, G = 16: 82,800 blocks,
+    647 tiles of 128; M = 102, K = 300) on the chunked engine, the cluster kernel
+    taking the short last round's worth of tiles first where the SM count leaves
+    one.  Blocks sampled from the first tiles, the middle and the ragged last tile
+    (112 rows) match the oracle block by block, and the uint8 frames are the
+    rounded float frames."""
+    h, w, gop, n_gops, b, m, iters, seed = 720, 1280, 16, 6, 32, 102, 300, 41
+    frames, out, u8 = _run(B, ctx, h, w, gop, b, m, iters, seed, n_gops=n_gops)
+    nbr, nbc = -(-h // b), -(-w // b)
+    nblk = nbr * nbc
+    total = n_gops * (gop - 1) * nblk
+    assert total == 82800
+    rng = np.random.default_rng(seed)
+    rows = np.concatenate([rng.choice(39 * 128, 32, replace=False),          # the first tiles
+                           39 * 128 + rng.choice(total - 40 * 128, 32, replace=False),
+                           (total // 128) * 128 + rng.choice(total % 128, 16, replace=False)])
+    oplan = O.Plan(b * b, m, seed)
+    yo = O.encode(oplan, frames, gop)
+    r_hat = O.decode_blocks(oplan, yo.reshape(-1, m)[rows], iters)
+    got, want, res_got, res_want = [], [], [], []
+    for i, r in enumerate(rows):
+        c, blk = divmod(int(r), nblk)
+        bi, bj = divmod(blk, nbc)
+        hh, ww = min(b, h - bi * b), min(b, w - bj * b)              # 720 = 22.5 blocks
+        sl = (slice(bi * b, bi * b + hh), slice(bj * b, bj * b + ww))
+        key = frames[(c // (gop - 1)) * gop].astype(np.float64)
+        g = out[c][sl].ravel()
+        rb = r_hat[i].reshape(b, b)[:hh, :ww].ravel()
+        want.append(key[sl].ravel() + rb)
+        got.append(g)
+        res_got.append(g - key[sl].ravel())
+        res_want.append(rb)
+        assert np.array_equal(u8[c][sl].ravel(), np.clip(np.rint(g), 0, 255).astype(np.uint8)), r
+    got, want = np.concatenate(got), np.concatenate(want)
+    res_got, res_want = np.concatenate(res_got), np.concatenate(res_want)
+    err = np.linalg.norm(got - want) / np.linalg.norm(want)
+    res_err = np.linalg.norm(res_got - res_want) / np.linalg.norm(res_want)
+    print("720p M=102 K=300 chunked, %d sampled blocks: frame rel-l2 %.3g, residual rel-l2 %.3g"
+          % (len(rows), err, res_err))
+    assert err <= 1e-4
+    assert res_err <= 1e-3
