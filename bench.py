@@ -73,7 +73,7 @@ L2_FLUSH_BYTES = 256 << 20
 # one cluster-kernel launch for the first 39 tiles and one chunked launch for the
 # other 608); reported as roofline.traffic when the step's decode ran on that
 # engine, null otherwise
-DECODE_DRAM_BYTES = {"cif": (2, 62_840_000), "720p": (4, 237_024_000_000)}
+DECODE_DRAM_BYTES = {"cif": (2, 62_840_000), "720p": (4, 236_941_000_000)}
 
 
 def decode_traffic(workload, res):

@@ -55,9 +55,11 @@ constexpr int kStages = 6;
 constexpr uint32_t kTBytes = kTile * 64;    // one 32-wide K slice of P (8 KB)
 constexpr uint32_t kPBytes = (kMaxM16z / kSliceK) * kTBytes;   // P hi (or lo): 32 KB
 constexpr uint32_t kOffP = kStages * kStageBytes;              // P hi, then P lo
-constexpr uint32_t kOffC = kOffP + 2 * kPBytes;                // DCT matrix, <= 32 x 32 floats
-constexpr uint32_t kOffMisc = kOffC + 4096;
-constexpr uint32_t kSmemBytes = kOffMisc + 2048 + 1024;        // + alignment slack
+constexpr uint32_t kOffMisc = kOffP + 2 * kPBytes;
+// 162 KB in all: with the SM's 1 KB reserve it fits the 164 KB shared-memory split, which
+// leaves about 92 KB of L1 for the tile's y rows, read again every iteration (the DCT
+// matrix waits in the P area, idle during reconstruction)
+constexpr uint32_t kSmemBytes = kOffMisc + 1024 + 1024;        // + alignment slack
 constexpr uint32_t kColG = 0;               // two G accumulators of 128 columns
 constexpr uint32_t kColU = 256;             // U: M16 <= 128 columns
 // the Z chunk in two halves: half h holds coefficients 32 j + 16 h .. 32 j + 16 h + 15 of
@@ -117,7 +119,7 @@ struct MiscZ {
     int job;
     uint32_t colmax[kTile];
 };
-static_assert(sizeof(MiscZ) <= 2048, "barrier block");
+static_assert(sizeof(MiscZ) <= 1024, "barrier block");
 static_assert(kOffMisc + sizeof(MiscZ) + 1024 <= kSmemBytes, "shared memory layout");
 
 template <bool BF>
@@ -519,7 +521,6 @@ __device__ __forceinline__ void epi_role_z(const TczLaunch& L, MiscZ* ms, uint8_
     float4* y4 = reinterpret_cast<float4*>(scr + kScrY);
     uint8_t* p_hi = sm + kOffP;
     uint8_t* p_lo = p_hi + kPBytes;
-    float* c_s = reinterpret_cast<float*>(sm + kOffC);
     uint32_t acc = 0, zw = 0, uc = 0;
     bool first_tile = true;
     for (;;) {
@@ -529,7 +530,6 @@ __device__ __forceinline__ void epi_role_z(const TczLaunch& L, MiscZ* ms, uint8_
         const GopShape& gs = J.gs;
         const int n = J.n, m16 = J.m16, K = J.iters, bsz = gs.b, nch = n / kCc;
         if (cg == 0) ms->colmax[r] = 0u;
-        for (int i = et; i < bsz * bsz; i += kEpiThreads) c_s[i] = J.dct[i];
         cta_sync_z();   // B
         const long long tile_row0 = J.row0 + (long long)(tile - J.tile_begin) * kTile;
         if (K > 0) {
@@ -607,10 +607,12 @@ __device__ __forceinline__ void epi_role_z(const TczLaunch& L, MiscZ* ms, uint8_
         }
         // --- reconstruct: R = C^T S C per block, S = s^{K-1}, one block at a time
         // (four for 16 x 16), through the idle P area of shared memory ---
-        __threadfence_block();
-        named_sync(kBarEpi, kEpiThreads);
         float* s_s = reinterpret_cast<float*>(sm + kOffP);
         float* t_s = s_s + 1024;
+        float* c_s = t_s + 1024;                      // the DCT matrix, <= 32 x 32
+        for (int i = et; i < bsz * bsz; i += kEpiThreads) c_s[i] = J.dct[i];
+        __threadfence_block();
+        named_sync(kBarEpi, kEpiThreads);
         const float4* sK = (K > 0 && ((K - 1) & 1)) ? buf1 : buf0;
         const int gb = 1024 / n;
         const size_t frame_px = (size_t)gs.h * gs.w;
