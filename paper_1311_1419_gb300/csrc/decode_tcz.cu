@@ -18,8 +18,10 @@
 // never goes to global memory.  The step recomputes z^k = s^{k-1} +
 // beta_{k-1} (s^{k-1} - s^{k-2}) in FP32 from the two previous iterates, which
 // stay in global memory (the new s^k is written over s^{k-2}): 8 bytes read and
-// 4 written per coefficient and iteration.  P stays in shared memory; only the
-// slices of A's two images stream, through a six-stage ring fed by a copy warp.
+// 4 written per coefficient and iteration, the reads past L1 so that L1 keeps the
+// tile's y rows, which every iteration's residual reads again.  P stays in shared
+// memory; only the slices of A's two images stream, through a six-stage ring fed
+// by a copy warp.
 // Tensor memory: two 128-column G accumulators (the step of chunk c overlaps
 // GEMM2 of chunk c + 1), U (M16 columns) and the Z chunk's hi and lo halves.
 // Mixed precision: a split product uses three MMAs (hi.hi + lo.hi + hi.lo), a
