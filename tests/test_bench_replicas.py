@@ -81,3 +81,18 @@ def test_mixed_launch_count():
     # launch; one of 216 tiles (64 left over) does not
     assert bench.mixed_launches(jobs + [dict(job(32, 102, 4), blocks=82800)]) == 2 + 1 + 1 + 1 + 2 + 1 + 1
     assert bench.mixed_launches(jobs + [dict(job(32, 102, 4), blocks=27600)]) == 2 + 1 + 1 + 1 + 2 + 1
+
+
+def test_decode_traffic_only_for_the_captured_engine():
+    """roofline.traffic is the stored ncu figure of a workload only when the step's
+    decode ran on the engine that capture measured (the chunked engine for 720p, the
+    on-chip one for the CIF sweep); any other engine, or a mix, reports null."""
+    import bench
+    eng_720p, bytes_720p = bench.DECODE_DRAM_BYTES["720p"]
+    assert bench.decode_traffic("720p", {"engines": [eng_720p]}) == bytes_720p
+    assert bench.decode_traffic("720p", {"engines": [1]}) is None
+    assert bench.decode_traffic("720p", {"engines": [2, eng_720p]}) is None
+    eng_cif, bytes_cif = bench.DECODE_DRAM_BYTES["cif"]
+    assert bench.decode_traffic("cif", {"engines": [eng_cif]}) == bytes_cif
+    assert bench.decode_traffic("cif", {"engines": [3]}) is None
+    assert bench.decode_traffic("mixed64", {"engines": [eng_cif]}) is None
