@@ -1090,7 +1090,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": wl["workload"], "engine": args.engine,
                        "decode": "per-M calls" if args.no_batch else
-                       "one batched launch (%d plans)" % len(wl["ms"]),
+                       "one batched cs_decode_batch call (%d plan%s)" % (len(wl["ms"]), "" if len(wl["ms"]) == 1 else "s"),
                        "l2": "flushed before every timed step (256 MB write)",
                        "parallelism": "replicas x%d" % world},
             "roofline": roof,
